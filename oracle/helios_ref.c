@@ -515,9 +515,12 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
  * layer that loses more net flux through its top than it receives at its
  * bottom cools (the printed sign makes the iteration run away).
  * Oscillation control (Sect. 2.2.4; reading): the signs of the last 6
- * temperature changes are kept; once 6 are recorded, strictly alternating
- * signs reduce m_i by 33% (x0.67), six equal signs increase it by 10% (x1.1,
- * capped at mult_max), anything else leaves it.  T is floored at T_floor.
+ * temperature changes are kept; once 6 are recorded, six equal signs (a
+ * monotonic change) increase m_i by 10% (x1.1, capped at mult_max) and any
+ * sign change among them counts as an oscillation and reduces m_i by 33%
+ * (x0.67).  The paper makes the two cases complementary ("no oscillations
+ * ... i.e. monotonic"); treating only strict alternation as an oscillation
+ * leaves period-4 cycles (++--) undamped forever.  T is floored at T_floor.
  * hist bit 0 is the newest sign (1 = positive change). */
 int ref_temp_update(const ref_atm* a, const ref_params* p, const double* Fup_bol, const double* Fdn_bol,
                     double* T, double* mult, int* hist, int* nhist, double* metric, double* dT)
@@ -561,10 +564,11 @@ int ref_temp_update(const ref_atm* a, const ref_params* p, const double* Fup_bol
         hist[i] = ((hist[i] << 1) | (step > 0.0 ? 1 : 0)) & 0x3F;
         if (nhist[i] < 6) nhist[i] += 1;
         if (nhist[i] >= 6) {
-            if (hist[i] == 0x15 || hist[i] == 0x2A) mult[i] *= p->osc_down;
-            else if (hist[i] == 0x00 || hist[i] == 0x3F) {
+            if (hist[i] == 0x00 || hist[i] == 0x3F) {
                 mult[i] *= p->osc_up;
                 if (mult[i] > p->mult_max) mult[i] = p->mult_max;
+            } else {
+                mult[i] *= p->osc_down;
             }
         }
     }

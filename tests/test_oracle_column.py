@@ -1,0 +1,189 @@
+"""Column-level pins of the oracle: closed forms and invariants of whole flux sweeps and of
+the radiative-equilibrium iteration.
+
+(a) isothermal pure absorption: cavity (every point carries pi B) and semi-infinite slab
+    (emergent flux in closed form);
+(b) D = 2 two-stream vs the exact pure-absorption solution: D = 2 is the best of
+    {1.66, 1.8, 1.9, 2} and its error shrinks under layer refinement (Sect. 3.1.5, Fig. 1);
+(c) conservative scattering conserves net flux through the column;
+(d) at radiative equilibrium the net flux is sigma T_int^4 at every interface;
+(e) the grey two-band case lands on the analytic two-stream grey profile.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SIG = oracle.SIGMA_SB
+
+
+def _const_table(L, G, kappa_lg):
+    t = synth.KTable(nP=2, nT=2, L=L, G=G, log10P0=-6.0, dlog10P=9.0, T0=200.0, dT=2800.0,
+                     kappa32=np.empty((2, 2, L, G), np.float32))
+    k = np.broadcast_to(kappa_lg, (2, 2, L, G)).copy()
+    t.kappa32[...] = k.astype(np.float32)
+    return t, k
+
+
+def _atm(n, L, T_irr, T_int, T_star, omega0=None, g0=None, P_top=1e-6, P_bot=1e2, grav=1000.0):
+    e = synth.nu_edges(L)
+    return synth.Atmosphere(n_layers=n, P_top_bar=P_top, P_bot_bar=P_bot, grav=grav, T_irr=T_irr, T_int=T_int,
+                            T_star=T_star, nu_edges=e,
+                            omega0=np.zeros(L, np.float32) if omega0 is None else omega0,
+                            g0=np.zeros(L, np.float32) if g0 is None else g0, table_id=0,
+                            T_init=np.full(n, 1000.0))
+
+
+def _planck(a, T):
+    return np.array([oracle.planck_bin(x, y, T) for x, y in zip(a.nu_edges[:-1], a.nu_edges[1:])])
+
+
+def _cavity_atm(T, L=12, G=4, omega0=None, g0=None):
+    B = None
+    e = synth.nu_edges(L)
+    B = np.array([oracle.planck_bin(x, y, T) for x, y in zip(e[:-1], e[1:])])
+    T_irr = (math.pi * B.sum() / SIG) ** 0.25
+    kap = np.logspace(-4, 1, L * G).reshape(L, G)
+    t, k = _const_table(L, G, kap)
+    a = _atm(20, L, T_irr, 0.0, T, omega0, g0)
+    return oracle.Atm(a, t, kappa64=k), B
+
+
+def test_isothermal_cavity_pure_absorption():
+    atm, B = _cavity_atm(1100.0)
+    r = oracle.flux_sweep(atm, np.full(20, 1100.0), spectra=True)
+    ref = math.pi * B[:, None]
+    assert np.allclose(r["up_spec"], ref, rtol=1e-12) and np.allclose(r["dn_spec"], ref, rtol=1e-12)
+
+
+def test_isothermal_cavity_with_scattering_is_a_fixed_point_of_the_passes():
+    L, G = 12, 4
+    w0 = np.linspace(0.05, 0.95, L).astype(np.float32)
+    g0 = np.linspace(-0.5, 0.6, L).astype(np.float32)
+    atm, B = _cavity_atm(900.0, L, G, w0, g0)
+    np_ = 2 * 20 + 1
+    warm = np.repeat(math.pi * B, G * np_)                   # [L][G][2n+1] = pi B_l
+    r = oracle.flux_sweep(atm, np.full(20, 900.0), n_passes=5, warm=warm, warm_valid=True, spectra=True)
+    ref = math.pi * B[:, None]
+    assert np.allclose(r["up_spec"], ref, rtol=1e-11) and np.allclose(r["dn_spec"], ref, rtol=1e-11)
+    # from a cold start the passes converge to the same field
+    r2 = oracle.flux_sweep(atm, np.full(20, 900.0), n_passes=600, spectra=True)
+    assert np.allclose(r2["up_spec"], ref, rtol=1e-8) and np.allclose(r2["dn_spec"], ref, rtol=1e-8)
+
+
+def test_semi_infinite_isothermal_slab_closed_form():
+    L, G, n, T = 10, 6, 30, 1300.0
+    kap = np.logspace(-6, -2, L * G).reshape(L, G)
+    t, k = _const_table(L, G, kap)
+    a = _atm(n, L, 0.0, 0.0, 5000.0)
+    atm = oracle.Atm(a, t, kappa64=k)
+    r = oracle.flux_sweep(atm, np.full(n, T))
+    _, P, _, _ = oracle.grid(atm)
+    _, w = oracle.gauss_legendre(G)
+    B = _planck(a, T)
+    tau = kap * (P[0] - P[-1]) / a.grav                       # [L, G]
+    e = np.exp(-2.0 * tau)
+    F0 = math.pi * B[:, None] * (1 - e)                       # BOA reflects the downward stream
+    Ftop = math.pi * B[:, None] * (1 - e) + e * F0
+    assert np.allclose(r["toa"], (Ftop * (w / 2)).sum(axis=1), rtol=1e-12)
+
+
+def _refined(n, D, exact=False):
+    wl = synth.config1()
+    base = wl.atms[0]
+    a = synth.Atmosphere(n_layers=n, P_top_bar=1e-6, P_bot_bar=1e2, grav=1000.0, T_irr=1200.0, T_int=100.0,
+                         T_star=5000.0, nu_edges=base.nu_edges, omega0=base.omega0, g0=base.g0, table_id=0,
+                         T_init=np.full(n, 1000.0))
+    atm = oracle.Atm(a, wl.tables[0])
+    x = np.linspace(0.0, 1.0, n)
+    T = 1500.0 - 600.0 * x + 100.0 * np.sin(6.0 * x)
+    r = oracle.flux_sweep(atm, T, p=oracle.params(D=D), exact=exact)
+    return r["Fup"][-1]
+
+
+def test_diffusivity_two_is_best_and_converges_to_exact_under_refinement():
+    errs = {}
+    for n in (25, 100, 400):
+        ex = _refined(n, 2.0, exact=True)
+        errs[n] = {D: abs(_refined(n, D) / ex - 1.0) for D in (1.66, 1.8, 1.9, 2.0)}
+        assert errs[n][2.0] < min(errs[n][D] for D in (1.66, 1.8, 1.9))
+    assert errs[25][2.0] > errs[100][2.0] > errs[400][2.0]
+    assert errs[400][2.0] < 3e-3
+
+
+def test_conservative_scattering_conserves_net_flux():
+    L, G, n = 6, 3, 25
+    kap = np.logspace(-5, -3, L * G).reshape(L, G)
+    t, k = _const_table(L, G, kap)
+    a = _atm(n, L, 1000.0, 300.0, 5000.0, omega0=np.ones(L, np.float32),
+             g0=np.linspace(-0.4, 0.6, L).astype(np.float32))
+    atm = oracle.Atm(a, t, kappa64=k)
+    r = oracle.flux_sweep(atm, np.linspace(1500, 800, n), n_passes=3000, spectra=True)
+    net = r["up_spec"] - r["dn_spec"]                        # [L, 2n+1]
+    scale = np.abs(r["up_spec"]).max(axis=1, keepdims=True)
+    assert (np.abs(net - net[:, :1]) < 1e-10 * scale).all()
+
+
+def test_passes_compose_with_warm_start():
+    wl = synth.small_scattering(L=8, n=12)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 5)
+    warm = np.zeros(atm.L * atm.G * (2 * atm.n + 1))
+    a = oracle.flux_sweep(atm, T, n_passes=7)
+    oracle.flux_sweep(atm, T, n_passes=3, warm=warm, warm_valid=False)
+    b = oracle.flux_sweep(atm, T, n_passes=4, warm=warm, warm_valid=True)
+    assert np.allclose(a["Fup"], b["Fup"], rtol=1e-14) and np.allclose(a["Fdn"], b["Fdn"], rtol=1e-14)
+
+
+def test_temperature_step_closed_form_and_sign():
+    # eqs. (24)-(28) collapse to dT = -m 1e5 sgn(dF) |dF|^0.1 / (sigma T^3 ln(P_i/P_i+1))
+    wl = synth.config1()
+    atm = oracle.Atm.from_workload(wl)
+    n = atm.n
+    st = oracle.State(atm, np.linspace(1400, 900, n))
+    rng = np.random.default_rng(7)
+    Fu = 1e8 + rng.normal(0, 1e5, n + 1)
+    Fd = 1e8 + rng.normal(0, 1e5, n + 1)
+    T0 = st.T.copy()
+    rc, metric, dT = oracle.temp_update(atm, st, Fu, Fd)
+    assert rc == oracle.UPDATED
+    _, P, _, _ = oracle.grid(atm)
+    dF = np.diff(Fu - Fd)
+    expect = -1e5 * np.sign(dF) * np.abs(dF) ** 0.1 / (SIG * T0 ** 3 * np.log(P[0:-1:2] / P[2::2]))
+    assert np.allclose(dT, expect, rtol=1e-12)
+    assert metric == pytest.approx(np.max(np.abs(dF) / (SIG * T0 ** 4)), rel=1e-14)
+
+
+def test_converged_net_flux_equals_internal_flux():
+    wl = synth.config1()
+    atm = oracle.Atm.from_workload(wl)
+    st = oracle.State(atm, wl.atms[0].T_init)
+    rc, it, m = oracle.solve_re(atm, st, oracle.params(tol=1e-11, max_iter=100000))
+    assert rc == oracle.CONVERGED
+    r = oracle.flux_sweep(atm, st.T, warm=st.warm, warm_valid=True)
+    net = r["Fup"] - r["Fdn"]
+    assert np.allclose(net, SIG * 100.0 ** 4, rtol=1e-5)
+    # the emergent flux balances what enters: sigma (T_irr^4 + T_int^4) leaves the top
+    assert r["Fup"][-1] == pytest.approx(SIG * (1200.0 ** 4 + 100.0 ** 4), rel=1e-6)
+
+
+def _grey_error(n):
+    g = synth.grey_two_band(n=n)
+    atm = oracle.Atm.from_workload(g)
+    st = oracle.State(atm, g.atms[0].T_init)
+    rc, it, m = oracle.solve_re(atm, st, oracle.params(tol=1e-10, max_iter=200000))
+    assert rc == oracle.CONVERGED
+    _, P, _, Pl = oracle.grid(atm)
+    gam, kth, D = g.meta["gamma"], g.meta["kappa_th"], 2.0
+    tau = kth * (Pl - P[-1]) / g.atms[0].grav
+    T4 = (D / 4) * (100.0 ** 4 * (1 + D * tau) + 1200.0 ** 4 * (1 + 1 / gam + (gam - 1 / gam) * np.exp(-D * gam * tau)))
+    return np.abs(st.T / T4 ** 0.25 - 1.0).max()
+
+
+def test_grey_two_band_matches_analytic_profile():
+    e25, e50 = _grey_error(25), _grey_error(50)
+    assert e50 < 1e-3           # 0.1% in T at 50 layers
+    assert e25 > 3.0 * e50      # second-order convergence under refinement
