@@ -1,0 +1,212 @@
+/*
+ * helios.h -- C ABI of the B300-native radiative-equilibrium hot path of
+ * HELIOS (Malik et al. 2016, arXiv:1606.05474).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units are CGS (erg, cm, g, s, K); pressures are given in bar.
+ * An atmosphere has n layers (layer 0 at the bottom), n+1 interfaces
+ * (interface 0 = BOA, interface n = TOA; Sect. 2.2.1, Fig. 2) and, with the
+ * non-isothermal two-sublayer grid, 2n+1 points (point 2i = interface i,
+ * point 2i+1 = centre of layer i).
+ * A batch holds A atmospheres with their own layer and bin counts.  Per-layer
+ * arrays are packed atmosphere after atmosphere: atmosphere a starts at
+ * sum_{b<a} n_b (layers), sum_{b<a} (n_b+1) (interfaces), sum_{b<a} L_b
+ * (bins), sum_{b<a} (2 n_b + 1) (points).
+ *
+ * Memory ownership: pointers documented "host" are read during the call only.
+ * Pointers documented "device" are caller-owned device memory on the plan's
+ * device; the library never frees them.  The library allocates only its
+ * context, its plans and each plan's internal workspace (helios_plan_create).
+ *
+ * Streams: every compute call is asynchronous on the given CUDA stream and
+ * returns before the GPU work completes, except helios_solve_re, which
+ * synchronises (it reads back the number of atmospheres still iterating).
+ *
+ * Errors: every call returns HELIOS_OK (0) or a negative code; the message of
+ * the last failure on the calling thread is returned by helios_last_error().
+ * The library never aborts, traps or prints.  Invalid arguments are rejected
+ * before any GPU work is queued.
+ */
+#ifndef HELIOS_H
+#define HELIOS_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HELIOS_VERSION 100
+
+enum {
+    HELIOS_OK = 0,
+    HELIOS_EINVAL = -1,     /* bad shape, pointer or parameter */
+    HELIOS_ENOMEM = -2,     /* workspace allocation failed */
+    HELIOS_ECUDA = -3,      /* a CUDA call failed (message in helios_last_error) */
+    HELIOS_ENOCONV = -5     /* helios_solve_re: some atmosphere did not converge (see status[]) */
+};
+
+/* Per-atmosphere status of the radiative-equilibrium iteration. */
+enum {
+    HELIOS_ATM_ACTIVE = 0,        /* still iterating */
+    HELIOS_ATM_CONVERGED = 1,     /* eq. (29) holds in every layer */
+    HELIOS_ATM_NOT_CONVERGED = 2, /* hit max_iter */
+    HELIOS_ATM_NONFINITE = 3      /* a non-finite flux or temperature appeared; frozen */
+};
+
+typedef struct helios_ctx helios_ctx;
+typedef struct helios_plan helios_plan;
+
+/* Correlated-k table (Sect. 2.3): kappa[nP][nT][L][G] in cm^2/g (device,
+ * float32, 16-byte aligned), tabulated at log10 P[bar] = log10P0 + i*dlog10P
+ * and T[K] = T0 + j*dT.  Interpolated bilinearly in (T, log10 P) and clamped
+ * to the nearest tabulated value outside the table (Sect. 2.3, footnote).
+ * G is the number of Gauss-Legendre points per bin (1 <= G <= 32); the
+ * table's g index runs over the Gauss-Legendre nodes of [0, 1] in ascending
+ * order (eqs. 30-32).  All tables of a plan share one G. */
+typedef struct {
+    int nP, nT, L, G;
+    double log10P0, dlog10P, T0, dT;
+    const float* kappa;
+} helios_ktable_t;
+
+/* A batch of atmospheres (all arrays host, read by helios_plan_create only).
+ * Atmosphere a: n_layers[a] >= 2 layers whose centres are log-spaced from
+ * P_bot_bar[a] (bottom) to P_top_bar[a] (top) (Sect. 2.2.1, Sect. 3);
+ * n_bins[a] >= 1 wavelength bins with edges nu_edges (cm^-1, increasing,
+ * n_bins[a]+1 values, packed); per-bin single-scattering albedo omega0 and
+ * asymmetry factor g0 (packed, n_bins[a] values, Sect. 2.1.1); it uses bins
+ * 0..n_bins[a]-1 of table table_id[a].  grav: cm s^-2.  T_irr: the incident
+ * diffuse stellar flux is sigma*T_irr^4, spread over the bins like a
+ * blackbody at T_star (Sect. 2.2.2, eq. 20, with f (R_star/a)^2 folded into
+ * T_irr).  T_int: the internal flux sigma*T_int^4 enters at the BOA, spread
+ * like a blackbody at T_int (eqs. 21-22). */
+typedef struct {
+    int A;
+    const int32_t* n_layers;
+    const int32_t* n_bins;
+    const int32_t* table_id;
+    const double* P_top_bar;
+    const double* P_bot_bar;
+    const double* grav;
+    const double* T_irr;
+    const double* T_int;
+    const double* T_star;
+    const double* nu_edges;
+    const float* omega0;
+    const float* g0;
+} helios_batch_t;
+
+/* Method parameters; helios_default_params fills the paper's values. */
+typedef struct {
+    double D;            /* diffusivity factor, eps = 1/D (Sect. 3: 2) */
+    double dtau_iso;     /* sublayers thinner than this use the isothermal form (Sect. 2.2.1: 1e-4) */
+    double w0_pure;      /* 1 - omega0 below this uses the pure-scattering form (Sect. 2.1.4: 1e-6) */
+    double tol;          /* convergence: |dF_i|/(sigma T_i^4) < tol in every layer (eq. 29: 1e-7) */
+    double fpre_num;     /* f_pre = fpre_num / |dF|^fpre_exp (eq. 28: 1e5, 0.9) */
+    double fpre_exp;
+    double osc_down;     /* timestep factor after an oscillation (Sect. 2.2.4: 0.67) */
+    double osc_up;       /* timestep factor after a monotonic run (Sect. 2.2.4: 1.1) */
+    double mult_max;     /* cap on the per-layer timestep multiplier (1e4) */
+    double T_floor;      /* temperatures are kept >= T_floor (1 K) */
+    int n_scat;          /* extra scattering passes per temperature step (Sect. 2.2.3: 4) */
+    int max_iter;        /* helios_solve_re: maximum flux evaluations per atmosphere */
+    int grey_mode;       /* 1: two-bin grey test mode (bin 0 visible: no emission, all stellar flux;
+                            bin 1 thermal: pi*B = sigma T^4, all internal flux) */
+    int printed_gradient;/* 1: gradient prefactor eps/(1 + w0 g0) as printed in eq. (15) */
+    int bins_per_item;   /* bins one thread block processes per work item (0: automatic) */
+    int check_every;     /* helios_solve_re: iterations per CUDA-graph launch between checks (0: auto) */
+} helios_params_t;
+
+void helios_default_params(helios_params_t* p);
+int helios_version(void);
+const char* helios_last_error(void);
+
+/* Context on CUDA device `device`; owns an internal stream used by
+ * helios_solve_re for graph capture. */
+int helios_create(helios_ctx** ctx, int device);
+int helios_destroy(helios_ctx* ctx);
+
+/* Validate a batch, precompute its static geometry (Sect. 2.2.1: pressure
+ * grid, sublayer column masses eq. 19, pressure-table indices), per-bin
+ * constants (Planck prefactors, boundary spectra eqs. 20-22, two-stream
+ * coefficients eqs. 8, 12-14), Gauss-Legendre weights (eqs. 31-32) and the
+ * work list, and allocate the plan's workspace (warm-start fluxes, partial
+ * sums, iteration state).  tables: host array of ntab descriptors whose
+ * kappa pointers are device memory that must outlive the plan. */
+int helios_plan_create(helios_ctx* ctx, const helios_batch_t* batch, const helios_ktable_t* tables, int ntab,
+                       const helios_params_t* params, helios_plan** plan);
+int helios_plan_destroy(helios_plan* plan);
+
+/* Packed sizes of a plan: total layers, interfaces, points, bins; the number
+ * of passes per temperature step (1 + n_scat if any omega0 > 0, else 1);
+ * bytes of workspace held. */
+typedef struct {
+    int64_t layers, interfaces, points, bins, cells;
+    int passes;
+    int64_t workspace_bytes;
+} helios_plan_info_t;
+int helios_plan_info(const helios_plan* plan, helios_plan_info_t* info);
+
+/* Opacity at every point, bin and Gauss point (Sect. 2.3): bilinear
+ * interpolation of the k-table in (T, log10 P), T at interfaces the mean of
+ * the adjacent centres (outer interfaces: the nearest centre).
+ *   T_layer   device, double [layers]
+ *   kappa_pts device, float, packed per atmosphere [2n+1][L][G]   (may be NULL)
+ *   idx_pts   device, int32 [points][2] = (iP, iT)                (may be NULL)
+ *   w_pts     device, double [points][2] = (wP, wT)               (may be NULL)
+ * Indices and weights are computed in IEEE double without contraction and
+ * match a plain C evaluation of the same formula bit for bit. */
+int helios_interp_opacity(helios_plan* plan, const double* T_layer, float* kappa_pts, int32_t* idx_pts,
+                          double* w_pts, cudaStream_t stream);
+
+/* One flux evaluation at the temperatures T_layer (Sects. 2.1.3, 2.2.2,
+ * 2.2.3, 2.3): opacities, sublayer optical depths (eq. 19), two-stream
+ * transmission and coefficients (eqs. 8, 11-15; thin sublayers eq. 11,
+ * pure scattering eq. 14), n_passes down/up passes with the boundary
+ * conditions of eqs. 20 and 22, Gauss-point sum (eq. 31) and bin sum.
+ *   T_layer  device, double [layers]
+ *   n_passes >= 1, or 0 for the plan's default (1 + n_scat with scattering)
+ *   warm     0: the coupled stream starts from zero (first temperature step);
+ *            1: it starts from the upward fluxes of this plan's previous
+ *               evaluation (later temperature steps, Sect. 2.2.3)
+ *   Fup_bol, Fdn_bol  device, double [interfaces]: bolometric fluxes
+ *   Fup_toa  device, float [bins]: emergent TOA spectrum per bin (may be NULL)
+ * Results are deterministic (fixed-order reductions). */
+int helios_flux_sweep(helios_plan* plan, const double* T_layer, int n_passes, int warm, double* Fup_bol,
+                      double* Fdn_bol, float* Fup_toa, cudaStream_t stream);
+
+/* One temperature step (Sects. 2.2.3-2.2.4, eqs. 23-29) for every atmosphere
+ * whose status is HELIOS_ATM_ACTIVE:
+ *   dF_i = (Fup-Fdn)(i+1) - (Fup-Fdn)(i); if max_i |dF_i|/(sigma T_i^4) < tol
+ *   the atmosphere becomes CONVERGED and T is left as is; otherwise
+ *   dT_i = -mult_i f_pre t_rad dF_i/(rho_i c_p dz_i), T floored at T_floor, and
+ *   the per-layer timestep multiplier follows the oscillation rule (six equal
+ *   signs: x osc_up, capped at mult_max; any sign change among the last six:
+ *   x osc_down).  All in double precision.
+ *   Fup_bol, Fdn_bol device double [interfaces]; T_layer device double [layers] (in/out)
+ *   mult  device double [layers] (in/out; start at 1)
+ *   hist  device uint8 [layers] (in/out; bit 0 = newest sign, 1 = warming; start 0)
+ *   nhist device uint8 [layers] (in/out; signs recorded so far, saturates at 6; start 0)
+ *   status device int32 [A] (in/out), iters device int32 [A] (incremented; may be NULL)
+ *   metric device double [A] (out: max |dF|/(sigma T^4); may be NULL) */
+int helios_temp_update(helios_plan* plan, const double* Fup_bol, const double* Fdn_bol, double* T_layer,
+                       double* mult, uint8_t* hist, uint8_t* nhist, int32_t* status, int32_t* iters,
+                       double* metric, cudaStream_t stream);
+
+/* The radiative-equilibrium iteration (Sect. 2.2.3): flux evaluation and
+ * temperature step repeated, every atmosphere dropping out when it converges,
+ * until none is active or max_iter evaluations were made.  The iteration runs
+ * as CUDA graphs on the context's stream, ordered after the work already on
+ * `stream`; the call returns when it is done.
+ *   T_layer device double [layers]: start profile in, final profile out
+ *   iters   device int32 [A] (out), status device int32 [A] (out)
+ * Returns HELIOS_ENOCONV if any atmosphere ends NOT_CONVERGED or NONFINITE. */
+int helios_solve_re(helios_plan* plan, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

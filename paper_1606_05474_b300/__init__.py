@@ -1,0 +1,214 @@
+"""B300-native radiative-equilibrium hot path of HELIOS (Malik et al. 2016, arXiv:1606.05474).
+
+Python binding of the C ABI in ``include/helios.h``: argument marshalling only.
+Every step of the method runs in the CUDA kernels of ``libhelios.so``;
+PyTorch supplies device memory and streams.  There is no CPU fallback: the
+package raises if the library or a CUDA device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ATM_ACTIVE, ATM_CONVERGED, ATM_NONFINITE, ATM_NOT_CONVERGED, HeliosError,  # noqa: F401
+                   check)
+
+__all__ = ["Context", "Plan", "default_params", "HeliosError", "build"]
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)
+
+
+def default_params(**overrides) -> _lib.Params:
+    p = _lib.Params()
+    _lib.load().helios_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_1606_05474_b300 needs a CUDA device; there is no CPU path")
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """A library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        _torch()
+        self.lib = _lib.load()
+        self.device = device
+        h = ctypes.c_void_p()
+        check(self.lib.helios_create(ctypes.byref(h), device))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.helios_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A validated batch of atmospheres with its device workspace.
+
+    atms: objects with n_layers, n_bins, table_id, P_top_bar, P_bot_bar, grav, T_irr,
+    T_int, T_star, nu_edges, omega0, g0.  tables: objects with nP, nT, L, G, log10P0,
+    dlog10P, T0, dT.  kappa: one float32 CUDA tensor [nP, nT, L, G] per table.
+    """
+
+    def __init__(self, ctx: Context, atms: Sequence, tables: Sequence, kappa: Sequence, params=None):
+        torch = _torch()
+        self.ctx, self.lib = ctx, ctx.lib
+        self.params = params if params is not None else default_params()
+        A = len(atms)
+        self.A = A
+        self.n = np.array([a.n_layers for a in atms], dtype=np.int32)
+        self.L = np.array([a.n_bins for a in atms], dtype=np.int32)
+        self._host = {
+            "n_layers": self.n,
+            "n_bins": self.L,
+            "table_id": np.array([a.table_id for a in atms], dtype=np.int32),
+            "P_top_bar": np.array([a.P_top_bar for a in atms], dtype=np.float64),
+            "P_bot_bar": np.array([a.P_bot_bar for a in atms], dtype=np.float64),
+            "grav": np.array([a.grav for a in atms], dtype=np.float64),
+            "T_irr": np.array([a.T_irr for a in atms], dtype=np.float64),
+            "T_int": np.array([a.T_int for a in atms], dtype=np.float64),
+            "T_star": np.array([a.T_star for a in atms], dtype=np.float64),
+            "nu_edges": np.ascontiguousarray(np.concatenate([np.asarray(a.nu_edges, np.float64) for a in atms])),
+            "omega0": np.ascontiguousarray(np.concatenate([np.asarray(a.omega0, np.float32) for a in atms])),
+            "g0": np.ascontiguousarray(np.concatenate([np.asarray(a.g0, np.float32) for a in atms])),
+        }
+        b = _lib.Batch()
+        b.A = A
+        for k, v in self._host.items():
+            setattr(b, k, v.ctypes.data)
+        self.kappa = list(kappa)
+        for k in self.kappa:
+            if not (k.is_cuda and k.dtype == torch.float32 and k.is_contiguous()):
+                raise ValueError("k-tables must be contiguous float32 CUDA tensors")
+        tabs = (_lib.KTable * len(tables))()
+        for i, (t, k) in enumerate(zip(tables, self.kappa)):
+            tabs[i].nP, tabs[i].nT, tabs[i].L, tabs[i].G = t.nP, t.nT, t.L, t.G
+            tabs[i].log10P0, tabs[i].dlog10P, tabs[i].T0, tabs[i].dT = t.log10P0, t.dlog10P, t.T0, t.dT
+            tabs[i].kappa = k.data_ptr()
+        h = ctypes.c_void_p()
+        check(self.lib.helios_plan_create(ctx.h, ctypes.byref(b), tabs, len(tables), ctypes.byref(self.params),
+                                          ctypes.byref(h)))
+        self.h = h
+        info = _lib.PlanInfo()
+        check(self.lib.helios_plan_info(h, ctypes.byref(info)))
+        self.info = info
+        self.G = tables[0].G
+        self.lay_off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.if_off = np.concatenate([[0], np.cumsum(self.n + 1)]).astype(np.int64)
+        self.pt_off = np.concatenate([[0], np.cumsum(2 * self.n + 1)]).astype(np.int64)
+        self.bin_off = np.concatenate([[0], np.cumsum(self.L)]).astype(np.int64)
+        self.dev = torch.device("cuda", ctx.device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.helios_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- helpers
+    def _empty(self, n, dtype):
+        return _torch().empty(int(n), dtype=dtype, device=self.dev)
+
+    def _check_T(self, T):
+        torch = _torch()
+        if not (T.is_cuda and T.dtype == torch.float64 and T.is_contiguous() and T.numel() == self.info.layers):
+            raise ValueError(f"T_layer must be a contiguous float64 CUDA tensor of {self.info.layers} values")
+
+    # ---- the four calls of the hot path
+    def interp_opacity(self, T, want_kappa=True, stream=None):
+        torch = _torch()
+        self._check_T(T)
+        nk = int(sum((2 * n + 1) * L for n, L in zip(self.n, self.L)) * self.G)
+        kap = self._empty(nk, torch.float32) if want_kappa else None
+        idx = self._empty(2 * self.info.points, torch.int32)
+        w = self._empty(2 * self.info.points, torch.float64)
+        check(self.lib.helios_interp_opacity(self.h, T.data_ptr(), _ptr(kap), idx.data_ptr(), w.data_ptr(),
+                                             _stream_ptr(stream)))
+        return kap, idx.view(-1, 2), w.view(-1, 2)
+
+    def flux_sweep(self, T, n_passes=0, warm=False, want_toa=True, out=None, stream=None):
+        torch = _torch()
+        self._check_T(T)
+        if out is None:
+            out = (self._empty(self.info.interfaces, torch.float64), self._empty(self.info.interfaces, torch.float64),
+                   self._empty(self.info.bins, torch.float32) if want_toa else None)
+        Fu, Fd, toa = out
+        check(self.lib.helios_flux_sweep(self.h, T.data_ptr(), int(n_passes), 1 if warm else 0, Fu.data_ptr(),
+                                         Fd.data_ptr(), _ptr(toa), _stream_ptr(stream)))
+        return Fu, Fd, toa
+
+    def new_state(self):
+        torch = _torch()
+        L = int(self.info.layers)
+        return {"mult": torch.ones(L, dtype=torch.float64, device=self.dev),
+                "hist": torch.zeros(L, dtype=torch.uint8, device=self.dev),
+                "nhist": torch.zeros(L, dtype=torch.uint8, device=self.dev),
+                "status": torch.zeros(self.A, dtype=torch.int32, device=self.dev),
+                "iters": torch.zeros(self.A, dtype=torch.int32, device=self.dev),
+                "metric": torch.zeros(self.A, dtype=torch.float64, device=self.dev)}
+
+    def temp_update(self, Fup, Fdn, T, state, stream=None):
+        self._check_T(T)
+        s = state
+        check(self.lib.helios_temp_update(self.h, Fup.data_ptr(), Fdn.data_ptr(), T.data_ptr(), s["mult"].data_ptr(),
+                                          s["hist"].data_ptr(), s["nhist"].data_ptr(), s["status"].data_ptr(),
+                                          _ptr(s.get("iters")), _ptr(s.get("metric")), _stream_ptr(stream)))
+        return state
+
+    def solve_re(self, T, stream=None, raise_on_noconv=False):
+        """Iterate to radiative equilibrium in place; returns (iters, status) CUDA tensors."""
+        torch = _torch()
+        self._check_T(T)
+        iters = self._empty(self.A, torch.int32)
+        status = self._empty(self.A, torch.int32)
+        rc = self.lib.helios_solve_re(self.h, T.data_ptr(), iters.data_ptr(), status.data_ptr(), _stream_ptr(stream))
+        if rc != _lib.HELIOS_OK and (raise_on_noconv or rc != _lib.HELIOS_ENOCONV):
+            check(rc)
+        return iters, status
+
+    # ---- packing helpers
+    def split_layers(self, x):
+        return [x[self.lay_off[a]:self.lay_off[a + 1]] for a in range(self.A)]
+
+    def split_interfaces(self, x):
+        return [x[self.if_off[a]:self.if_off[a + 1]] for a in range(self.A)]
+
+    def split_bins(self, x):
+        return [x[self.bin_off[a]:self.bin_off[a + 1]] for a in range(self.A)]

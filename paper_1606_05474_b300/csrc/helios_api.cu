@@ -1,0 +1,666 @@
+// C ABI of the radiative-equilibrium hot path: validation, plan set-up (static
+// geometry and per-bin constants in double precision on the host), kernel
+// launches and the CUDA-graph radiative-equilibrium loop.  See include/helios.h.
+#include "helios.h"
+#include "helios_kernels.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace helios_dev;
+
+namespace {
+
+// CODATA 2018, CGS
+constexpr double kB = 1.380649e-16;
+constexpr double hP = 6.62607015e-27;
+constexpr double cL = 2.99792458e10;
+constexpr double sigmaSB = 5.670374419e-5;
+constexpr double kPi = 3.14159265358979323846;
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(HELIOS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kMaxG = 20;           // 32 G threads per block <= 640
+constexpr int kMaxM = 15;           // 2n+1 <= 32*15  ->  n <= 239
+constexpr int kMaxN = (32 * kMaxM - 1) / 2;
+
+int lane_chunk(int n)
+{
+    int m = (2 * n + 1 + 31) / 32;
+    if (!(m & 1)) ++m;
+    return m;
+}
+
+// IEEE double table coordinate, same formula as the device code (no contraction:
+// this file is compiled with -ffp-contract=off for the host).
+void host_table_coord(double x, double x0, double dx, int nx, int& i, double& w)
+{
+    if (nx < 2) { i = 0; w = 0.0; return; }
+    double u = (x - x0) / dx;
+    if (!(u > 0.0)) i = 0;
+    else if (u >= (double)(nx - 2)) i = nx - 2;
+    else i = (int)std::floor(u);
+    double t = (x - (x0 + (double)i * dx)) / dx;
+    if (!(t > 0.0)) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    w = t;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] (eqs. 31-32): Newton iteration on P_G in long
+// double from Tricomi's initial approximation, w = 2 / ((1 - y^2) P_G'(y)^2).
+void gauss_legendre(int G, std::vector<double>& y, std::vector<double>& w)
+{
+    y.assign(G, 0.0);
+    w.assign(G, 0.0);
+    if (G == 1) { w[0] = 2.0; return; }
+    for (int k = 1; k <= G; ++k) {
+        long double th = kPi * (4.0L * k - 1.0L) / (4.0L * G + 2.0L);
+        long double x = (1.0L - (G - 1.0L) / (8.0L * G * G * G)) * cosl(th);
+        long double dP = 1.0L;
+        for (int it = 0; it < 60; ++it) {
+            long double pm = 1.0L, pc = x;
+            for (int j = 2; j <= G; ++j) {
+                long double pn = ((2.0L * j - 1.0L) * x * pc - (j - 1.0L) * pm) / j;
+                pm = pc;
+                pc = pn;
+            }
+            dP = G * (pm - x * pc) / (1.0L - x * x);
+            long double dx = pc / dP;
+            x -= dx;
+            if (fabsl(dx) < 1e-19L) break;
+        }
+        y[G - k] = (double)x;
+        w[G - k] = (double)(2.0L / ((1.0L - x * x) * dP * dP));
+    }
+}
+
+// Planck intensity of a wavenumber bin at its centre, times the bin width (per steradian).
+double planck_bin(double nu_lo, double nu_hi, double T)
+{
+    if (!(T > 0.0)) return 0.0;
+    const double nu = 0.5 * (nu_lo + nu_hi), dnu = nu_hi - nu_lo;
+    return 2.0 * hP * cL * cL * nu * nu * nu * dnu / std::expm1(hP * cL * nu / (kB * T));
+}
+
+template <typename T>
+int dev_alloc(T** p, size_t count, size_t& total)
+{
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(HELIOS_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    total += bytes;
+    return HELIOS_OK;
+}
+
+template <typename T>
+int upload(T* dst, const std::vector<T>& src)
+{
+    if (src.empty()) return HELIOS_OK;
+    CUDA_TRY(cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HELIOS_OK;
+}
+
+size_t sweep_smem(int M, int G)
+{
+    const size_t W = 32 * (size_t)M, KST = W + 1;
+    return 3 * (W / 2) * sizeof(double) + (G * KST + 5 * W + 1) * sizeof(float);
+}
+
+}  // namespace
+
+struct helios_ctx {
+    int device;
+    cudaStream_t stream;
+    cudaEvent_t ev_in, ev_out;
+    int* h_active;    // pinned
+};
+
+struct MGroup {
+    int M;
+    int count;
+    int* order;       // device
+};
+
+struct helios_plan {
+    helios_ctx* ctx;
+    helios_params_t prm;
+    int A, G, TB, passes;
+    int64_t layers, interfaces, points, subs, bins, items, cells;
+    int64_t ws_bytes;
+    std::vector<AtmDesc> atms_h;
+    std::vector<MGroup> groups;
+    PlanDev dev;
+    std::vector<void*> allocs;
+    // solve state
+    double *Fup, *Fdn, *mult;
+    uint8_t *hist, *nhist;
+    int* n_active;
+    bool warm_ready;
+    cudaGraphExec_t graph;
+    const void* graph_key[3];
+    int graph_chunk;
+};
+
+extern "C" {
+
+void helios_default_params(helios_params_t* p)
+{
+    if (!p) return;
+    p->D = 2.0;
+    p->dtau_iso = 1e-4;
+    p->w0_pure = 1e-6;
+    p->tol = 1e-7;
+    p->fpre_num = 1e5;
+    p->fpre_exp = 0.9;
+    p->osc_down = 0.67;
+    p->osc_up = 1.1;
+    p->mult_max = 1e4;
+    p->T_floor = 1.0;
+    p->n_scat = 4;
+    p->max_iter = 20000;
+    p->grey_mode = 0;
+    p->printed_gradient = 0;
+    p->bins_per_item = 0;
+    p->check_every = 0;
+}
+
+int helios_version(void) { return HELIOS_VERSION; }
+
+const char* helios_last_error(void) { return g_err.c_str(); }
+
+int helios_create(helios_ctx** out, int device)
+{
+    if (!out) return fail(HELIOS_EINVAL, "helios_create: null output pointer");
+    *out = nullptr;
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(HELIOS_EINVAL, "helios_create: device %d of %d", device, ndev);
+    CUDA_TRY(cudaSetDevice(device));
+    helios_ctx* c = new helios_ctx();
+    c->device = device;
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    CUDA_TRY(cudaMallocHost((void**)&c->h_active, sizeof(int)));
+    *out = c;
+    return HELIOS_OK;
+}
+
+int helios_destroy(helios_ctx* c)
+{
+    if (!c) return HELIOS_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+    cudaEventDestroy(c->ev_in);
+    cudaEventDestroy(c->ev_out);
+    cudaFreeHost(c->h_active);
+    delete c;
+    return HELIOS_OK;
+}
+
+int helios_plan_destroy(helios_plan* p)
+{
+    if (!p) return HELIOS_OK;
+    cudaSetDevice(p->ctx->device);
+    cudaDeviceSynchronize();
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (void* a : p->allocs) cudaFree(a);
+    delete p;
+    return HELIOS_OK;
+}
+
+int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_ktable_t* tabs, int ntab,
+                       const helios_params_t* prm, helios_plan** out)
+{
+    if (!out) return fail(HELIOS_EINVAL, "helios_plan_create: null output pointer");
+    *out = nullptr;
+    if (!ctx || !b || !tabs || !prm) return fail(HELIOS_EINVAL, "helios_plan_create: null argument");
+    if (b->A < 1) return fail(HELIOS_EINVAL, "batch has %d atmospheres", b->A);
+    if (ntab < 1) return fail(HELIOS_EINVAL, "no k-table given");
+    if (!b->n_layers || !b->n_bins || !b->table_id || !b->P_top_bar || !b->P_bot_bar || !b->grav || !b->T_irr ||
+        !b->T_int || !b->T_star || !b->nu_edges || !b->omega0 || !b->g0)
+        return fail(HELIOS_EINVAL, "batch has a null array");
+    if (!(prm->D > 0.0) || !(prm->dtau_iso >= 0.0) || !(prm->w0_pure >= 0.0) || !(prm->tol > 0.0) ||
+        prm->n_scat < 0 || prm->max_iter < 1 || !(prm->osc_down > 0.0) || !(prm->osc_up > 0.0) ||
+        !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0)
+        return fail(HELIOS_EINVAL, "invalid parameter set");
+    const int G = tabs[0].G;
+    if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
+    for (int t = 0; t < ntab; ++t) {
+        const helios_ktable_t& k = tabs[t];
+        if (k.G != G) return fail(HELIOS_EINVAL, "table %d has G = %d, table 0 has %d", t, k.G, G);
+        if (k.nP < 1 || k.nT < 1 || k.L < 1) return fail(HELIOS_EINVAL, "table %d has an empty axis", t);
+        if ((k.nP > 1 && !(k.dlog10P > 0.0)) || (k.nT > 1 && !(k.dT > 0.0)))
+            return fail(HELIOS_EINVAL, "table %d has a non-increasing axis", t);
+        if (!k.kappa || ((uintptr_t)k.kappa & 15)) return fail(HELIOS_EINVAL, "table %d: kappa null or not 16-byte aligned", t);
+    }
+    if (prm->grey_mode) {
+        for (int a = 0; a < b->A; ++a)
+            if (b->n_bins[a] != 2) return fail(HELIOS_EINVAL, "grey mode needs exactly 2 bins (atmosphere %d)", a);
+    }
+    CUDA_TRY(cudaSetDevice(ctx->device));
+
+    helios_plan* P = new helios_plan();
+    P->ctx = ctx;
+    P->prm = *prm;
+    P->A = b->A;
+    P->G = G;
+    P->graph = nullptr;
+    P->warm_ready = false;
+
+    // ---- per-atmosphere layout
+    const int A = b->A;
+    std::vector<AtmDesc> ad(A);
+    int64_t lay = 0, ifc = 0, pts = 0, sub = 0, bins = 0, nu_off = 0;
+    for (int a = 0; a < A; ++a) {
+        const int n = b->n_layers[a], L = b->n_bins[a], t = b->table_id[a];
+        if (n < 2 || n > kMaxN) { delete P; return fail(HELIOS_EINVAL, "atmosphere %d: n_layers = %d outside [2, %d]", a, n, kMaxN); }
+        if (L < 1) { delete P; return fail(HELIOS_EINVAL, "atmosphere %d: n_bins = %d", a, L); }
+        if (t < 0 || t >= ntab) { delete P; return fail(HELIOS_EINVAL, "atmosphere %d: table_id %d", a, t); }
+        if (L > tabs[t].L) { delete P; return fail(HELIOS_EINVAL, "atmosphere %d: %d bins > table %d's %d", a, L, t, tabs[t].L); }
+        if (!(b->P_top_bar[a] > 0.0) || !(b->P_bot_bar[a] > b->P_top_bar[a]) || !(b->grav[a] > 0.0) ||
+            !(b->T_irr[a] >= 0.0) || !(b->T_int[a] >= 0.0) || !(b->T_star[a] > 0.0) ||
+            !std::isfinite(b->P_bot_bar[a]) || !std::isfinite(b->T_irr[a]) || !std::isfinite(b->T_int[a])) {
+            delete P;
+            return fail(HELIOS_EINVAL, "atmosphere %d: invalid pressure range, gravity or temperatures", a);
+        }
+        for (int l = 0; l <= L; ++l) {
+            const double v = b->nu_edges[nu_off + l];
+            if (!(v > 0.0) || !std::isfinite(v) || (l > 0 && !(v > b->nu_edges[nu_off + l - 1]))) {
+                delete P;
+                return fail(HELIOS_EINVAL, "atmosphere %d: bin edges must be positive and increasing", a);
+            }
+        }
+        for (int l = 0; l < L; ++l) {
+            const float w0 = b->omega0[bins + l], g0 = b->g0[bins + l];
+            if (!(w0 >= 0.0f && w0 <= 1.0f) || !(g0 >= -1.0f && g0 <= 1.0f) ||
+                (!(1.0 - (double)w0 < prm->w0_pure) && !(w0 < 1.0f))) {
+                delete P;
+                return fail(HELIOS_EINVAL, "atmosphere %d bin %d: omega0 %g / g0 %g invalid", a, l, w0, g0);
+            }
+        }
+        AtmDesc& d = ad[a];
+        std::memset(&d, 0, sizeof d);
+        d.n = n; d.L = L; d.M = lane_chunk(n); d.tab = t;
+        d.lay_off = (int)lay; d.if_off = (int)ifc; d.pt_off = (int)pts; d.sub_off = (int)sub; d.bin_off = (int)bins;
+        lay += n; ifc += n + 1; pts += 2 * n + 1; sub += 2 * n; bins += L; nu_off += L + 1;
+    }
+    if (pts > INT32_MAX / 2 || bins > INT32_MAX / 2) { delete P; return fail(HELIOS_EINVAL, "batch too large"); }
+    P->layers = lay; P->interfaces = ifc; P->points = pts; P->subs = sub; P->bins = bins;
+    int64_t cells = 0;
+    for (int a = 0; a < A; ++a) cells += (int64_t)ad[a].n * ad[a].L * G;
+    P->cells = cells;
+
+    // ---- work items: tiles of TB bins
+    int TB = prm->bins_per_item;
+    if (TB <= 0) TB = (int)std::max<int64_t>(1, std::min<int64_t>(16, bins / (148 * 8)));
+    P->TB = TB;
+    std::vector<int2> items;
+    int64_t part = 0, warm = 0;
+    for (int a = 0; a < A; ++a) {
+        AtmDesc& d = ad[a];
+        d.n_items = (d.L + TB - 1) / TB;
+        d.item_off = (int)items.size();
+        for (int t = 0; t < d.n_items; ++t) items.push_back(make_int2(a, t));
+        d.part_off = part;
+        part += (int64_t)d.n_items * 3 * (d.n + 1);
+        d.warm_off = warm;
+        warm += (int64_t)d.L * G * 32 * d.M;
+    }
+    P->items = (int64_t)items.size();
+    // launch order per lane-chunk size M, most expensive items first
+    std::vector<std::vector<int>> byM(kMaxM + 1);
+    for (int i = 0; i < (int)items.size(); ++i) byM[ad[items[i].x].M].push_back(i);
+    for (int M = 1; M <= kMaxM; M += 2) {
+        auto& v = byM[M];
+        std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+            const AtmDesc& a = ad[items[x].x];
+            const AtmDesc& c = ad[items[y].x];
+            int ca = a.n * std::min(TB, a.L - items[x].y * TB), cb = c.n * std::min(TB, c.L - items[y].y * TB);
+            return ca > cb;
+        });
+    }
+
+    // ---- static geometry (Sect. 2.2.1, eq. 19) and pressure-table coordinates
+    std::vector<int> iP(pts);
+    std::vector<double> wP(pts), lnr(lay);
+    std::vector<float> dm(sub);
+    for (int a = 0; a < A; ++a) {
+        const AtmDesc& d = ad[a];
+        const helios_ktable_t& k = tabs[d.tab];
+        const int n = d.n;
+        const double lb = std::log10(b->P_bot_bar[a]), lt = std::log10(b->P_top_bar[a]);
+        const double h = (lb - lt) / (double)(n - 1);
+        std::vector<double> Pp(2 * n + 1);
+        for (int p = 0; p <= 2 * n; ++p) {
+            const double lp = (lb + 0.5 * h) - (0.5 * h) * (double)p;
+            Pp[p] = 1e6 * std::pow(10.0, lp);
+            host_table_coord(lp, k.log10P0, k.dlog10P, k.nP, iP[d.pt_off + p], wP[d.pt_off + p]);
+        }
+        for (int s = 0; s < 2 * n; ++s) dm[d.sub_off + s] = (float)((Pp[s] - Pp[s + 1]) / b->grav[a]);
+        for (int i = 0; i < n; ++i) lnr[d.lay_off + i] = std::log(Pp[2 * i] / Pp[2 * i + 2]);
+    }
+
+    // ---- per-bin constants (eqs. 8, 12-14, 20-22), double precision then rounded
+    const double D = prm->D, eps = 1.0 / D;
+    std::vector<BinConst> bc(bins);
+    bool any_scat = false;
+    nu_off = 0;
+    for (int a = 0; a < A; ++a) {
+        const AtmDesc& d = ad[a];
+        const double* e = b->nu_edges + nu_off;
+        double s_star = 0.0, s_int = 0.0;
+        for (int l = 0; l < d.L; ++l) {
+            s_star += planck_bin(e[l], e[l + 1], b->T_star[a]);
+            s_int += planck_bin(e[l], e[l + 1], b->T_int[a]);
+        }
+        const double Firr = sigmaSB * std::pow(b->T_irr[a], 4), Fint = sigmaSB * std::pow(b->T_int[a], 4);
+        for (int l = 0; l < d.L; ++l) {
+            BinConst& c = bc[d.bin_off + l];
+            std::memset(&c, 0, sizeof c);
+            const double nu = 0.5 * (e[l] + e[l + 1]), dnu = e[l + 1] - e[l];
+            c.xs = (float)(hP * cL * nu / kB);
+            c.E = (float)(2.0 * kPi * eps * 2.0 * hP * cL * cL * nu * nu * nu * dnu);
+            double toa = (s_star > 0.0 && Firr > 0.0) ? Firr * planck_bin(e[l], e[l + 1], b->T_star[a]) / s_star : 0.0;
+            double bint = (s_int > 0.0 && Fint > 0.0) ? Fint * planck_bin(e[l], e[l + 1], b->T_int[a]) / s_int : 0.0;
+            if (prm->grey_mode) {
+                if (l == 0) { c.flags |= BIN_GREY_DARK; toa = Firr; bint = 0.0; }
+                else { c.flags |= BIN_GREY_THERM; c.E = (float)(eps * sigmaSB); toa = 0.0; bint = Fint; }
+            }
+            c.toa = (float)toa;
+            c.bint = (float)bint;
+            const double w0 = b->omega0[d.bin_off + l], g0 = b->g0[d.bin_off + l];
+            if (w0 != 0.0) any_scat = true;
+            if (1.0 - w0 < prm->w0_pure) c.flags |= BIN_PURE_SCAT;
+            if (w0 == 0.0) c.flags |= BIN_NO_SCAT;
+            const double one_wg = 1.0 - w0 * g0;
+            c.lam = (float)(D * std::sqrt(one_wg * (1.0 - w0)));
+            const double kk = one_wg > 0.0 ? std::sqrt((1.0 - w0) / one_wg) : 0.0;
+            const double q = (1.0 - kk) / (1.0 + kk);
+            c.q = (float)q;
+            c.q2 = (float)(q * q);
+            c.omq2 = (float)(1.0 - q * q);
+            c.cg = (float)(eps / (prm->printed_gradient ? (1.0 + w0 * g0) : one_wg));
+            c.gam = (float)(D * (1.0 - g0) / 2.0);
+        }
+        nu_off += d.L + 1;
+    }
+    P->passes = any_scat ? 1 + prm->n_scat : 1;
+
+    // ---- Gauss weights on [0, 1]
+    std::vector<double> gy, gwd;
+    gauss_legendre(G, gy, gwd);
+    std::vector<float> gw(G);
+    for (int g = 0; g < G; ++g) gw[g] = (float)(0.5 * gwd[g]);
+
+    std::vector<TabDesc> td(ntab);
+    for (int t = 0; t < ntab; ++t) {
+        td[t].kappa = tabs[t].kappa;
+        td[t].nP = tabs[t].nP; td[t].nT = tabs[t].nT; td[t].L = tabs[t].L; td[t].G = tabs[t].G;
+        td[t].log10P0 = tabs[t].log10P0; td[t].dlog10P = tabs[t].dlog10P;
+        td[t].T0 = tabs[t].T0; td[t].dT = tabs[t].dT;
+    }
+
+    // ---- device workspace
+    size_t tot = 0;
+    int rc = HELIOS_OK;
+    PlanDev& dv = P->dev;
+    std::memset(&dv, 0, sizeof dv);
+    AtmDesc* d_atm; TabDesc* d_tab; BinConst* d_bc; int2* d_items; int* d_order; float* d_gw;
+    int* d_iP; double* d_wP; float* d_dm; double* d_lnr;
+#define ALLOC(ptr, cnt)                                              \
+    do {                                                             \
+        if ((rc = dev_alloc(&ptr, (cnt), tot)) != HELIOS_OK) {       \
+            helios_plan_destroy(P);                                  \
+            return rc;                                               \
+        }                                                            \
+        P->allocs.push_back((void*)ptr);                             \
+    } while (0)
+    ALLOC(d_atm, A); ALLOC(d_tab, ntab); ALLOC(d_bc, bins); ALLOC(d_items, items.size());
+    ALLOC(d_order, items.size()); ALLOC(d_gw, G); ALLOC(d_iP, pts); ALLOC(d_wP, pts); ALLOC(d_dm, sub);
+    ALLOC(d_lnr, lay);
+    ALLOC(dv.Tpt, pts); ALLOC(dv.iT, pts); ALLOC(dv.wT, pts); ALLOC(dv.invT, pts); ALLOC(dv.Tf, pts);
+    ALLOC(dv.invT_old, pts); ALLOC(dv.dinv_step, pts); ALLOC(dv.dT_step, pts);
+    ALLOC(dv.dinv_sub, sub); ALLOC(dv.dT_sub, sub);
+    ALLOC(dv.part, part); ALLOC(dv.warm, warm);
+    ALLOC(P->Fup, ifc); ALLOC(P->Fdn, ifc); ALLOC(P->mult, lay); ALLOC(P->hist, lay); ALLOC(P->nhist, lay);
+    ALLOC(P->n_active, 1);
+#undef ALLOC
+    std::vector<int> order;
+    for (int M = 1; M <= kMaxM; M += 2) {
+        if (byM[M].empty()) continue;
+        MGroup gr;
+        gr.M = M;
+        gr.count = (int)byM[M].size();
+        gr.order = d_order + order.size();
+        order.insert(order.end(), byM[M].begin(), byM[M].end());
+        P->groups.push_back(gr);
+    }
+    if ((rc = upload(d_atm, ad)) || (rc = upload(d_tab, td)) || (rc = upload(d_bc, bc)) ||
+        (rc = upload(d_items, items)) || (rc = upload(d_order, order)) || (rc = upload(d_gw, gw)) ||
+        (rc = upload(d_iP, iP)) || (rc = upload(d_wP, wP)) || (rc = upload(d_dm, dm)) || (rc = upload(d_lnr, lnr))) {
+        helios_plan_destroy(P);
+        return rc;
+    }
+    cudaError_t ce = cudaMemset(dv.warm, 0, std::max<int64_t>(warm, 1) * sizeof(float));
+    if (ce != cudaSuccess) { helios_plan_destroy(P); return fail(HELIOS_ECUDA, "cudaMemset: %s", cudaGetErrorString(ce)); }
+    dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.order = d_order; dv.gw = d_gw;
+    dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr;
+    dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso;
+    P->atms_h = ad;
+    P->ws_bytes = (int64_t)tot;
+    *out = P;
+    return HELIOS_OK;
+}
+
+int helios_plan_info(const helios_plan* p, helios_plan_info_t* info)
+{
+    if (!p || !info) return fail(HELIOS_EINVAL, "helios_plan_info: null argument");
+    info->layers = p->layers; info->interfaces = p->interfaces; info->points = p->points;
+    info->bins = p->bins; info->cells = p->cells; info->passes = p->passes;
+    info->workspace_bytes = p->ws_bytes;
+    return HELIOS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+namespace {
+
+template <int M>
+int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
+                   float* Fup_toa, cudaStream_t s)
+{
+    const size_t smem = sweep_smem(M, p->G);
+    static thread_local int configured_dev[kMaxM + 1] = {};
+    if (configured_dev[M] != p->ctx->device + 1) {
+        CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured_dev[M] = p->ctx->device + 1;
+    }
+    sweep_kernel<M><<<gr.count, 32 * p->G, smem, s>>>(p->dev, gr.order, gr.count, status, n_passes, warm_valid, Fup_toa);
+    CUDA_TRY(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, float* Fup_toa, cudaStream_t s)
+{
+    for (const MGroup& gr : p->groups) {
+        int rc = HELIOS_OK;
+        switch (gr.M) {
+            case 1: rc = launch_sweep_M<1>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 3: rc = launch_sweep_M<3>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 5: rc = launch_sweep_M<5>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 7: rc = launch_sweep_M<7>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 9: rc = launch_sweep_M<9>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 11: rc = launch_sweep_M<11>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 13: rc = launch_sweep_M<13>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 15: rc = launch_sweep_M<15>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            default: rc = fail(HELIOS_EINVAL, "unsupported lane chunk %d", gr.M);
+        }
+        if (rc) return rc;
+    }
+    return HELIOS_OK;
+}
+
+int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes, int warm_valid, double* Fup,
+                double* Fdn, float* Fup_toa, cudaStream_t s)
+{
+    prep_kernel<<<p->A, 256, 0, s>>>(p->dev, T, status, warm_valid);
+    CUDA_TRY(cudaGetLastError());
+    int rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
+    if (rc) return rc;
+    finalize_kernel<<<p->A, 128, 0, s>>>(p->dev, status, Fup, Fdn);
+    CUDA_TRY(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+TempArgs temp_args(const helios_plan* p)
+{
+    TempArgs t;
+    t.sigma = sigmaSB; t.tol = p->prm.tol; t.fpre_num = p->prm.fpre_num; t.fpre_exp = p->prm.fpre_exp;
+    t.osc_down = p->prm.osc_down; t.osc_up = p->prm.osc_up; t.mult_max = p->prm.mult_max;
+    t.T_floor = p->prm.T_floor; t.max_iter = p->prm.max_iter;
+    return t;
+}
+
+}  // namespace
+
+extern "C" {
+
+int helios_interp_opacity(helios_plan* p, const double* T_layer, float* kappa_pts, int32_t* idx_pts, double* w_pts,
+                          cudaStream_t s)
+{
+    if (!p || !T_layer) return fail(HELIOS_EINVAL, "helios_interp_opacity: null argument");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    long long off = 0;
+    for (int a = 0; a < p->A; ++a) {
+        const AtmDesc& d = p->atms_h[a];
+        const long long total = (long long)(2 * d.n + 1) * d.L * p->G;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 148 * 16);
+        interp_kernel<<<blocks, 256, 0, s>>>(p->dev, T_layer, a, kappa_pts, off, idx_pts, w_pts);
+        CUDA_TRY(cudaGetLastError());
+        off += total;
+    }
+    return HELIOS_OK;
+}
+
+int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int warm, double* Fup_bol,
+                      double* Fdn_bol, float* Fup_toa, cudaStream_t s)
+{
+    if (!p || !T_layer || !Fup_bol || !Fdn_bol) return fail(HELIOS_EINVAL, "helios_flux_sweep: null argument");
+    if (n_passes < 0) return fail(HELIOS_EINVAL, "helios_flux_sweep: n_passes = %d", n_passes);
+    if (n_passes == 0) n_passes = p->passes;
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    const int warm_valid = (warm && p->warm_ready) ? 1 : 0;
+    int rc = launch_eval(p, T_layer, nullptr, n_passes, warm_valid, Fup_bol, Fdn_bol, Fup_toa, s);
+    if (rc) return rc;
+    p->warm_ready = true;
+    return HELIOS_OK;
+}
+
+int helios_temp_update(helios_plan* p, const double* Fup_bol, const double* Fdn_bol, double* T_layer, double* mult,
+                       uint8_t* hist, uint8_t* nhist, int32_t* status, int32_t* iters, double* metric, cudaStream_t s)
+{
+    if (!p || !Fup_bol || !Fdn_bol || !T_layer || !mult || !hist || !nhist || !status)
+        return fail(HELIOS_EINVAL, "helios_temp_update: null argument");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    temp_kernel<<<p->A, 256, 0, s>>>(p->dev, temp_args(p), Fup_bol, Fdn_bol, T_layer, mult, hist, nhist, status, iters,
+                                     metric, nullptr);
+    CUDA_TRY(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t s)
+{
+    if (!p || !T_layer || !iters || !status) return fail(HELIOS_EINVAL, "helios_solve_re: null argument");
+    helios_ctx* c = p->ctx;
+    CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t w = c->stream;
+    CUDA_TRY(cudaEventRecord(c->ev_in, s));
+    CUDA_TRY(cudaStreamWaitEvent(w, c->ev_in, 0));
+    // fresh iteration state
+    std::vector<double> ones(p->layers, 1.0);
+    CUDA_TRY(cudaMemcpyAsync(p->mult, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice, w));
+    CUDA_TRY(cudaMemsetAsync(p->hist, 0, p->layers, w));
+    CUDA_TRY(cudaMemsetAsync(p->nhist, 0, p->layers, w));
+    CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t) * p->A, w));
+    CUDA_TRY(cudaMemsetAsync(iters, 0, sizeof(int32_t) * p->A, w));
+    const int A = p->A;
+    CUDA_TRY(cudaMemcpyAsync(p->n_active, &A, sizeof(int), cudaMemcpyHostToDevice, w));
+    const TempArgs ta = temp_args(p);
+    // first temperature step: the coupled stream starts from zero
+    int rc = launch_eval(p, T_layer, status, p->passes, 0, p->Fup, p->Fdn, nullptr, w);
+    if (rc) return rc;
+    temp_kernel<<<A, 256, 0, w>>>(p->dev, ta, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters,
+                                  nullptr, p->n_active);
+    CUDA_TRY(cudaGetLastError());
+    // later steps start from the previous step's fluxes; captured as a graph of `chunk` steps
+    const int chunk = p->prm.check_every > 0 ? p->prm.check_every : 16;
+    const void* key[3] = {T_layer, iters, status};
+    if (!p->graph || p->graph_chunk != chunk || std::memcmp(key, p->graph_key, sizeof key) != 0) {
+        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        cudaGraph_t g;
+        CUDA_TRY(cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < chunk && rc == HELIOS_OK; ++i) {
+            rc = launch_eval(p, T_layer, status, p->passes, 1, p->Fup, p->Fdn, nullptr, w);
+            if (rc == HELIOS_OK) {
+                temp_kernel<<<A, 256, 0, w>>>(p->dev, ta, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status,
+                                              iters, nullptr, p->n_active);
+            }
+        }
+        cudaError_t ec = cudaStreamEndCapture(w, &g);
+        if (rc) { if (ec == cudaSuccess) cudaGraphDestroy(g); return rc; }
+        if (ec != cudaSuccess) return fail(HELIOS_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+        cudaError_t ei = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) { p->graph = nullptr; return fail(HELIOS_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei)); }
+        std::memcpy(p->graph_key, key, sizeof key);
+        p->graph_chunk = chunk;
+    }
+    int done = 1;   // the kernel itself retires atmospheres at max_iter; this bound is only a backstop
+    while (done < p->prm.max_iter + chunk) {
+        CUDA_TRY(cudaGraphLaunch(p->graph, w));
+        done += chunk;
+        CUDA_TRY(cudaMemcpyAsync(c->h_active, p->n_active, sizeof(int), cudaMemcpyDeviceToHost, w));
+        CUDA_TRY(cudaStreamSynchronize(w));
+        if (*c->h_active <= 0) break;
+    }
+    p->warm_ready = true;
+    CUDA_TRY(cudaEventRecord(c->ev_out, w));
+    CUDA_TRY(cudaStreamWaitEvent(s, c->ev_out, 0));
+    std::vector<int32_t> st(A);
+    CUDA_TRY(cudaMemcpyAsync(st.data(), status, sizeof(int32_t) * A, cudaMemcpyDeviceToHost, w));
+    CUDA_TRY(cudaStreamSynchronize(w));
+    for (int a = 0; a < A; ++a)
+        if (st[a] != HELIOS_ATM_CONVERGED)
+            return fail(HELIOS_ENOCONV, "atmosphere %d ended with status %d", a, st[a]);
+    return HELIOS_OK;
+}
+
+}  // extern "C"

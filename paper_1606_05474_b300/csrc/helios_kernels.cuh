@@ -1,0 +1,575 @@
+// Device kernels of the radiative-equilibrium hot path (sm_103a).
+//
+// Layout of the work (one flux evaluation):
+//   prep_kernel      one block per atmosphere: point temperatures (Sect. 2.2.1),
+//                    temperature-table indices in IEEE double (Sect. 2.3) and the
+//                    float inputs of the Planck evaluations.
+//   sweep_kernel<M>  one block per work item = (atmosphere, tile of bins); one warp
+//                    per Gauss point g, so a block holds the G columns of one bin at
+//                    a time.  The 2n sublayers of a column are spread over the 32
+//                    lanes of its warp (M consecutive sublayers per lane), their
+//                    two-stream coefficients stay in registers for all K passes, and
+//                    each down or up sweep is a first-order linear recurrence solved
+//                    as a warp-wide affine scan (lane-local composition, 5 shuffle
+//                    levels, lane-local application).
+//   finalize_kernel  fixed-order FP64 sums of the per-item partials -> bolometric fluxes.
+//   temp_kernel      one block per atmosphere: FP64 temperature step and convergence.
+//
+// Fluxes are carried in the sweep as deviations from the local two-stream Planck
+// flux, G = F - 2 pi eps B_l(T_p).  With per-sublayer transmission Ts, reflection
+// Rs and source Ss the layer solutions of eqs. (11), (14) and (15) become
+//     G_top,up   = Ts G_bot,up + Rs G_top,dn + Ss
+//     G_bot,dn   = Ts G_top,dn + Rs G_bot,up - Ss
+// (an exact algebraic rewrite), so the net flux G_up - G_dn = F_up - F_dn never
+// forms the difference of two large float numbers, and every source term is a
+// product of the small Planck difference across the sublayer, computed with
+// expm1 from the temperature difference in double precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace helios_dev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// per-bin flags
+constexpr int BIN_PURE_SCAT = 1;    // 1 - omega0 < w0_pure: eq. (14)
+constexpr int BIN_NO_SCAT = 2;      // omega0 == 0: streams decouple, one pass is exact
+constexpr int BIN_GREY_DARK = 4;    // grey mode visible band: no emission
+constexpr int BIN_GREY_THERM = 8;   // grey mode thermal band: pi B = sigma T^4
+
+struct BinConst {
+    float xs;      // h c nu_c / k_B  (x = xs / T)
+    float E;       // 2 pi eps * 2 h c^2 nu_c^3 dnu  (2 pi eps B_l(T) = E / expm1(x))
+    float toa;     // downward flux entering at the TOA (eq. 20)
+    float bint;    // internal flux entering at the BOA (eq. 22)
+    float lam;     // D sqrt((1 - w0 g0)(1 - w0))  (eq. 8 exponent per unit dtau)
+    float q;       // zeta_- / zeta_+  (eq. 13)
+    float q2;      // q^2
+    float omq2;    // 1 - q^2
+    float cg;      // eps / (1 - w0 g0): gradient prefactor of eq. (15)
+    float gam;     // D (1 - g0) / 2: pure-scattering coupling, eq. (14)
+    int flags;
+    int pad;
+};
+
+struct AtmDesc {
+    int n, L, M, tab;
+    int lay_off, if_off, pt_off, sub_off;
+    int bin_off, item_off, n_items, pad;
+    long long warm_off;     // float offset of this atmosphere's warm-start block
+    long long part_off;     // double offset of this atmosphere's partial sums
+};
+
+struct TabDesc {
+    const float* kappa;
+    int nP, nT, L, G;
+    double log10P0, dlog10P, T0, dT;
+};
+
+struct PlanDev {
+    const AtmDesc* atms;
+    const TabDesc* tabs;
+    const BinConst* bins;
+    const int2* items;          // (atm, tile)
+    const int* order;           // launch order of items, per M group (indices into items)
+    const float* gw;            // Gauss weights on [0, 1], [G]
+    const int* iP;              // [points]
+    const double* wP;           // [points]
+    const float* dm;            // [sublayers]  column mass (g cm^-2)
+    const double* lnr;          // [layers]  ln(P_int,i / P_int,i+1)
+    // per-evaluation state written by prep_kernel
+    double* Tpt;                // [points] temperature at the point in the previous evaluation
+    int* iT;                    // [points]
+    double* wT;                 // [points]
+    float* invT;                // [points] 1/T
+    float* Tf;                  // [points] T (grey mode)
+    float* invT_old;            // [points] 1/T of the previous evaluation
+    float* dinv_step;           // [points] (T_old - T)/(T_old T)
+    float* dT_step;             // [points] T_old - T (grey mode)
+    float* dinv_sub;            // [sublayers] (T_a - T_b)/(T_a T_b), a below b
+    float* dT_sub;              // [sublayers] T_a - T_b (grey mode)
+    float* warm;                // warm-start G_up per column, lane-interleaved
+    double* part;               // per-item partial sums [3][n+1]
+    int G, TB, A;
+    float dtau_iso;
+};
+
+// ---------------------------------------------------------------------------
+// Table coordinate in IEEE double without contraction (Sect. 2.3 and footnote):
+// i = clamp(floor((x - x0)/dx), 0, nx-2), w = clamp((x - (x0 + i dx))/dx, 0, 1).
+__device__ __forceinline__ void table_coord(double x, double x0, double dx, int nx, int& i, double& w)
+{
+    if (nx < 2) { i = 0; w = 0.0; return; }
+    double u = __ddiv_rn(__dsub_rn(x, x0), dx);
+    if (!(u > 0.0)) i = 0;
+    else if (u >= (double)(nx - 2)) i = nx - 2;
+    else i = (int)floor(u);
+    double t = __ddiv_rn(__dsub_rn(x, __dadd_rn(x0, __dmul_rn((double)i, dx))), dx);
+    if (!(t > 0.0)) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    w = t;
+}
+
+// temperature at point p of an n-layer column (Sect. 2.2.1; outer interfaces take the
+// nearest centre)
+__device__ __forceinline__ double point_T(const double* T, int n, int p)
+{
+    if (p & 1) return T[p >> 1];
+    int i = p >> 1;
+    if (i == 0) return T[0];
+    if (i == n) return T[n - 1];
+    return __dmul_rn(0.5, __dadd_rn(T[i - 1], T[i]));
+}
+
+__device__ __forceinline__ float bilinear(const float* tab, const TabDesc& td, int iP, double wP, int iT, double wT,
+                                          int l, int g)
+{
+    const int iP1 = td.nP > 1 ? iP + 1 : iP;
+    const int iT1 = td.nT > 1 ? iT + 1 : iT;
+    const size_t rowL = (size_t)td.L * td.G;
+    const size_t o = (size_t)l * td.G + g;
+    float k00 = __ldg(tab + ((size_t)iP * td.nT + iT) * rowL + o);
+    float k10 = __ldg(tab + ((size_t)iP1 * td.nT + iT) * rowL + o);
+    float k01 = __ldg(tab + ((size_t)iP * td.nT + iT1) * rowL + o);
+    float k11 = __ldg(tab + ((size_t)iP1 * td.nT + iT1) * rowL + o);
+    float wp = (float)wP, wt = (float)wT;
+    float a = fmaf(wp, k10 - k00, k00);
+    float b = fmaf(wp, k11 - k01, k01);
+    return fmaf(wt, b - a, a);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const int* __restrict__ status,
+                            int warm_valid)
+{
+    const int a = blockIdx.x;
+    if (status && status[a] != 0) return;
+    const AtmDesc ad = P.atms[a];
+    const TabDesc td = P.tabs[ad.tab];
+    const double* T = T_layer + ad.lay_off;
+    const int n = ad.n, np = 2 * n + 1;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const int q = ad.pt_off + p;
+        double Tn = point_T(T, n, p);
+        int it;
+        double w;
+        table_coord(Tn, td.T0, td.dT, td.nT, it, w);
+        P.iT[q] = it;
+        P.wT[q] = w;
+        double To = warm_valid ? P.Tpt[q] : Tn;
+        P.invT[q] = (float)(1.0 / Tn);
+        P.Tf[q] = (float)Tn;
+        P.invT_old[q] = (float)(1.0 / To);
+        P.dinv_step[q] = (float)((To - Tn) / (To * Tn));
+        P.dT_step[q] = (float)(To - Tn);
+        P.Tpt[q] = Tn;
+    }
+    for (int s = threadIdx.x; s < 2 * n; s += blockDim.x) {
+        double Ta = point_T(T, n, s), Tb = point_T(T, n, s + 1);
+        P.dinv_sub[ad.sub_off + s] = (float)((Ta - Tb) / (Ta * Tb));
+        P.dT_sub[ad.sub_off + s] = (float)(Ta - Tb);
+    }
+}
+
+// Planck difference 2 pi eps (B(x_a) - B(x_b)) from B(x_b), 1 - e^{-x_a} and
+// y = x_b - x_a without cancellation: B_a - B_b = B_b expm1(y) / (1 - e^{-x_a}).
+__device__ __forceinline__ float planck_diff(float Bb, float em1n_a, float y, float Ba_direct)
+{
+    if (fabsf(y) < 1.0f) return Bb * expm1f(y) / em1n_a;
+    return Ba_direct - Bb;
+}
+
+// Two-stream coefficients of one sublayer in deviation form (see file header).
+// dB = 2 pi eps (B_bottom - B_top).
+__device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
+                                           float& Ts, float& Rs, float& Ss)
+{
+    if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source
+        float a = b.gam * dtau;
+        float t = 1.0f / (1.0f + a);
+        Ts = t;
+        Rs = a * t;
+        Ss = dB * t;
+        return;
+    }
+    const float x = b.lam * dtau;
+    const float u = -expm1f(-x);            // 1 - trans, eq. (8)
+    const float tr = (u < 0.5f) ? 1.0f - u : __expf(-x);
+    const bool iso = dtau < dtau_iso;       // Sect. 2.2.1: thin sublayers use eq. (11)
+    if (b.flags & BIN_NO_SCAT) {            // zeta_- = 0: Ts = trans, Rs = 0
+        Ts = tr;
+        Rs = 0.0f;
+        Ss = iso ? 0.5f * dB * (1.0f + tr) : b.cg * dB * __fdividef(u, dtau);
+        return;
+    }
+    // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha
+    const float t2u = u * (2.0f - u);                         // 1 - trans^2
+    const float d = 1.0f / fmaf(b.q2, t2u, b.omq2);           // 1 / (1 - q^2 trans^2)
+    Ts = b.omq2 * tr * d;
+    Rs = b.q * t2u * d;
+    const float g = d * u * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);   // 1 - Ts + Rs
+    Ss = iso ? 0.5f * dB * (2.0f - g) : b.cg * dB * __fdividef(g, dtau);
+}
+
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(640) sweep_kernel(PlanDev P, const int* __restrict__ order, int n_items,
+                                                    const int* __restrict__ status, int n_passes, int warm_valid,
+                                                    float* __restrict__ Fup_toa)
+{
+    constexpr int W = 32 * M;               // point slots per column
+    constexpr int KST = W + 1;              // row stride of the per-column smem rows
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = P.G;
+    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+    const int item = order[blockIdx.x];
+    const int2 it = P.items[item];
+    if (status && status[it.x] != 0) return;
+    const AtmDesc ad = P.atms[it.x];
+    const TabDesc td = P.tabs[ad.tab];
+    const int n = ad.n, NP = 2 * n + 1, NS = 2 * n;
+    const int l_begin = it.y * P.TB;
+    const int l_end = min(l_begin + P.TB, ad.L);
+
+    double* acc = reinterpret_cast<double*>(smem_raw);         // [3][n+1], n+1 <= W/2
+    float* kap = reinterpret_cast<float*>(acc + 3 * (W / 2));  // [G][KST]; later per-warp reduction rows
+    float* bt = kap + G * KST;                                 // [W] 2 pi eps B at points
+    float* em1n = bt + W;                                      // [W] 1 - e^{-x} at points
+    float* dbs = em1n + W;                                     // [W] warm-start shift B_old - B_new
+    float* dbt = dbs + W;                                      // [W] 2 pi eps (B_a - B_b) per sublayer
+    float* dm = dbt + W;                                       // [W] sublayer column mass
+    float* bc_toa = dm + W;                                    // [1] TOA value in deviation form
+
+    const int nthreads = blockDim.x;
+    for (int t = tid; t < W; t += nthreads) dm[t] = t < NS ? P.dm[ad.sub_off + t] : 0.0f;
+    for (int t = tid; t < 3 * (n + 1); t += nthreads) acc[t] = 0.0;
+    const float wg = P.gw[g];
+    const int p_first = tid / G, g_of = tid - p_first * G;     // gather mapping: consecutive g
+    const int p_stride = nthreads / G;
+    const float* tab = td.kappa;
+    float* wbase = P.warm + ad.warm_off;
+
+    for (int l = l_begin; l < l_end; ++l) {
+        const BinConst bc = P.bins[ad.bin_off + l];
+        // ---- phase 1a: per-point Planck values for this bin
+        for (int p = tid; p < W; p += nthreads) {
+            float B = 0.0f, e = 1.0f, sh = 0.0f;
+            if (p < NP) {
+                const int q = ad.pt_off + p;
+                if (bc.flags & BIN_GREY_THERM) {
+                    const float T = P.Tf[q], c = 2.0f * bc.E;       // E holds eps*sigma for grey bins
+                    const float T2 = T * T;
+                    B = c * T2 * T2;
+                    if (warm_valid) {
+                        const float dT = P.dT_step[q], To = T + dT;
+                        sh = c * dT * (To + T) * (To * To + T2);
+                    }
+                } else if (!(bc.flags & BIN_GREY_DARK)) {
+                    const float x = bc.xs * P.invT[q];
+                    B = x > 80.0f ? 0.0f : __fdividef(bc.E, expm1f(x));   // Wien tail below 1e-34 E
+                    e = -expm1f(-x);
+                    if (warm_valid) {
+                        const float y = bc.xs * P.dinv_step[q];
+                        const float xo = bc.xs * P.invT_old[q];
+                        const float Bo = xo > 80.0f ? 0.0f : __fdividef(bc.E, expm1f(xo));
+                        sh = (fabsf(y) < 1.0f) ? B * expm1f(y) / (-expm1f(-xo)) : Bo - B;
+                    }
+                }
+            }
+            bt[p] = B;
+            em1n[p] = e;
+            dbs[p] = sh;
+        }
+        __syncthreads();
+        // ---- phase 1b: per-sublayer Planck differences and the opacity gather
+        for (int s = tid; s < W; s += nthreads) {
+            float d = 0.0f;
+            if (s < NS) {
+                const int q = ad.sub_off + s;
+                if (bc.flags & BIN_GREY_THERM) {
+                    const float Ta = P.Tf[ad.pt_off + s], Tb = P.Tf[ad.pt_off + s + 1];
+                    d = 2.0f * bc.E * P.dT_sub[q] * (Ta + Tb) * (Ta * Ta + Tb * Tb);
+                } else if (!(bc.flags & BIN_GREY_DARK)) {
+                    const float y = bc.xs * P.dinv_sub[q];
+                    d = planck_diff(bt[s + 1], em1n[s], y, bt[s]);
+                }
+            }
+            dbt[s] = d;
+        }
+        if (tid == 0) bc_toa[0] = bc.toa - bt[NP - 1];
+        for (int p = p_first; p < NP; p += p_stride) {
+            const int q = ad.pt_off + p;
+            kap[g_of * KST + p] = bilinear(tab, td, P.iP[q], P.wP[q], P.iT[q], P.wT[q], l, g_of);
+        }
+        __syncthreads();
+
+        // ---- phase 2: one warp per Gauss point; lane holds sublayers lane*M .. lane*M+M-1
+        float Ts[M], Rs[M], Ss[M], X[M + 1];
+        float Ap = 1.0f;
+        const float* krow = kap + g * KST;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int s = lane * M + k;
+            float t = 1.0f, r = 0.0f, src = 0.0f;
+            if (s < NS) {
+                const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
+            }
+            Ts[k] = t;
+            Rs[k] = r;
+            Ss[k] = src;
+            Ap *= t;
+        }
+        // scan multipliers (depend on the transmissions only)
+        float adn[5], aup[5], adn_fin, aup_fin;
+        {
+            float a = Ap;
+#pragma unroll
+            for (int lv = 0; lv < 5; ++lv) {
+                const int d = 1 << lv;
+                const float ao = __shfl_down_sync(FULL, a, d);
+                const bool ok = lane + d < 32;
+                adn[lv] = ok ? a : 0.0f;
+                a = ok ? a * ao : a;
+            }
+            adn_fin = a;
+            a = Ap;
+#pragma unroll
+            for (int lv = 0; lv < 5; ++lv) {
+                const int d = 1 << lv;
+                const float ao = __shfl_up_sync(FULL, a, d);
+                const bool ok = lane >= d;
+                aup[lv] = ok ? a : 0.0f;
+                a = ok ? a * ao : a;
+            }
+            aup_fin = a;
+        }
+        // initial upward deviation: previous evaluation shifted to the new Planck values, or
+        // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero)
+        const long long col = (long long)(l * G + g) * W;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int p = lane * M + k;
+            X[k] = warm_valid ? wbase[col + k * 32 + lane] + dbs[p] : -bt[p];
+        }
+        X[M] = 0.0f;
+        const float toa_g = bc_toa[0];
+        const float bint = bc.bint;
+        __syncwarp();
+        float* red_dn = kap + g * KST;          // this warp's row is free now
+        float* red_up = red_dn + (n + 1);
+        const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
+        for (int pass = 0; pass < K; ++pass) {
+            const bool last = pass == K - 1;
+            // downward sweep: G_dn[s] = Ts G_dn[s+1] + (Rs G_up[s] - Ss), from the TOA
+            {
+                float b = 0.0f;
+#pragma unroll
+                for (int k = M - 1; k >= 0; --k) b = fmaf(Ts[k], b, fmaf(Rs[k], X[k], -Ss[k]));
+#pragma unroll
+                for (int lv = 0; lv < 5; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv), b);
+                const float outv = fmaf(adn_fin, toa_g, b);
+                float inv = __shfl_down_sync(FULL, outv, 1);
+                if (lane == 31) inv = toa_g;
+                X[M] = inv;
+#pragma unroll
+                for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], fmaf(Rs[k], X[k], -Ss[k]));
+                if (last) {
+#pragma unroll
+                    for (int k = 0; k < M; ++k) {
+                        const int p = lane * M + k;
+                        if (p < NP && !(p & 1)) red_dn[p >> 1] = wg * X[k];
+                    }
+                }
+            }
+            // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
+            {
+                float c = 0.0f;
+#pragma unroll
+                for (int k = 0; k < M; ++k) c = fmaf(Ts[k], c, fmaf(Rs[k], X[k + 1], Ss[k]));
+#pragma unroll
+                for (int lv = 0; lv < 5; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv), c);
+                const float boa = __shfl_sync(FULL, X[0], 0) + bint;
+                const float outv = fmaf(aup_fin, boa, c);
+                float inv = __shfl_up_sync(FULL, outv, 1);
+                if (lane == 0) inv = boa;
+                X[0] = inv;
+#pragma unroll
+                for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], fmaf(Rs[k], X[k + 1], Ss[k]));
+                if (last) {
+#pragma unroll
+                    for (int k = 1; k <= M; ++k) {
+                        const int p = lane * M + k;
+                        if (p < NP && !(p & 1)) red_up[p >> 1] = wg * X[k];
+                    }
+                    if (lane == 0) red_up[0] = wg * X[0];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = X[k];
+        __syncthreads();
+        // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators
+        for (int i = tid; i <= n; i += nthreads) {
+            float su = 0.0f, sd = 0.0f;
+            for (int gg = 0; gg < G; ++gg) {
+                su += kap[gg * KST + (n + 1) + i];
+                sd += kap[gg * KST + i];
+            }
+            acc[i] += (double)su;
+            acc[(n + 1) + i] += (double)sd;
+            acc[2 * (n + 1) + i] += (double)bt[2 * i];
+            if (i == n && Fup_toa) Fup_toa[ad.bin_off + l] = su + bt[2 * n];
+        }
+        __syncthreads();
+    }
+    double* part = P.part + ad.part_off + (long long)it.y * 3 * (n + 1);
+    for (int t = tid; t < 3 * (n + 1); t += nthreads) part[t] = acc[t];
+}
+
+// ---------------------------------------------------------------------------
+// bolometric fluxes: F_up = sum_items (sum G_up + sum B), F_dn likewise, FP64, fixed order
+__global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, double* __restrict__ Fup,
+                                double* __restrict__ Fdn)
+{
+    const int a = blockIdx.x;
+    if (status && status[a] != 0) return;
+    const AtmDesc ad = P.atms[a];
+    const int n = ad.n, stride = 3 * (n + 1);
+    const double* part = P.part + ad.part_off;
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) {
+        double su = 0.0, sd = 0.0, sb = 0.0;
+        for (int t = 0; t < ad.n_items; ++t) {
+            su += part[t * stride + i];
+            sd += part[t * stride + (n + 1) + i];
+            sb += part[t * stride + 2 * (n + 1) + i];
+        }
+        Fup[ad.if_off + i] = su + sb;
+        Fdn[ad.if_off + i] = sd + sb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// temperature step, eqs. (23)-(29), one block per atmosphere, FP64
+struct TempArgs {
+    double sigma, tol, fpre_num, fpre_exp, osc_down, osc_up, mult_max, T_floor;
+    int max_iter;
+};
+
+__global__ void temp_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
+                            double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
+                            uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
+                            double* __restrict__ metric, int* __restrict__ n_active)
+{
+    const int a = blockIdx.x;
+    if (status[a] != 0) return;
+    const AtmDesc ad = P.atms[a];
+    const int n = ad.n;
+    const double* fu = Fup + ad.if_off;
+    const double* fd = Fdn + ad.if_off;
+    double* T = T_layer + ad.lay_off;
+    __shared__ double red[32];
+    __shared__ int bad_s;
+    if (threadIdx.x == 0) bad_s = 0;
+    __syncthreads();
+    double worst = 0.0;
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double dF = (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
+        const double Ti = T[i];
+        const double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
+        if (!isfinite(m) || !isfinite(Ti)) bad = 1;
+        else worst = fmax(worst, m);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        worst = fmax(worst, __shfl_xor_sync(FULL, worst, o));
+        bad |= __shfl_xor_sync(FULL, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+    if (bad) atomicOr(&bad_s, 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(FULL, w, o));
+        if (threadIdx.x == 0) red[0] = w;
+    }
+    __syncthreads();
+    worst = red[0];
+    const int it = (iters ? iters[a] : 0) + 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (iters) iters[a] = it;
+        if (metric) metric[a] = bad_s ? NAN : worst;
+    }
+    if (bad_s) {
+        if (threadIdx.x == 0) { status[a] = 3; if (n_active) atomicSub(n_active, 1); }
+        return;
+    }
+    if (worst < targ.tol) {
+        if (threadIdx.x == 0) { status[a] = 1; if (n_active) atomicSub(n_active, 1); }
+        return;
+    }
+    // eqs. (24)-(28): rho, c_p, dz, t_rad and g cancel, leaving
+    // dT_i = -m_i fpre_num sgn(dF) |dF|^(1 - fpre_exp) / (sigma T_i^3 ln(P_int,i/P_int,i+1))
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int li = ad.lay_off + i;
+        const double dF = (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
+        const double Ti = T[i];
+        double step = 0.0;
+        if (dF != 0.0) {
+            const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) /
+                               (targ.sigma * Ti * Ti * Ti * P.lnr[li]);
+            step = -mult[li] * (dF > 0.0 ? mag : -mag);
+        }
+        double Tn = Ti + step;
+        if (Tn < targ.T_floor) Tn = targ.T_floor;
+        T[i] = Tn;
+        const unsigned h = ((unsigned)hist[li] << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
+        hist[li] = (uint8_t)h;
+        unsigned c = nhist[li];
+        if (c < 6) c += 1;
+        nhist[li] = (uint8_t)c;
+        if (c >= 6) {
+            double m = mult[li];
+            if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
+            else m = m * targ.osc_down;
+            mult[li] = m;
+        }
+    }
+    if (threadIdx.x == 0 && it >= targ.max_iter) {
+        status[a] = 2;
+        if (n_active) atomicSub(n_active, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// standalone opacity interpolation (same index and bilinear code as the fused path)
+__global__ void interp_kernel(PlanDev P, const double* __restrict__ T_layer, int a, float* __restrict__ kappa_out,
+                              long long kap_off, int32_t* __restrict__ idx_out, double* __restrict__ w_out)
+{
+    const AtmDesc ad = P.atms[a];
+    const TabDesc td = P.tabs[ad.tab];
+    const int n = ad.n, np = 2 * n + 1;
+    const double* T = T_layer + ad.lay_off;
+    const long long total = (long long)np * ad.L * P.G;
+    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < total;
+         f += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(f % P.G);
+        const long long pl = f / P.G;
+        const int l = (int)(pl % ad.L);
+        const int p = (int)(pl / ad.L);
+        const int q = ad.pt_off + p;
+        int it;
+        double wt;
+        table_coord(point_T(T, n, p), td.T0, td.dT, td.nT, it, wt);
+        if (kappa_out) kappa_out[kap_off + f] = bilinear(td.kappa, td, P.iP[q], P.wP[q], it, wt, l, g);
+        if (l == 0 && g == 0) {
+            if (idx_out) { idx_out[2 * q] = P.iP[q]; idx_out[2 * q + 1] = it; }
+            if (w_out) { w_out[2 * q] = P.wP[q]; w_out[2 * q + 1] = wt; }
+        }
+    }
+}
+
+}  // namespace helios_dev

@@ -1,0 +1,128 @@
+"""GPU parity: the CUDA path through the C ABI vs the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances (stated in the design notes): table indices and weights bit-exact; opacities 2e-6
+relative (float32 bilinear of the float32 table); bolometric fluxes and the TOA spectrum 1e-5
+relative; net flux 1e-5 of the local flux; one temperature step 1e-9 relative with bit-exact
+multipliers and sign histories; converged temperatures 0.1 K.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import make_plan, pack, rel_err
+
+pytestmark = pytest.mark.gpu
+
+FLUX_TOL = 1e-5
+
+
+def _oracle_sweep(wl, a, T, **kw):
+    return oracle.flux_sweep(oracle.Atm.from_workload(wl, a), T, **kw)
+
+
+@pytest.mark.parametrize("case", ["config1", "scat", "clamp"])
+def test_interp_opacity_indices_bit_exact(case):
+    if case == "config1":
+        wl = synth.config1(); T = synth.perturbed_profile(wl.atms[0], 1, amp=900)
+    elif case == "scat":
+        wl = synth.small_scattering(L=9, n=45); T = synth.perturbed_profile(wl.atms[0], 2)
+    else:
+        wl = synth.small_scattering(L=5, n=30)
+        T = np.linspace(80.0, 4000.0, 30)         # below and above the table's temperature range
+    plan = make_plan(wl)
+    kap, idx, w = plan.interp_opacity(pack([T]))
+    okap, oidx, ow = oracle.interp_opacity(oracle.Atm.from_workload(wl), T)
+    assert np.array_equal(idx.cpu().numpy(), oidx)
+    assert np.array_equal(w.cpu().numpy(), ow)                      # bit-exact weights
+    assert rel_err(kap.cpu().numpy(), okap.reshape(-1)) < 2e-6
+
+
+def _check_fluxes(Fu, Fd, r, tol=FLUX_TOL):
+    Fu = Fu.cpu().numpy(); Fd = Fd.cpu().numpy()
+    assert rel_err(Fu, r["Fup"]) < tol
+    assert rel_err(Fd, r["Fdn"]) < tol
+    scale = np.maximum(r["Fup"], r["Fdn"])
+    assert np.max(np.abs((Fu - Fd) - (r["Fup"] - r["Fdn"])) / scale) < tol
+
+
+def test_flux_sweep_pure_absorption_config1():
+    wl = synth.config1()
+    T = synth.perturbed_profile(wl.atms[0], 4)
+    plan = make_plan(wl)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]))
+    r = _oracle_sweep(wl, 0, T)
+    _check_fluxes(Fu, Fd, r)
+    assert rel_err(toa.cpu().numpy(), r["toa"], floor=1e-12 * r["toa"].max()) < FLUX_TOL
+
+
+@pytest.mark.parametrize("n,L", [(40, 12), (111, 7), (200, 5), (239, 3), (2, 4)])
+def test_flux_sweep_scattering_cold_then_warm(n, L):
+    # several lane tiles and a ragged tail (2n+1 not a multiple of 32), five passes,
+    # then a second evaluation at new temperatures warm-started from the first
+    wl = synth.small_scattering(L=L, n=n)
+    atm = oracle.Atm.from_workload(wl)
+    T1 = synth.perturbed_profile(wl.atms[0], 5)
+    T2 = T1 + 7.0 * np.sin(np.arange(n))
+    plan = make_plan(wl)
+    Fu, Fd, toa = plan.flux_sweep(pack([T1]), n_passes=5)
+    warm = np.zeros(atm.L * atm.G * (2 * n + 1))
+    r1 = oracle.flux_sweep(atm, T1, n_passes=5, warm=warm, warm_valid=False)
+    _check_fluxes(Fu, Fd, r1)
+    assert rel_err(toa.cpu().numpy(), r1["toa"], floor=1e-12 * r1["toa"].max()) < FLUX_TOL
+    Fu2, Fd2, _ = plan.flux_sweep(pack([T2]), n_passes=5, warm=True)
+    r2 = oracle.flux_sweep(atm, T2, n_passes=5, warm=warm, warm_valid=True)
+    _check_fluxes(Fu2, Fd2, r2)
+
+
+def test_flux_sweep_full_size_single_atmosphere():
+    # 100 layers x 3000 bins x 20 g with scattering, the launch configuration the benchmark times
+    wl = synth.config2()
+    T = synth.perturbed_profile(wl.atms[0], 6)
+    plan = make_plan(wl)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]))
+    r = _oracle_sweep(wl, 0, T)
+    _check_fluxes(Fu, Fd, r)
+    assert rel_err(toa.cpu().numpy(), r["toa"], floor=1e-9 * r["toa"].max()) < FLUX_TOL
+
+
+def test_pure_scattering_bins_conserve_net_flux():
+    wl = synth.small_scattering(L=4, n=20)
+    wl.atms[0].omega0[:] = 1.0
+    T = synth.perturbed_profile(wl.atms[0], 8)
+    plan = make_plan(wl)
+    Fu, Fd, _ = plan.flux_sweep(pack([T]), n_passes=5)
+    r = _oracle_sweep(wl, 0, T, n_passes=5)
+    _check_fluxes(Fu, Fd, r)
+
+
+def test_temperature_step_matches_oracle():
+    import torch
+    wl = synth.config1()
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 9)
+    plan = make_plan(wl)
+    st = oracle.State(atm, T)
+    Tg = pack([T])
+    state = plan.new_state()
+    for step in range(12):                                   # enough steps to exercise the 6-step rule
+        r = oracle.flux_sweep(atm, st.T)
+        Fu = torch.from_numpy(r["Fup"]).cuda(); Fd = torch.from_numpy(r["Fdn"]).cuda()
+        Tg.copy_(torch.from_numpy(st.T))
+        plan.temp_update(Fu, Fd, Tg, state)
+        rc, metric, dT = oracle.temp_update(atm, st, r["Fup"], r["Fdn"])
+        assert rel_err(Tg.cpu().numpy(), st.T) < 1e-12
+        assert np.array_equal(state["hist"].cpu().numpy(), st.hist.astype(np.uint8))
+        assert np.array_equal(state["nhist"].cpu().numpy(), st.nhist.astype(np.uint8))
+        assert rel_err(state["mult"].cpu().numpy(), st.mult) < 1e-15
+        assert state["metric"].item() == pytest.approx(metric, rel=1e-12)
+
+
+def test_deterministic_repeat():
+    wl = synth.small_scattering(L=16, n=60)
+    T = pack([synth.perturbed_profile(wl.atms[0], 10)])
+    plan = make_plan(wl)
+    a = [x.clone() for x in plan.flux_sweep(T, n_passes=5)]
+    b = plan.flux_sweep(T, n_passes=5)
+    for x, y in zip(a, b):
+        assert bool((x == y).all())
