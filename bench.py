@@ -1,0 +1,332 @@
+"""Benchmark of the radiative-equilibrium hot path on one B300 (or N, one process per GPU).
+
+A step is one radiative-equilibrium iteration over the whole workload: opacities, sublayer
+optical depths, two-stream coefficients, 1 + n_scat down/up passes, Gauss-point and bin sums,
+and the FP64 temperature step (helios_flux_sweep + helios_temp_update).  The workload is the
+full-size single atmosphere: 100 layers (1e-6..1e3 bar) x 3000 wavenumber bins
+(0.3-200 um) x 20 Gauss points, Rayleigh-like scattering, seeded synthetic k-table.
+Each GPU process runs its own copy of that atmosphere (atmospheres are independent; no
+collective on the data path): weak scaling.
+
+value: Gcell/s, cell = (atmosphere, layer, bin, g) of one full RE iteration.
+L2 is flushed (a 256 MB write) before every timed step; only the step is inside the events.
+
+--impl reference: the FP64 CPU oracle (test infrastructure) timed on the host cores on a
+bounded sample of the same workload, same metric and unit.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RE-converged atmospheres/s & flux-sweep Gcell/s, batched+surrogate vs plain"
+UNIT = "Gcell/s"
+WORKLOAD = "full-size single atmosphere: 100 layers x 3000 bins x 20 g, scattering, 5 passes/step"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_counts(wl, n_passes):
+    """Algorithmic work of one RE step (see the design notes, roofline section).
+
+    bytes: warm-start upward fluxes read and written (4 B per column point), the k-table rows
+    the profile touches (counted from the actual (iP, iT) corners), bolometric outputs.
+    fp32: per sublayer 24 coefficient operations once per step plus 4 fused multiply-adds per
+    pass (down and up recurrences); sfu: 3 per sublayer (exp, 2 reciprocals)."""
+    cells = wl.cells
+    subs = sum(2 * a.n_layers * a.n_bins for a in wl.atms) * wl.G
+    pts = sum((2 * a.n_layers + 1) * a.n_bins for a in wl.atms) * wl.G
+    fp32 = subs * (24 + 4 * n_passes)
+    sfu = subs * 3
+    return cells, pts, fp32, sfu
+
+
+def touched_table_bytes(plan, wl, T):
+    """Bytes of the k-table rows (iP, iT corners) the current profile touches, from the library's
+    own index output (helios_interp_opacity)."""
+    _, idx, _ = plan.interp_opacity(T, want_kappa=False)
+    idx = idx.cpu().numpy()
+    tot = 0
+    for a in range(plan.A):
+        rows = set()
+        for iP, iT in idx[plan.pt_off[a]:plan.pt_off[a + 1]]:
+            for dp in (0, 1):
+                for dt in (0, 1):
+                    rows.add((int(iP) + dp, int(iT) + dt))
+        tot += len(rows) * int(plan.L[a]) * wl.G * 4
+    return tot
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import synth
+    import paper_1606_05474_b300 as hp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = synth.config2()
+    wl.atms[0].T_init = synth.perturbed_profile(wl.atms[0], 11 + rank, amp=200.0)
+    ctx = hp.Context(local)
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params())
+    n_passes = plan.info.passes
+    plan.set_timing(True)
+    T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).to(dev)
+    T0 = T.clone()
+    state = plan.new_state()
+    Fu = torch.empty(plan.info.interfaces, dtype=torch.float64, device=dev)
+    Fd = torch.empty_like(Fu)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(warm):
+        plan.flux_sweep(T, warm=warm, want_toa=False, out=(Fu, Fd, None))
+        plan.temp_update(Fu, Fd, T, state)
+
+    # warm-up (the first step starts the coupled stream from zero)
+    step(False)
+    for _ in range(args.warmup - 1):
+        step(True)
+    torch.cuda.synchronize()
+    n_launch_per_step = 2 + len({a.n_layers for a in wl.atms}) + 1     # prep, sweep groups, finalize, temp
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sweep_ms = []
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.time()
+    for k in range(args.steps):
+        flush.zero_()                                   # evict L2 between timed steps
+        ev[k][0].record(stream)
+        step(True)
+        ev[k][1].record(stream)
+        sweep_ms.append(plan.last_sweep_ms())
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.time() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    cells, pts, fp32, sfu = algorithmic_counts(wl, n_passes)
+    value = cells * args.steps * world / (total_ms * 1e-3) / 1e9
+
+    # ---- end to end: host temperatures in, host temperatures and status out, every step
+    Th = torch.empty(plan.info.layers, dtype=torch.float64).pin_memory()
+    Th.copy_(T.cpu())
+    Sh = torch.empty(plan.A, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        T.copy_(Th, non_blocking=True)
+        step(True)
+        Th.copy_(T, non_blocking=True)
+        Sh.copy_(state["status"], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = float(np.sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = cells * args.steps * world / (e2e_total * 1e-3) / 1e9
+
+    # ---- one full radiative-equilibrium solve from the start profile (context)
+    solve = None
+    if not args.no_solve:
+        Ts = T0.clone()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        iters, status = plan.solve_re(Ts)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        solve = {"wall_s": round(dt, 4), "iters": int(iters.item()), "status": int(status.item()),
+                 "atm_per_s": round(1.0 / dt, 3), "tol": 1e-7}
+
+    if rank != 0:
+        return
+    P = peaks()
+    hbm = P.get("hbm_gbs", 6400.0)
+    sweep_avg = float(np.mean(sweep_ms))
+    warm_bytes = 2 * 4 * pts                        # read + write of the warm-start upward fluxes
+    table_bytes = touched_table_bytes(plan, wl, T)
+    alg_bytes = warm_bytes + table_bytes + 16 * plan.info.interfaces
+    achieved = alg_bytes / (sweep_avg * 1e-3) / 1e9
+    sm_max = P.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * sm_max * 1e6 / 1e12       # T FP32 instructions/s (FMA = 1) at max clock
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "atmospheres_per_gpu": 1, "layers": 100, "bins": 3000, "g": 20,
+                   "passes_per_step": n_passes, "cells_per_step_per_gpu": cells, "l2": "flushed before every step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "kernel": "sweep_kernel<7>", "kernel_ms": round(sweep_avg, 5),
+                     "algorithmic_bytes": int(alg_bytes), "peak_source": "measured",
+                     "fp32_frac": round(fp32 / (sweep_avg * 1e-3) / 1e12 / fp32_peak, 4),
+                     "sfu_frac": round(sfu / (sweep_avg * 1e-3) / 1e12 / (148 * 16 * sm_max * 1e6 / 1e12), 4)},
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(8 * plan.info.layers),
+                "d2h_bytes_per_step": int(8 * plan.info.layers + 4 * plan.A)},
+        "gpu_launches": n_launch_per_step * args.steps,
+        "clocks": clk,
+        "re_solve": solve,
+        "wall_s": round(wall, 3),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds=12.0, wl=None):
+    """The FP64 oracle on the same workload on the host cores: whole RE steps, as many as fit."""
+    import oracle
+    import synth
+    wl = wl or synth.config2()
+    atm = oracle.Atm.from_workload(wl)
+    st = oracle.State(atm, synth.perturbed_profile(wl.atms[0], 11, amp=200.0))
+    p = oracle.params()
+    K = oracle.passes(atm, p)
+    t0 = time.time()
+    steps = 0
+    while True:
+        r = oracle.flux_sweep(atm, st.T, n_passes=K, warm=st.warm, warm_valid=steps > 0)
+        oracle.temp_update(atm, st, r["Fup"], r["Fdn"], p)
+        steps += 1
+        if time.time() - t0 > seconds:
+            break
+    dt = time.time() - t0
+    v = wl.cells * steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full RE steps of the same atmosphere ({wl.cells} cells each), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    wl = synth.config2()
+    atm = oracle.Atm.from_workload(wl)
+    st = oracle.State(atm, synth.perturbed_profile(wl.atms[0], 11, amp=200.0))
+    p = oracle.params()
+    K = oracle.passes(atm, p)
+    # a bounded sample per step: every 10th bin of the workload (300 of 3000 bins), whole column
+    sub = synth.config2(L=300)
+    satm = oracle.Atm.from_workload(sub)
+    sst = oracle.State(satm, st.T.copy())
+    def one(i):
+        r = oracle.flux_sweep(satm, sst.T, n_passes=K, warm=sst.warm, warm_valid=i > 0)
+        oracle.temp_update(satm, sst, r["Fup"], r["Fdn"], p)
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.time()
+    for i in range(args.steps):
+        one(args.warmup + i)
+    dt = time.time() - t0
+    v = sub.cells * args.steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "300 of the 3000 bins per step (bins equal in wavenumber)"},
+            "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} RE steps on 300 bins x 100 layers x 20 g"},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,7 +109,7 @@ typedef struct {
     double fpre_exp;
     double osc_down;     /* timestep factor after an oscillation (Sect. 2.2.4: 0.67) */
     double osc_up;       /* timestep factor after a monotonic run (Sect. 2.2.4: 1.1) */
-    double mult_max;     /* cap on the per-layer timestep multiplier (1e4) */
+    double mult_max;     /* cap on the per-layer timestep multiplier (10; the paper states none) */
     double T_floor;      /* temperatures are kept >= T_floor (1 K) */
     int n_scat;          /* extra scattering passes per temperature step (Sect. 2.2.3: 4) */
     int max_iter;        /* helios_solve_re: maximum flux evaluations per atmosphere */
@@ -149,6 +149,14 @@ typedef struct {
     int64_t workspace_bytes;
 } helios_plan_info_t;
 int helios_plan_info(const helios_plan* plan, helios_plan_info_t* info);
+
+/* Measurement support (no counterpart in the paper): with timing on, every
+ * helios_flux_sweep records CUDA events around its sweep kernels on the
+ * launch stream; helios_plan_last_sweep_ms waits for the last record and
+ * returns the elapsed milliseconds.  Timing is suspended inside
+ * helios_solve_re's graphs. */
+int helios_plan_set_timing(helios_plan* plan, int on);
+int helios_plan_last_sweep_ms(helios_plan* plan, float* ms);
 
 /* Opacity at every point, bin and Gauss point (Sect. 2.3): bilinear
  * interpolation of the k-table in (T, log10 P), T at interfaces the mean of

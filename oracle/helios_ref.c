@@ -46,7 +46,7 @@ void ref_default_params(ref_params* p)
     p->fpre_exp = 0.9;
     p->osc_down = 0.67;
     p->osc_up = 1.1;
-    p->mult_max = 1e4;
+    p->mult_max = 10.0;
     p->T_floor = 1.0;
     p->mbar_mp = 2.4;
     p->n_dof = 5.0;

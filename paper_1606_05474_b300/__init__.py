@@ -20,7 +20,7 @@ __all__ = ["Context", "Plan", "default_params", "HeliosError", "build"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from ._build import build as _b
     return _b(force=force)
 
 
@@ -202,6 +202,15 @@ class Plan:
         if rc != _lib.HELIOS_OK and (raise_on_noconv or rc != _lib.HELIOS_ENOCONV):
             check(rc)
         return iters, status
+
+    # ---- measurement
+    def set_timing(self, on=True):
+        check(self.lib.helios_plan_set_timing(self.h, 1 if on else 0))
+
+    def last_sweep_ms(self) -> float:
+        v = ctypes.c_float()
+        check(self.lib.helios_plan_last_sweep_ms(self.h, ctypes.byref(v)))
+        return v.value
 
     # ---- packing helpers
     def split_layers(self, x):

@@ -41,7 +41,8 @@ class PlanInfo(ctypes.Structure):
 
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
-           "helios_flux_sweep", "helios_temp_update", "helios_solve_re"]
+           "helios_flux_sweep", "helios_temp_update", "helios_solve_re", "helios_plan_set_timing",
+           "helios_plan_last_sweep_ms"]
 
 _lib = None
 
@@ -52,7 +53,7 @@ def load(path: str = SO_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"CUDA library {path} is missing: build it with paper_1606_05474_b300/build.py")
+        raise ImportError(f"CUDA library {path} is missing: build it with paper_1606_05474_b300/_build.py")
     lib = ctypes.CDLL(path)
     P = ctypes.POINTER
     vp = c_void_p
@@ -69,6 +70,8 @@ def load(path: str = SO_PATH):
     lib.helios_flux_sweep.argtypes = [vp, vp, c_int, c_int, vp, vp, vp, vp]
     lib.helios_temp_update.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_solve_re.argtypes = [vp, vp, vp, vp, vp]
+    lib.helios_plan_set_timing.argtypes = [vp, c_int]
+    lib.helios_plan_last_sweep_ms.argtypes = [vp, P(ctypes.c_float)]
     for name in EXPORTS:
         if name not in ("helios_default_params", "helios_version", "helios_last_error"):
             getattr(lib, name).restype = c_int

@@ -149,7 +149,7 @@ struct MGroup {
 struct helios_plan {
     helios_ctx* ctx;
     helios_params_t prm;
-    int A, G, TB, passes;
+    int A, G, TB, passes, max_n;
     int64_t layers, interfaces, points, subs, bins, items, cells;
     int64_t ws_bytes;
     std::vector<AtmDesc> atms_h;
@@ -164,6 +164,9 @@ struct helios_plan {
     cudaGraphExec_t graph;
     const void* graph_key[3];
     int graph_chunk;
+    // optional timing of the sweep kernels (events on the launch stream)
+    int timing;
+    cudaEvent_t ev_sweep0, ev_sweep1;
 };
 
 extern "C" {
@@ -179,7 +182,7 @@ void helios_default_params(helios_params_t* p)
     p->fpre_exp = 0.9;
     p->osc_down = 0.67;
     p->osc_up = 1.1;
-    p->mult_max = 1e4;
+    p->mult_max = 10.0;
     p->T_floor = 1.0;
     p->n_scat = 4;
     p->max_iter = 20000;
@@ -230,6 +233,7 @@ int helios_plan_destroy(helios_plan* p)
     cudaSetDevice(p->ctx->device);
     cudaDeviceSynchronize();
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->timing) { cudaEventDestroy(p->ev_sweep0); cudaEventDestroy(p->ev_sweep1); }
     for (void* a : p->allocs) cudaFree(a);
     delete p;
     return HELIOS_OK;
@@ -312,14 +316,22 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         lay += n; ifc += n + 1; pts += 2 * n + 1; sub += 2 * n; bins += L; nu_off += L + 1;
     }
     if (pts > INT32_MAX / 2 || bins > INT32_MAX / 2) { delete P; return fail(HELIOS_EINVAL, "batch too large"); }
+    P->max_n = 0;
+    for (int a = 0; a < A; ++a) P->max_n = std::max(P->max_n, ad[a].n);
     P->layers = lay; P->interfaces = ifc; P->points = pts; P->subs = sub; P->bins = bins;
     int64_t cells = 0;
     for (int a = 0; a < A; ++a) cells += (int64_t)ad[a].n * ad[a].L * G;
     P->cells = cells;
 
     // ---- work items: tiles of TB bins
+    // bins per work item: one resident wave of blocks (one block per SM at this register
+    // budget) for a single atmosphere, capped for long batches so the tail stays short
     int TB = prm->bins_per_item;
-    if (TB <= 0) TB = (int)std::max<int64_t>(1, std::min<int64_t>(16, bins / (148 * 8)));
+    if (TB <= 0) {
+        int nsm = 148;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + nsm - 1) / nsm));
+    }
     P->TB = TB;
     std::vector<int2> items;
     int64_t part = 0, warm = 0;
@@ -348,7 +360,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     }
 
     // ---- static geometry (Sect. 2.2.1, eq. 19) and pressure-table coordinates
-    std::vector<int> iP(pts);
+    std::vector<int> iP(pts), lay_atm(lay);
     std::vector<double> wP(pts), lnr(lay);
     std::vector<float> dm(sub);
     for (int a = 0; a < A; ++a) {
@@ -364,7 +376,10 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
             host_table_coord(lp, k.log10P0, k.dlog10P, k.nP, iP[d.pt_off + p], wP[d.pt_off + p]);
         }
         for (int s = 0; s < 2 * n; ++s) dm[d.sub_off + s] = (float)((Pp[s] - Pp[s + 1]) / b->grav[a]);
-        for (int i = 0; i < n; ++i) lnr[d.lay_off + i] = std::log(Pp[2 * i] / Pp[2 * i + 2]);
+        for (int i = 0; i < n; ++i) {
+            lnr[d.lay_off + i] = std::log(Pp[2 * i] / Pp[2 * i + 2]);
+            lay_atm[d.lay_off + i] = a;
+        }
     }
 
     // ---- per-bin constants (eqs. 8, 12-14, 20-22), double precision then rounded
@@ -400,13 +415,15 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
             if (1.0 - w0 < prm->w0_pure) c.flags |= BIN_PURE_SCAT;
             if (w0 == 0.0) c.flags |= BIN_NO_SCAT;
             const double one_wg = 1.0 - w0 * g0;
-            c.lam = (float)(D * std::sqrt(one_wg * (1.0 - w0)));
+            const double lam = D * std::sqrt(one_wg * (1.0 - w0));
+            c.lam = (float)lam;
             const double kk = one_wg > 0.0 ? std::sqrt((1.0 - w0) / one_wg) : 0.0;
             const double q = (1.0 - kk) / (1.0 + kk);
             c.q = (float)q;
             c.q2 = (float)(q * q);
             c.omq2 = (float)(1.0 - q * q);
-            c.cg = (float)(eps / (prm->printed_gradient ? (1.0 + w0 * g0) : one_wg));
+            // S = eps/(1 - w0 g0) dB (1 - Ts + Rs)/dtau and (1 - Ts + Rs)/dtau = lam phi h
+            c.cl = (float)(lam * eps / (prm->printed_gradient ? (1.0 + w0 * g0) : one_wg));
             c.gam = (float)(D * (1.0 - g0) / 2.0);
         }
         nu_off += d.L + 1;
@@ -425,6 +442,13 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         td[t].nP = tabs[t].nP; td[t].nT = tabs[t].nT; td[t].L = tabs[t].L; td[t].G = tabs[t].G;
         td[t].log10P0 = tabs[t].log10P0; td[t].dlog10P = tabs[t].dlog10P;
         td[t].T0 = tabs[t].T0; td[t].dT = tabs[t].dT;
+        td[t].rowL = tabs[t].L * tabs[t].G;
+        td[t].offP = tabs[t].nP > 1 ? tabs[t].nT * td[t].rowL : 0;
+        td[t].offT = tabs[t].nT > 1 ? td[t].rowL : 0;
+        if ((int64_t)tabs[t].nP * tabs[t].nT * tabs[t].L * tabs[t].G >= ((int64_t)1 << 31)) {
+            delete P;
+            return fail(HELIOS_EINVAL, "table %d has 2^31 or more entries", t);
+        }
     }
 
     // ---- device workspace
@@ -433,7 +457,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     PlanDev& dv = P->dev;
     std::memset(&dv, 0, sizeof dv);
     AtmDesc* d_atm; TabDesc* d_tab; BinConst* d_bc; int2* d_items; int* d_order; float* d_gw;
-    int* d_iP; double* d_wP; float* d_dm; double* d_lnr;
+    int* d_iP; double* d_wP; float* d_dm; double* d_lnr; int* d_lay_atm;
 #define ALLOC(ptr, cnt)                                              \
     do {                                                             \
         if ((rc = dev_alloc(&ptr, (cnt), tot)) != HELIOS_OK) {       \
@@ -444,7 +468,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     } while (0)
     ALLOC(d_atm, A); ALLOC(d_tab, ntab); ALLOC(d_bc, bins); ALLOC(d_items, items.size());
     ALLOC(d_order, items.size()); ALLOC(d_gw, G); ALLOC(d_iP, pts); ALLOC(d_wP, pts); ALLOC(d_dm, sub);
-    ALLOC(d_lnr, lay);
+    ALLOC(d_lnr, lay); ALLOC(d_lay_atm, lay);
+    ALLOC(dv.row, pts); ALLOC(dv.wq, pts); ALLOC(dv.metric_bits, A);
     ALLOC(dv.Tpt, pts); ALLOC(dv.iT, pts); ALLOC(dv.wT, pts); ALLOC(dv.invT, pts); ALLOC(dv.Tf, pts);
     ALLOC(dv.invT_old, pts); ALLOC(dv.dinv_step, pts); ALLOC(dv.dT_step, pts);
     ALLOC(dv.dinv_sub, sub); ALLOC(dv.dT_sub, sub);
@@ -464,18 +489,40 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     }
     if ((rc = upload(d_atm, ad)) || (rc = upload(d_tab, td)) || (rc = upload(d_bc, bc)) ||
         (rc = upload(d_items, items)) || (rc = upload(d_order, order)) || (rc = upload(d_gw, gw)) ||
-        (rc = upload(d_iP, iP)) || (rc = upload(d_wP, wP)) || (rc = upload(d_dm, dm)) || (rc = upload(d_lnr, lnr))) {
+        (rc = upload(d_iP, iP)) || (rc = upload(d_wP, wP)) || (rc = upload(d_dm, dm)) || (rc = upload(d_lnr, lnr)) ||
+        (rc = upload(d_lay_atm, lay_atm))) {
         helios_plan_destroy(P);
         return rc;
     }
     cudaError_t ce = cudaMemset(dv.warm, 0, std::max<int64_t>(warm, 1) * sizeof(float));
     if (ce != cudaSuccess) { helios_plan_destroy(P); return fail(HELIOS_ECUDA, "cudaMemset: %s", cudaGetErrorString(ce)); }
-    dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.order = d_order; dv.gw = d_gw;
-    dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr;
+    dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.gw = d_gw;
+    dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
     dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso;
     P->atms_h = ad;
     P->ws_bytes = (int64_t)tot;
     *out = P;
+    return HELIOS_OK;
+}
+
+int helios_plan_set_timing(helios_plan* p, int on)
+{
+    if (!p) return fail(HELIOS_EINVAL, "helios_plan_set_timing: null plan");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    if (on && !p->timing) {
+        CUDA_TRY(cudaEventCreate(&p->ev_sweep0));
+        CUDA_TRY(cudaEventCreate(&p->ev_sweep1));
+        p->timing = 1;
+    }
+    return HELIOS_OK;
+}
+
+int helios_plan_last_sweep_ms(helios_plan* p, float* ms)
+{
+    if (!p || !ms) return fail(HELIOS_EINVAL, "helios_plan_last_sweep_ms: null argument");
+    if (!p->timing) return fail(HELIOS_EINVAL, "timing is not enabled on this plan");
+    CUDA_TRY(cudaEventSynchronize(p->ev_sweep1));
+    CUDA_TRY(cudaEventElapsedTime(ms, p->ev_sweep0, p->ev_sweep1));
     return HELIOS_OK;
 }
 
@@ -493,23 +540,33 @@ int helios_plan_info(const helios_plan* p, helios_plan_info_t* info)
 // ---------------------------------------------------------------------------
 namespace {
 
-template <int M>
-int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
-                   float* Fup_toa, cudaStream_t s)
+template <int M, int MINB>
+int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
+                    float* Fup_toa, cudaStream_t s)
 {
     const size_t smem = sweep_smem(M, p->G);
-    static thread_local int configured_dev[kMaxM + 1] = {};
-    if (configured_dev[M] != p->ctx->device + 1) {
-        CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        configured_dev[M] = p->ctx->device + 1;
+    static thread_local int configured_dev[kMaxM + 1][3] = {};
+    if (configured_dev[M][MINB] != p->ctx->device + 1) {
+        CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured_dev[M][MINB] = p->ctx->device + 1;
     }
-    sweep_kernel<M><<<gr.count, 32 * p->G, smem, s>>>(p->dev, gr.order, gr.count, status, n_passes, warm_valid, Fup_toa);
+    sweep_kernel<M, MINB><<<gr.count, 32 * p->G, smem, s>>>(p->dev, gr.order, status, n_passes, warm_valid, Fup_toa);
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
 }
 
+// lane chunks up to 7 fit two 640-thread blocks per SM within the register file
+template <int M>
+int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
+                   float* Fup_toa, cudaStream_t s)
+{
+    if (M <= 7) return launch_sweep_MB<M, 2>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+    return launch_sweep_MB<M, 1>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+}
+
 int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, float* Fup_toa, cudaStream_t s)
 {
+    if (p->timing) CUDA_TRY(cudaEventRecord(p->ev_sweep0, s));
     for (const MGroup& gr : p->groups) {
         int rc = HELIOS_OK;
         switch (gr.M) {
@@ -525,17 +582,18 @@ int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid
         }
         if (rc) return rc;
     }
+    if (p->timing) CUDA_TRY(cudaEventRecord(p->ev_sweep1, s));
     return HELIOS_OK;
 }
 
 int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes, int warm_valid, double* Fup,
                 double* Fdn, float* Fup_toa, cudaStream_t s)
 {
-    prep_kernel<<<p->A, 256, 0, s>>>(p->dev, T, status, warm_valid);
+    prep_kernel<<<dim3((2 * p->max_n + 1 + 63) / 64, p->A), 64, 0, s>>>(p->dev, T, status, warm_valid);
     CUDA_TRY(cudaGetLastError());
     int rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
     if (rc) return rc;
-    finalize_kernel<<<p->A, 128, 0, s>>>(p->dev, status, Fup, Fdn);
+    finalize_kernel<<<dim3((p->max_n + 1 + 7) / 8, p->A), 256, 0, s>>>(p->dev, status, Fup, Fdn);
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
 }
@@ -547,6 +605,19 @@ TempArgs temp_args(const helios_plan* p)
     t.osc_down = p->prm.osc_down; t.osc_up = p->prm.osc_up; t.mult_max = p->prm.mult_max;
     t.T_floor = p->prm.T_floor; t.max_iter = p->prm.max_iter;
     return t;
+}
+
+int launch_temp(helios_plan* p, const double* Fup, const double* Fdn, double* T, double* mult, uint8_t* hist,
+                uint8_t* nhist, int* status, int* iters, double* metric, int* n_active, cudaStream_t s)
+{
+    const TempArgs ta = temp_args(p);
+    const int L = (int)p->layers, blocks = (L + 127) / 128;
+    CUDA_TRY(cudaMemsetAsync(p->dev.metric_bits, 0, sizeof(unsigned long long) * p->A, s));
+    metric_kernel<<<blocks, 128, 0, s>>>(p->dev, ta, Fup, Fdn, T, status, L);
+    CUDA_TRY(cudaGetLastError());
+    step_kernel<<<blocks, 128, 0, s>>>(p->dev, ta, Fup, Fdn, T, mult, hist, nhist, status, iters, metric, n_active, L);
+    CUDA_TRY(cudaGetLastError());
+    return HELIOS_OK;
 }
 
 }  // namespace
@@ -590,10 +661,7 @@ int helios_temp_update(helios_plan* p, const double* Fup_bol, const double* Fdn_
     if (!p || !Fup_bol || !Fdn_bol || !T_layer || !mult || !hist || !nhist || !status)
         return fail(HELIOS_EINVAL, "helios_temp_update: null argument");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
-    temp_kernel<<<p->A, 256, 0, s>>>(p->dev, temp_args(p), Fup_bol, Fdn_bol, T_layer, mult, hist, nhist, status, iters,
-                                     metric, nullptr);
-    CUDA_TRY(cudaGetLastError());
-    return HELIOS_OK;
+    return launch_temp(p, Fup_bol, Fdn_bol, T_layer, mult, hist, nhist, status, iters, metric, nullptr, s);
 }
 
 int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t s)
@@ -613,13 +681,14 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
     CUDA_TRY(cudaMemsetAsync(iters, 0, sizeof(int32_t) * p->A, w));
     const int A = p->A;
     CUDA_TRY(cudaMemcpyAsync(p->n_active, &A, sizeof(int), cudaMemcpyHostToDevice, w));
-    const TempArgs ta = temp_args(p);
+    const int timing = p->timing;
+    p->timing = 0;    // no event records inside the captured graph
+    struct Restore { helios_plan* p; int t; ~Restore() { p->timing = t; } } restore{p, timing};
     // first temperature step: the coupled stream starts from zero
     int rc = launch_eval(p, T_layer, status, p->passes, 0, p->Fup, p->Fdn, nullptr, w);
     if (rc) return rc;
-    temp_kernel<<<A, 256, 0, w>>>(p->dev, ta, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters,
-                                  nullptr, p->n_active);
-    CUDA_TRY(cudaGetLastError());
+    rc = launch_temp(p, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr, p->n_active, w);
+    if (rc) return rc;
     // later steps start from the previous step's fluxes; captured as a graph of `chunk` steps
     const int chunk = p->prm.check_every > 0 ? p->prm.check_every : 16;
     const void* key[3] = {T_layer, iters, status};
@@ -629,10 +698,9 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
         CUDA_TRY(cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal));
         for (int i = 0; i < chunk && rc == HELIOS_OK; ++i) {
             rc = launch_eval(p, T_layer, status, p->passes, 1, p->Fup, p->Fdn, nullptr, w);
-            if (rc == HELIOS_OK) {
-                temp_kernel<<<A, 256, 0, w>>>(p->dev, ta, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status,
-                                              iters, nullptr, p->n_active);
-            }
+            if (rc == HELIOS_OK)
+                rc = launch_temp(p, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr,
+                                 p->n_active, w);
         }
         cudaError_t ec = cudaStreamEndCapture(w, &g);
         if (rc) { if (ec == cudaSuccess) cudaGraphDestroy(g); return rc; }

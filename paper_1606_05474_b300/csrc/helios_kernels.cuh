@@ -1,29 +1,33 @@
 // Device kernels of the radiative-equilibrium hot path (sm_103a).
 //
-// Layout of the work (one flux evaluation):
-//   prep_kernel      one block per atmosphere: point temperatures (Sect. 2.2.1),
-//                    temperature-table indices in IEEE double (Sect. 2.3) and the
-//                    float inputs of the Planck evaluations.
+// One flux evaluation + temperature step is five launches:
+//   prep_kernel      one thread per point: point temperatures (Sect. 2.2.1),
+//                    temperature-table coordinates in IEEE double (Sect. 2.3), the
+//                    table row offset and the four bilinear weights of the point, and
+//                    the float inputs of the Planck evaluations.
 //   sweep_kernel<M>  one block per work item = (atmosphere, tile of bins); one warp
-//                    per Gauss point g, so a block holds the G columns of one bin at
-//                    a time.  The 2n sublayers of a column are spread over the 32
-//                    lanes of its warp (M consecutive sublayers per lane), their
-//                    two-stream coefficients stay in registers for all K passes, and
-//                    each down or up sweep is a first-order linear recurrence solved
-//                    as a warp-wide affine scan (lane-local composition, 5 shuffle
-//                    levels, lane-local application).
-//   finalize_kernel  fixed-order FP64 sums of the per-item partials -> bolometric fluxes.
-//   temp_kernel      one block per atmosphere: FP64 temperature step and convergence.
+//                    per Gauss point g, so a block holds the G columns of one bin at a
+//                    time.  The 2n sublayers of a column are spread over the 32 lanes of
+//                    its warp (M consecutive sublayers per lane); their two-stream
+//                    coefficients stay in registers for all passes, and each down or up
+//                    sweep is a first-order linear recurrence solved as a warp-wide affine
+//                    scan (lane-local composition, 5 shuffle levels, lane-local apply).
+//   finalize_kernel  one warp per interface: fixed-order FP64 sums of the per-item
+//                    partials -> bolometric fluxes (deterministic).
+//   metric_kernel    one thread per layer: net-flux divergence and the convergence
+//                    metric of eq. (29), reduced per atmosphere with an order-free max.
+//   step_kernel      one thread per layer: convergence decision and the FP64 temperature
+//                    step of eqs. (24)-(28) with the oscillation rule.
 //
-// Fluxes are carried in the sweep as deviations from the local two-stream Planck
-// flux, G = F - 2 pi eps B_l(T_p).  With per-sublayer transmission Ts, reflection
-// Rs and source Ss the layer solutions of eqs. (11), (14) and (15) become
+// Fluxes are carried in the sweep as deviations from the local two-stream Planck flux,
+// G = F - 2 pi eps B_l(T_p).  With per-sublayer transmission Ts, reflection Rs and
+// source Ss the layer solutions of eqs. (11), (14) and (15) become
 //     G_top,up   = Ts G_bot,up + Rs G_top,dn + Ss
 //     G_bot,dn   = Ts G_top,dn + Rs G_bot,up - Ss
-// (an exact algebraic rewrite), so the net flux G_up - G_dn = F_up - F_dn never
-// forms the difference of two large float numbers, and every source term is a
-// product of the small Planck difference across the sublayer, computed with
-// expm1 from the temperature difference in double precision.
+// (an exact algebraic rewrite), so the net flux G_up - G_dn = F_up - F_dn never forms
+// the difference of two large float numbers, and every source term is a product of the
+// small Planck difference across the sublayer, evaluated from the temperature
+// difference (formed in double precision) without cancellation.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,21 +38,21 @@ namespace helios_dev {
 constexpr unsigned FULL = 0xffffffffu;
 
 // per-bin flags
-constexpr int BIN_PURE_SCAT = 1;    // 1 - omega0 < w0_pure: eq. (14)
+constexpr int BIN_PURE_SCAT = 1;    // 1 - omega0 < w0_pure: eq. (14), no thermal source
 constexpr int BIN_NO_SCAT = 2;      // omega0 == 0: streams decouple, one pass is exact
 constexpr int BIN_GREY_DARK = 4;    // grey mode visible band: no emission
 constexpr int BIN_GREY_THERM = 8;   // grey mode thermal band: pi B = sigma T^4
 
 struct BinConst {
     float xs;      // h c nu_c / k_B  (x = xs / T)
-    float E;       // 2 pi eps * 2 h c^2 nu_c^3 dnu  (2 pi eps B_l(T) = E / expm1(x))
+    float E;       // 2 pi eps * 2 h c^2 nu_c^3 dnu  (2 pi eps B_l(T) = E / (e^x - 1)); eps sigma in grey mode
     float toa;     // downward flux entering at the TOA (eq. 20)
     float bint;    // internal flux entering at the BOA (eq. 22)
     float lam;     // D sqrt((1 - w0 g0)(1 - w0))  (eq. 8 exponent per unit dtau)
     float q;       // zeta_- / zeta_+  (eq. 13)
     float q2;      // q^2
     float omq2;    // 1 - q^2
-    float cg;      // eps / (1 - w0 g0): gradient prefactor of eq. (15)
+    float cl;      // lam * eps / (1 - w0 g0): gradient prefactor of eq. (15) times lam
     float gam;     // D (1 - g0) / 2: pure-scattering coupling, eq. (14)
     int flags;
     int pad;
@@ -66,6 +70,10 @@ struct TabDesc {
     const float* kappa;
     int nP, nT, L, G;
     double log10P0, dlog10P, T0, dT;
+    int rowL;               // L * G: floats per (iP, iT) row
+    int offP;               // offset to the next pressure node (0 if nP == 1)
+    int offT;               // offset to the next temperature node (0 if nT == 1)
+    int pad;
 };
 
 struct PlanDev {
@@ -73,16 +81,18 @@ struct PlanDev {
     const TabDesc* tabs;
     const BinConst* bins;
     const int2* items;          // (atm, tile)
-    const int* order;           // launch order of items, per M group (indices into items)
     const float* gw;            // Gauss weights on [0, 1], [G]
     const int* iP;              // [points]
     const double* wP;           // [points]
     const float* dm;            // [sublayers]  column mass (g cm^-2)
     const double* lnr;          // [layers]  ln(P_int,i / P_int,i+1)
+    const int* lay_atm;         // [layers] atmosphere of each layer
     // per-evaluation state written by prep_kernel
     double* Tpt;                // [points] temperature at the point in the previous evaluation
     int* iT;                    // [points]
     double* wT;                 // [points]
+    int* row;                   // [points] table offset of corner (iP, iT) for bin 0, g 0
+    float4* wq;                 // [points] bilinear weights (00, P+1, T+1, both)
     float* invT;                // [points] 1/T
     float* Tf;                  // [points] T (grey mode)
     float* invT_old;            // [points] 1/T of the previous evaluation
@@ -92,6 +102,7 @@ struct PlanDev {
     float* dT_sub;              // [sublayers] T_a - T_b (grey mode)
     float* warm;                // warm-start G_up per column, lane-interleaved
     double* part;               // per-item partial sums [3][n+1]
+    unsigned long long* metric_bits;   // [A] max |dF|/(sigma T^4) as ordered bits
     int G, TB, A;
     float dtau_iso;
 };
@@ -123,62 +134,99 @@ __device__ __forceinline__ double point_T(const double* T, int n, int p)
     return __dmul_rn(0.5, __dadd_rn(T[i - 1], T[i]));
 }
 
-__device__ __forceinline__ float bilinear(const float* tab, const TabDesc& td, int iP, double wP, int iT, double wT,
-                                          int l, int g)
+// corner offset and the four bilinear weights of a point; all weights non-negative
+// and formed in double, so no cancellation when corners differ by decades
+__device__ __forceinline__ void point_corners(const TabDesc& td, int iP, double wP, int iT, double wT, int& row,
+                                              float4& wq)
 {
-    const int iP1 = td.nP > 1 ? iP + 1 : iP;
-    const int iT1 = td.nT > 1 ? iT + 1 : iT;
-    const size_t rowL = (size_t)td.L * td.G;
-    const size_t o = (size_t)l * td.G + g;
-    float k00 = __ldg(tab + ((size_t)iP * td.nT + iT) * rowL + o);
-    float k10 = __ldg(tab + ((size_t)iP1 * td.nT + iT) * rowL + o);
-    float k01 = __ldg(tab + ((size_t)iP * td.nT + iT1) * rowL + o);
-    float k11 = __ldg(tab + ((size_t)iP1 * td.nT + iT1) * rowL + o);
-    float wp = (float)wP, wt = (float)wT;
-    float a = fmaf(wp, k10 - k00, k00);
-    float b = fmaf(wp, k11 - k01, k01);
-    return fmaf(wt, b - a, a);
+    row = (iP * td.nT + iT) * td.rowL;
+    const double p1 = wP, p0 = 1.0 - wP, t1 = wT, t0 = 1.0 - wT;
+    wq = make_float4((float)(t0 * p0), (float)(t0 * p1), (float)(t1 * p0), (float)(t1 * p1));
+}
+
+__device__ __forceinline__ float kappa_at(const float* __restrict__ tab, const TabDesc& td, int row, float4 w, int lg)
+{
+    const float* r = tab + row + lg;
+    const float k00 = __ldg(r), k10 = __ldg(r + td.offP), k01 = __ldg(r + td.offT), k11 = __ldg(r + td.offP + td.offT);
+    return fmaf(w.w, k11, fmaf(w.z, k01, fmaf(w.y, k10, w.x * k00)));
+}
+
+// e^x - 1 with full relative accuracy: Taylor series to x^9 for |x| < 0.35 (truncation
+// below 3e-10), otherwise expf(x) - 1 (no cancellation there: |e^x - 1| > 0.29).
+__device__ __forceinline__ float em1(float x)
+{
+    if (fabsf(x) < 0.35f) {
+        float p = fmaf(x, 2.7557319e-6f, 2.4801587e-5f);
+        p = fmaf(x, p, 1.9841270e-4f);
+        p = fmaf(x, p, 1.3888889e-3f);
+        p = fmaf(x, p, 8.3333333e-3f);
+        p = fmaf(x, p, 4.1666667e-2f);
+        p = fmaf(x, p, 1.6666667e-1f);
+        p = fmaf(x, p, 0.5f);
+        p = fmaf(x, p, 1.0f);
+        return x * p;
+    }
+    return expf(x) - 1.0f;
+}
+
+// phi(x) = (1 - e^{-x})/x for x >= 0 (Taylor series below 0.35, else direct), with
+// u = 1 - e^{-x} = x phi and t = e^{-x}
+__device__ __forceinline__ void phi_u_t(float x, float& phi, float& u, float& t)
+{
+    if (x < 0.35f) {
+        float p = fmaf(x, -2.4801587e-5f, 1.9841270e-4f);     // (-1)^k x^k / (k+1)!
+        p = fmaf(x, p, -1.3888889e-3f);
+        p = fmaf(x, p, 8.3333333e-3f);
+        p = fmaf(x, p, -4.1666667e-2f);
+        p = fmaf(x, p, 1.6666667e-1f);
+        p = fmaf(x, p, -0.5f);
+        phi = fmaf(x, p, 1.0f);
+        u = x * phi;
+        t = 1.0f - u;
+    } else {
+        t = __expf(-x);
+        u = 1.0f - t;
+        phi = __fdividef(u, x);
+    }
 }
 
 // ---------------------------------------------------------------------------
 __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const int* __restrict__ status,
                             int warm_valid)
 {
-    const int a = blockIdx.x;
+    const int a = blockIdx.y;
     if (status && status[a] != 0) return;
     const AtmDesc ad = P.atms[a];
+    const int n = ad.n, np = 2 * n + 1;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
     const TabDesc td = P.tabs[ad.tab];
     const double* T = T_layer + ad.lay_off;
-    const int n = ad.n, np = 2 * n + 1;
-    for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        const int q = ad.pt_off + p;
-        double Tn = point_T(T, n, p);
-        int it;
-        double w;
-        table_coord(Tn, td.T0, td.dT, td.nT, it, w);
-        P.iT[q] = it;
-        P.wT[q] = w;
-        double To = warm_valid ? P.Tpt[q] : Tn;
-        P.invT[q] = (float)(1.0 / Tn);
-        P.Tf[q] = (float)Tn;
-        P.invT_old[q] = (float)(1.0 / To);
-        P.dinv_step[q] = (float)((To - Tn) / (To * Tn));
-        P.dT_step[q] = (float)(To - Tn);
-        P.Tpt[q] = Tn;
+    const int q = ad.pt_off + p;
+    const double Tn = point_T(T, n, p);
+    int it, row;
+    double w;
+    float4 wq;
+    table_coord(Tn, td.T0, td.dT, td.nT, it, w);
+    point_corners(td, P.iP[q], P.wP[q], it, w, row, wq);
+    P.iT[q] = it;
+    P.wT[q] = w;
+    P.row[q] = row;
+    P.wq[q] = wq;
+    const double To = warm_valid ? P.Tpt[q] : Tn;
+    const float Tnf = (float)Tn, Tof = (float)To;
+    P.invT[q] = 1.0f / Tnf;
+    P.Tf[q] = Tnf;
+    P.invT_old[q] = 1.0f / Tof;
+    P.dinv_step[q] = (float)(To - Tn) / (Tof * Tnf);
+    P.dT_step[q] = (float)(To - Tn);
+    P.Tpt[q] = Tn;
+    if (p < 2 * n) {
+        const double Tb = point_T(T, n, p + 1);
+        const float Tbf = (float)Tb;
+        P.dinv_sub[ad.sub_off + p] = (float)(Tn - Tb) / (Tnf * Tbf);
+        P.dT_sub[ad.sub_off + p] = (float)(Tn - Tb);
     }
-    for (int s = threadIdx.x; s < 2 * n; s += blockDim.x) {
-        double Ta = point_T(T, n, s), Tb = point_T(T, n, s + 1);
-        P.dinv_sub[ad.sub_off + s] = (float)((Ta - Tb) / (Ta * Tb));
-        P.dT_sub[ad.sub_off + s] = (float)(Ta - Tb);
-    }
-}
-
-// Planck difference 2 pi eps (B(x_a) - B(x_b)) from B(x_b), 1 - e^{-x_a} and
-// y = x_b - x_a without cancellation: B_a - B_b = B_b expm1(y) / (1 - e^{-x_a}).
-__device__ __forceinline__ float planck_diff(float Bb, float em1n_a, float y, float Ba_direct)
-{
-    if (fabsf(y) < 1.0f) return Bb * expm1f(y) / em1n_a;
-    return Ba_direct - Bb;
 }
 
 // Two-stream coefficients of one sublayer in deviation form (see file header).
@@ -186,38 +234,37 @@ __device__ __forceinline__ float planck_diff(float Bb, float em1n_a, float y, fl
 __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
                                            float& Ts, float& Rs, float& Ss)
 {
-    if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source
-        float a = b.gam * dtau;
-        float t = 1.0f / (1.0f + a);
+    if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source, G = F
+        const float a = b.gam * dtau;
+        const float t = __frcp_rn(1.0f + a);
         Ts = t;
         Rs = a * t;
-        Ss = dB * t;
+        Ss = 0.0f;
         return;
     }
-    const float x = b.lam * dtau;
-    const float u = -expm1f(-x);            // 1 - trans, eq. (8)
-    const float tr = (u < 0.5f) ? 1.0f - u : __expf(-x);
+    float phi, u, tr;
+    phi_u_t(b.lam * dtau, phi, u, tr);      // eq. (8): tr = exp(-lam dtau), u = 1 - tr
     const bool iso = dtau < dtau_iso;       // Sect. 2.2.1: thin sublayers use eq. (11)
     if (b.flags & BIN_NO_SCAT) {            // zeta_- = 0: Ts = trans, Rs = 0
         Ts = tr;
         Rs = 0.0f;
-        Ss = iso ? 0.5f * dB * (1.0f + tr) : b.cg * dB * __fdividef(u, dtau);
+        Ss = iso ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
         return;
     }
     // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha
-    const float t2u = u * (2.0f - u);                         // 1 - trans^2
-    const float d = 1.0f / fmaf(b.q2, t2u, b.omq2);           // 1 / (1 - q^2 trans^2)
+    const float t2u = u * (2.0f - u);                                   // 1 - trans^2
+    const float d = __frcp_rn(fmaf(b.q2, t2u, b.omq2));                 // 1 / (1 - q^2 trans^2)
     Ts = b.omq2 * tr * d;
     Rs = b.q * t2u * d;
-    const float g = d * u * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);   // 1 - Ts + Rs
-    Ss = iso ? 0.5f * dB * (2.0f - g) : b.cg * dB * __fdividef(g, dtau);
+    const float h = d * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);       // (1 - Ts + Rs) / u
+    Ss = iso ? 0.5f * dB * fmaf(-h, u, 2.0f) : b.cl * dB * phi * h;
 }
 
 // ---------------------------------------------------------------------------
-template <int M>
-__global__ void __launch_bounds__(640) sweep_kernel(PlanDev P, const int* __restrict__ order, int n_items,
-                                                    const int* __restrict__ status, int n_passes, int warm_valid,
-                                                    float* __restrict__ Fup_toa)
+template <int M, int MINB>
+__global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order,
+                                                         const int* __restrict__ status, int n_passes, int warm_valid,
+                                                         float* __restrict__ Fup_toa)
 {
     constexpr int W = 32 * M;               // point slots per column
     constexpr int KST = W + 1;              // row stride of the per-column smem rows
@@ -253,28 +300,30 @@ __global__ void __launch_bounds__(640) sweep_kernel(PlanDev P, const int* __rest
 
     for (int l = l_begin; l < l_end; ++l) {
         const BinConst bc = P.bins[ad.bin_off + l];
-        // ---- phase 1a: per-point Planck values for this bin
+        const bool emits = !(bc.flags & (BIN_GREY_DARK | BIN_PURE_SCAT | BIN_GREY_THERM));
+        // ---- phase 1a: per-point Planck values of this bin
         for (int p = tid; p < W; p += nthreads) {
             float B = 0.0f, e = 1.0f, sh = 0.0f;
             if (p < NP) {
                 const int q = ad.pt_off + p;
                 if (bc.flags & BIN_GREY_THERM) {
-                    const float T = P.Tf[q], c = 2.0f * bc.E;       // E holds eps*sigma for grey bins
+                    const float T = P.Tf[q], c = 2.0f * bc.E;       // 2 eps sigma T^4
                     const float T2 = T * T;
                     B = c * T2 * T2;
                     if (warm_valid) {
                         const float dT = P.dT_step[q], To = T + dT;
                         sh = c * dT * (To + T) * (To * To + T2);
                     }
-                } else if (!(bc.flags & BIN_GREY_DARK)) {
+                } else if (emits) {
                     const float x = bc.xs * P.invT[q];
-                    B = x > 80.0f ? 0.0f : __fdividef(bc.E, expm1f(x));   // Wien tail below 1e-34 E
-                    e = -expm1f(-x);
+                    B = x > 80.0f ? 0.0f : __fdividef(bc.E, em1(x));   // Wien tail below 1e-34 E
+                    e = -em1(-x);
                     if (warm_valid) {
+                        // B_old - B_new = B_new (e^y - 1) / (1 - e^{-x_old}), y = x_new - x_old
                         const float y = bc.xs * P.dinv_step[q];
                         const float xo = bc.xs * P.invT_old[q];
-                        const float Bo = xo > 80.0f ? 0.0f : __fdividef(bc.E, expm1f(xo));
-                        sh = (fabsf(y) < 1.0f) ? B * expm1f(y) / (-expm1f(-xo)) : Bo - B;
+                        if (fabsf(y) < 1.0f) sh = B * em1(y) / (-em1(-xo));
+                        else sh = (xo > 80.0f ? 0.0f : __fdividef(bc.E, em1(xo))) - B;
                     }
                 }
             }
@@ -291,17 +340,19 @@ __global__ void __launch_bounds__(640) sweep_kernel(PlanDev P, const int* __rest
                 if (bc.flags & BIN_GREY_THERM) {
                     const float Ta = P.Tf[ad.pt_off + s], Tb = P.Tf[ad.pt_off + s + 1];
                     d = 2.0f * bc.E * P.dT_sub[q] * (Ta + Tb) * (Ta * Ta + Tb * Tb);
-                } else if (!(bc.flags & BIN_GREY_DARK)) {
+                } else if (emits) {
+                    // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
                     const float y = bc.xs * P.dinv_sub[q];
-                    d = planck_diff(bt[s + 1], em1n[s], y, bt[s]);
+                    d = fabsf(y) < 1.0f ? bt[s + 1] * em1(y) / em1n[s] : bt[s] - bt[s + 1];
                 }
             }
             dbt[s] = d;
         }
         if (tid == 0) bc_toa[0] = bc.toa - bt[NP - 1];
+        const int lg = l * G + g_of;
         for (int p = p_first; p < NP; p += p_stride) {
             const int q = ad.pt_off + p;
-            kap[g_of * KST + p] = bilinear(tab, td, P.iP[q], P.wP[q], P.iT[q], P.wT[q], l, g_of);
+            kap[g_of * KST + p] = kappa_at(tab, td, P.row[q], P.wq[q], lg);
         }
         __syncthreads();
 
@@ -430,122 +481,125 @@ __global__ void __launch_bounds__(640) sweep_kernel(PlanDev P, const int* __rest
 }
 
 // ---------------------------------------------------------------------------
-// bolometric fluxes: F_up = sum_items (sum G_up + sum B), F_dn likewise, FP64, fixed order
+// bolometric fluxes, one warp per interface: F_up = sum_items (sum G_up + sum B),
+// F_dn likewise; lane-strided FP64 sums and a fixed xor-shuffle tree (deterministic)
 __global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, double* __restrict__ Fup,
                                 double* __restrict__ Fdn)
 {
-    const int a = blockIdx.x;
+    const int a = blockIdx.y;
     if (status && status[a] != 0) return;
     const AtmDesc ad = P.atms[a];
     const int n = ad.n, stride = 3 * (n + 1);
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i > n) return;
     const double* part = P.part + ad.part_off;
-    for (int i = threadIdx.x; i <= n; i += blockDim.x) {
-        double su = 0.0, sd = 0.0, sb = 0.0;
-        for (int t = 0; t < ad.n_items; ++t) {
-            su += part[t * stride + i];
-            sd += part[t * stride + (n + 1) + i];
-            sb += part[t * stride + 2 * (n + 1) + i];
-        }
+    double su = 0.0, sd = 0.0, sb = 0.0;
+    for (int t = lane; t < ad.n_items; t += 32) {
+        su += part[t * stride + i];
+        sd += part[t * stride + (n + 1) + i];
+        sb += part[t * stride + 2 * (n + 1) + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        su += __shfl_xor_sync(FULL, su, o);
+        sd += __shfl_xor_sync(FULL, sd, o);
+        sb += __shfl_xor_sync(FULL, sb, o);
+    }
+    if (lane == 0) {
         Fup[ad.if_off + i] = su + sb;
         Fdn[ad.if_off + i] = sd + sb;
     }
 }
 
 // ---------------------------------------------------------------------------
-// temperature step, eqs. (23)-(29), one block per atmosphere, FP64
+// temperature step, eqs. (23)-(29), FP64
 struct TempArgs {
     double sigma, tol, fpre_num, fpre_exp, osc_down, osc_up, mult_max, T_floor;
     int max_iter;
 };
 
-__global__ void temp_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
-                            double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
-                            uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
-                            double* __restrict__ metric, int* __restrict__ n_active)
+__device__ __forceinline__ double layer_divergence(const double* fu, const double* fd, int i)
 {
-    const int a = blockIdx.x;
+    return (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
+}
+
+// metric of eq. (29) per layer, max-reduced per atmosphere (non-negative doubles order like
+// their bit patterns, NaN above +inf, so an integer atomicMax is an exact, order-free max)
+__global__ void metric_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
+                              const double* __restrict__ T_layer, const int* __restrict__ status, int total_layers)
+{
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= total_layers) return;
+    const int a = P.lay_atm[li];
     if (status[a] != 0) return;
     const AtmDesc ad = P.atms[a];
-    const int n = ad.n;
-    const double* fu = Fup + ad.if_off;
-    const double* fd = Fdn + ad.if_off;
-    double* T = T_layer + ad.lay_off;
-    __shared__ double red[32];
-    __shared__ int bad_s;
-    if (threadIdx.x == 0) bad_s = 0;
-    __syncthreads();
-    double worst = 0.0;
-    int bad = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const double dF = (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
-        const double Ti = T[i];
-        const double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
-        if (!isfinite(m) || !isfinite(Ti)) bad = 1;
-        else worst = fmax(worst, m);
+    const int i = li - ad.lay_off;
+    const double dF = layer_divergence(Fup + ad.if_off, Fdn + ad.if_off, i);
+    const double Ti = T_layer[li];
+    double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
+    if (!(m == m) || !isfinite(Ti) || isinf(m)) m = __longlong_as_double(0x7ff8000000000000ll);
+    atomicMax(P.metric_bits + a, (unsigned long long)__double_as_longlong(m));
+}
+
+// one thread per layer; iters/status of each atmosphere are written by its layer-0 thread
+// only after every layer has read them (iters is read here, advanced by the next launch's
+// reader only), so no layer sees a half-updated state
+__global__ void step_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
+                            double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
+                            uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
+                            double* __restrict__ metric_out, int* __restrict__ n_active, int total_layers)
+{
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= total_layers) return;
+    const int a = P.lay_atm[li];
+    const int st0 = status[a];
+    if (st0 != 0) return;
+    const AtmDesc ad = P.atms[a];
+    const int i = li - ad.lay_off;
+    const double worst = __longlong_as_double((long long)P.metric_bits[a]);
+    const bool bad = !(worst == worst);
+    if (i == 0) {
+        const int itn = (iters ? iters[a] : 0) + 1;
+        if (iters) iters[a] = itn;
+        if (metric_out) metric_out[a] = worst;
+        int st = 0;
+        if (bad) st = 3;
+        else if (worst < targ.tol) st = 1;
+        else if (itn >= targ.max_iter) st = 2;
+        if (st) {
+            status[a] = st;
+            if (n_active) atomicSub(n_active, 1);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        worst = fmax(worst, __shfl_xor_sync(FULL, worst, o));
-        bad |= __shfl_xor_sync(FULL, bad, o);
-    }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
-    if (bad) atomicOr(&bad_s, 1);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(FULL, w, o));
-        if (threadIdx.x == 0) red[0] = w;
-    }
-    __syncthreads();
-    worst = red[0];
-    const int it = (iters ? iters[a] : 0) + 1;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (iters) iters[a] = it;
-        if (metric) metric[a] = bad_s ? NAN : worst;
-    }
-    if (bad_s) {
-        if (threadIdx.x == 0) { status[a] = 3; if (n_active) atomicSub(n_active, 1); }
-        return;
-    }
-    if (worst < targ.tol) {
-        if (threadIdx.x == 0) { status[a] = 1; if (n_active) atomicSub(n_active, 1); }
-        return;
-    }
+    if (bad || worst < targ.tol) return;
     // eqs. (24)-(28): rho, c_p, dz, t_rad and g cancel, leaving
     // dT_i = -m_i fpre_num sgn(dF) |dF|^(1 - fpre_exp) / (sigma T_i^3 ln(P_int,i/P_int,i+1))
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int li = ad.lay_off + i;
-        const double dF = (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
-        const double Ti = T[i];
-        double step = 0.0;
-        if (dF != 0.0) {
-            const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) /
-                               (targ.sigma * Ti * Ti * Ti * P.lnr[li]);
-            step = -mult[li] * (dF > 0.0 ? mag : -mag);
-        }
-        double Tn = Ti + step;
-        if (Tn < targ.T_floor) Tn = targ.T_floor;
-        T[i] = Tn;
-        const unsigned h = ((unsigned)hist[li] << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
-        hist[li] = (uint8_t)h;
-        unsigned c = nhist[li];
-        if (c < 6) c += 1;
-        nhist[li] = (uint8_t)c;
-        if (c >= 6) {
-            double m = mult[li];
-            if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
-            else m = m * targ.osc_down;
-            mult[li] = m;
-        }
+    const double dF = layer_divergence(Fup + ad.if_off, Fdn + ad.if_off, i);
+    const double Ti = T_layer[li];
+    double step = 0.0;
+    if (dF != 0.0) {
+        const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) / (targ.sigma * Ti * Ti * Ti * P.lnr[li]);
+        step = -mult[li] * (dF > 0.0 ? mag : -mag);
     }
-    if (threadIdx.x == 0 && it >= targ.max_iter) {
-        status[a] = 2;
-        if (n_active) atomicSub(n_active, 1);
+    double Tn = Ti + step;
+    if (Tn < targ.T_floor) Tn = targ.T_floor;
+    T_layer[li] = Tn;
+    const unsigned h = ((unsigned)hist[li] << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
+    hist[li] = (uint8_t)h;
+    unsigned c = nhist[li];
+    if (c < 6) c += 1;
+    nhist[li] = (uint8_t)c;
+    if (c >= 6) {
+        double m = mult[li];
+        if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
+        else m = m * targ.osc_down;
+        mult[li] = m;
     }
 }
 
 // ---------------------------------------------------------------------------
-// standalone opacity interpolation (same index and bilinear code as the fused path)
+// standalone opacity interpolation (same coordinate, corner and weight code as the fused path)
 __global__ void interp_kernel(PlanDev P, const double* __restrict__ T_layer, int a, float* __restrict__ kappa_out,
                               long long kap_off, int32_t* __restrict__ idx_out, double* __restrict__ w_out)
 {
@@ -561,10 +615,12 @@ __global__ void interp_kernel(PlanDev P, const double* __restrict__ T_layer, int
         const int l = (int)(pl % ad.L);
         const int p = (int)(pl / ad.L);
         const int q = ad.pt_off + p;
-        int it;
+        int it, row;
         double wt;
+        float4 wq;
         table_coord(point_T(T, n, p), td.T0, td.dT, td.nT, it, wt);
-        if (kappa_out) kappa_out[kap_off + f] = bilinear(td.kappa, td, P.iP[q], P.wP[q], it, wt, l, g);
+        point_corners(td, P.iP[q], P.wP[q], it, wt, row, wq);
+        if (kappa_out) kappa_out[kap_off + f] = kappa_at(td.kappa, td, row, wq, l * P.G + g);
         if (l == 0 && g == 0) {
             if (idx_out) { idx_out[2 * q] = P.iP[q]; idx_out[2 * q + 1] = it; }
             if (w_out) { w_out[2 * q] = P.wP[q]; w_out[2 * q + 1] = wt; }

@@ -31,18 +31,26 @@ def test_converged_profile_within_0p1K(which):
 
 
 def test_converged_net_flux_is_internal_flux():
+    # at convergence every layer has |dF_i| < tol sigma T_i^4, so the net flux departs from its
+    # BOA value sigma T_int^4 by at most sum_i tol sigma T_i^4; the TOA emits what enters
     wl = synth.config1()
-    plan = make_plan(wl, max_iter=100000)
+    tol = 1e-7
+    plan = make_plan(wl, max_iter=100000, tol=tol)
     T = pack([wl.atms[0].T_init])
-    plan.solve_re(T)
+    iters, status = plan.solve_re(T)
+    assert status.item() == 1
     Fu, Fd, _ = plan.flux_sweep(T, warm=True)
     net = (Fu - Fd).cpu().numpy()
-    assert np.allclose(net, oracle.SIGMA_SB * 100.0 ** 4, rtol=2e-2)
+    Tn = T.cpu().numpy()
+    bound = tol * oracle.SIGMA_SB * np.sum(Tn ** 4)
+    assert np.abs(net - oracle.SIGMA_SB * 100.0 ** 4).max() <= bound
+    assert abs(net[0] - oracle.SIGMA_SB * 100.0 ** 4) < 1e-6 * Fu[0].item()
+    assert abs(Fu[-1].item() - oracle.SIGMA_SB * (1200.0 ** 4 + 100.0 ** 4)) <= bound
 
 
 def test_grey_two_band_profile():
     wl = synth.grey_two_band(n=50)
-    plan = make_plan(wl, max_iter=200000, tol=1e-9)
+    plan = make_plan(wl, max_iter=200000, tol=1e-7)   # the float32 noise floor of the metric is near 1e-8
     T = pack([wl.atms[0].T_init])
     iters, status = plan.solve_re(T)
     assert status.item() == 1
