@@ -55,7 +55,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -130,7 +130,7 @@ def run_gpu(args):
     kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
     plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params())
     n_passes = plan.info.passes
-    plan.set_timing(True)
+    plan.set_timing(args.steps)
     T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).to(dev)
     T0 = T.clone()
     state = plan.new_state()
@@ -150,20 +150,20 @@ def run_gpu(args):
     torch.cuda.synchronize()
     n_launch_per_step = 2 + len({a.n_layers for a in wl.atms}) + 1     # prep, sweep groups, finalize, temp
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sweep_ms = []
     clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)                                     # let the sampler attach before timing
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     t_wall = time.time()
     for k in range(args.steps):
         flush.zero_()                                   # evict L2 between timed steps
         ev[k][0].record(stream)
         step(True)
         ev[k][1].record(stream)
-        sweep_ms.append(plan.last_sweep_ms())
     torch.cuda.synchronize()
+    sweep_ms = list(plan.sweep_times(args.steps))
     if world > 1:
         torch.distributed.barrier()
     wall = time.time() - t_wall
@@ -183,7 +183,8 @@ def run_gpu(args):
     Th.copy_(T.cpu())
     Sh = torch.empty(plan.A, dtype=torch.int32).pin_memory()
     e2e_ms = []
-    for k in range(args.steps):
+    e2e_steps = min(args.steps, 200)
+    for k in range(e2e_steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -199,7 +200,7 @@ def run_gpu(args):
         t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = cells * args.steps * world / (e2e_total * 1e-3) / 1e9
+    e2e_value = cells * e2e_steps * world / (e2e_total * 1e-3) / 1e9
 
     # ---- one full radiative-equilibrium solve from the start profile (context)
     solve = None
@@ -313,8 +314,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -150,12 +150,15 @@ typedef struct {
 } helios_plan_info_t;
 int helios_plan_info(const helios_plan* plan, helios_plan_info_t* info);
 
-/* Measurement support (no counterpart in the paper): with timing on, every
- * helios_flux_sweep records CUDA events around its sweep kernels on the
- * launch stream; helios_plan_last_sweep_ms waits for the last record and
- * returns the elapsed milliseconds.  Timing is suspended inside
- * helios_solve_re's graphs. */
-int helios_plan_set_timing(helios_plan* plan, int on);
+/* Measurement support (no counterpart in the paper).  helios_plan_set_timing
+ * keeps a ring of `slots` CUDA event pairs (0 turns timing off; at most
+ * 65536); while on, every helios_flux_sweep records a pair around its sweep
+ * kernels on the launch stream (timing is suspended inside helios_solve_re's
+ * graphs).  helios_plan_sweep_times waits for and returns the elapsed
+ * milliseconds of the last min(max_n, slots, evaluations) sweeps, oldest first;
+ * helios_plan_last_sweep_ms returns the last one. */
+int helios_plan_set_timing(helios_plan* plan, int slots);
+int helios_plan_sweep_times(helios_plan* plan, float* ms, int max_n, int* n_out);
 int helios_plan_last_sweep_ms(helios_plan* plan, float* ms);
 
 /* Opacity at every point, bin and Gauss point (Sect. 2.3): bilinear

@@ -204,8 +204,15 @@ class Plan:
         return iters, status
 
     # ---- measurement
-    def set_timing(self, on=True):
-        check(self.lib.helios_plan_set_timing(self.h, 1 if on else 0))
+    def set_timing(self, slots=1):
+        """Record CUDA events around the sweep kernels of the last `slots` evaluations (0: off)."""
+        check(self.lib.helios_plan_set_timing(self.h, int(slots)))
+
+    def sweep_times(self, max_n=65536):
+        buf = np.zeros(max_n, dtype=np.float32)
+        n = ctypes.c_int()
+        check(self.lib.helios_plan_sweep_times(self.h, buf.ctypes.data, max_n, ctypes.byref(n)))
+        return buf[:n.value].copy()
 
     def last_sweep_ms(self) -> float:
         v = ctypes.c_float()

@@ -128,7 +128,7 @@ int upload(T* dst, const std::vector<T>& src)
 size_t sweep_smem(int M, int G)
 {
     const size_t W = 32 * (size_t)M, KST = W + 1;
-    return 3 * (W / 2) * sizeof(double) + (G * KST + 5 * W + 1) * sizeof(float);
+    return 3 * (W / 2) * sizeof(double) + (G * KST + 4 * W + 1) * sizeof(float);
 }
 
 }  // namespace
@@ -164,9 +164,11 @@ struct helios_plan {
     cudaGraphExec_t graph;
     const void* graph_key[3];
     int graph_chunk;
-    // optional timing of the sweep kernels (events on the launch stream)
+    // optional timing of the sweep kernels: a ring of event pairs on the launch stream
     int timing;
-    cudaEvent_t ev_sweep0, ev_sweep1;
+    std::vector<cudaEvent_t> ev_ring;
+    int64_t n_timed;
+    cudaEvent_t ev_sweep0, ev_sweep1;   // the pair used by the current evaluation
 };
 
 extern "C" {
@@ -233,7 +235,7 @@ int helios_plan_destroy(helios_plan* p)
     cudaSetDevice(p->ctx->device);
     cudaDeviceSynchronize();
     if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->timing) { cudaEventDestroy(p->ev_sweep0); cudaEventDestroy(p->ev_sweep1); }
+    for (cudaEvent_t e : p->ev_ring) cudaEventDestroy(e);
     for (void* a : p->allocs) cudaFree(a);
     delete p;
     return HELIOS_OK;
@@ -330,7 +332,10 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     if (TB <= 0) {
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + nsm - 1) / nsm));
+        int maxM = 1;
+        for (int a = 0; a < A; ++a) maxM = std::max(maxM, ad[a].M);
+        const int per_sm = maxM <= 7 ? 2 : 1;      // resident sweep blocks per SM (register budget)
+        TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + (int64_t)nsm * per_sm - 1) / ((int64_t)nsm * per_sm)));
     }
     P->TB = TB;
     std::vector<int2> items;
@@ -400,7 +405,9 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
             BinConst& c = bc[d.bin_off + l];
             std::memset(&c, 0, sizeof c);
             const double nu = 0.5 * (e[l] + e[l + 1]), dnu = e[l + 1] - e[l];
-            c.xs = (float)(hP * cL * nu / kB);
+            const double xs = hP * cL * nu / kB;
+            c.xs = (float)xs;
+            c.xs_lo = (float)(xs - (double)c.xs);
             c.E = (float)(2.0 * kPi * eps * 2.0 * hP * cL * cL * nu * nu * nu * dnu);
             double toa = (s_star > 0.0 && Firr > 0.0) ? Firr * planck_bin(e[l], e[l + 1], b->T_star[a]) / s_star : 0.0;
             double bint = (s_int > 0.0 && Fint > 0.0) ? Fint * planck_bin(e[l], e[l + 1], b->T_int[a]) / s_int : 0.0;
@@ -505,24 +512,48 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     return HELIOS_OK;
 }
 
-int helios_plan_set_timing(helios_plan* p, int on)
+int helios_plan_set_timing(helios_plan* p, int slots)
 {
     if (!p) return fail(HELIOS_EINVAL, "helios_plan_set_timing: null plan");
+    if (slots < 0 || slots > 65536) return fail(HELIOS_EINVAL, "helios_plan_set_timing: %d slots", slots);
     CUDA_TRY(cudaSetDevice(p->ctx->device));
-    if (on && !p->timing) {
-        CUDA_TRY(cudaEventCreate(&p->ev_sweep0));
-        CUDA_TRY(cudaEventCreate(&p->ev_sweep1));
-        p->timing = 1;
+    CUDA_TRY(cudaDeviceSynchronize());
+    for (cudaEvent_t e : p->ev_ring) cudaEventDestroy(e);
+    p->ev_ring.clear();
+    p->timing = 0;
+    p->n_timed = 0;
+    for (int i = 0; i < 2 * slots; ++i) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        p->ev_ring.push_back(e);
     }
+    p->timing = slots > 0;
+    return HELIOS_OK;
+}
+
+int helios_plan_sweep_times(helios_plan* p, float* ms, int max_n, int* n_out)
+{
+    if (!p || !ms || !n_out || max_n < 0) return fail(HELIOS_EINVAL, "helios_plan_sweep_times: bad argument");
+    if (!p->timing) return fail(HELIOS_EINVAL, "timing is not enabled on this plan");
+    const int64_t slots = (int64_t)p->ev_ring.size() / 2;
+    const int64_t avail = std::min<int64_t>(p->n_timed, slots);
+    const int64_t n = std::min<int64_t>(avail, max_n);
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t idx = (p->n_timed - n + k) % slots;      // oldest of the last n first
+        CUDA_TRY(cudaEventSynchronize(p->ev_ring[2 * idx + 1]));
+        CUDA_TRY(cudaEventElapsedTime(ms + k, p->ev_ring[2 * idx], p->ev_ring[2 * idx + 1]));
+    }
+    *n_out = (int)n;
     return HELIOS_OK;
 }
 
 int helios_plan_last_sweep_ms(helios_plan* p, float* ms)
 {
-    if (!p || !ms) return fail(HELIOS_EINVAL, "helios_plan_last_sweep_ms: null argument");
-    if (!p->timing) return fail(HELIOS_EINVAL, "timing is not enabled on this plan");
-    CUDA_TRY(cudaEventSynchronize(p->ev_sweep1));
-    CUDA_TRY(cudaEventElapsedTime(ms, p->ev_sweep0, p->ev_sweep1));
+    int n = 0;
+    if (!ms) return fail(HELIOS_EINVAL, "helios_plan_last_sweep_ms: null argument");
+    int rc = helios_plan_sweep_times(p, ms, 1, &n);
+    if (rc) return rc;
+    if (n == 0) return fail(HELIOS_EINVAL, "no timed evaluation yet");
     return HELIOS_OK;
 }
 
@@ -560,13 +591,19 @@ template <int M>
 int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
                    float* Fup_toa, cudaStream_t s)
 {
-    if (M <= 7) return launch_sweep_MB<M, 2>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
-    return launch_sweep_MB<M, 1>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+    if constexpr (M <= 7) return launch_sweep_MB<M, 2>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+    else return launch_sweep_MB<M, 1>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
 }
 
 int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, float* Fup_toa, cudaStream_t s)
 {
-    if (p->timing) CUDA_TRY(cudaEventRecord(p->ev_sweep0, s));
+    if (p->timing) {
+        const size_t slot = (size_t)(p->n_timed % (int64_t)(p->ev_ring.size() / 2));
+        p->ev_sweep0 = p->ev_ring[2 * slot];
+        p->ev_sweep1 = p->ev_ring[2 * slot + 1];
+        ++p->n_timed;
+        CUDA_TRY(cudaEventRecord(p->ev_sweep0, s));
+    }
     for (const MGroup& gr : p->groups) {
         int rc = HELIOS_OK;
         switch (gr.M) {

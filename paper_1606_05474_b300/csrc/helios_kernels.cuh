@@ -44,7 +44,8 @@ constexpr int BIN_GREY_DARK = 4;    // grey mode visible band: no emission
 constexpr int BIN_GREY_THERM = 8;   // grey mode thermal band: pi B = sigma T^4
 
 struct BinConst {
-    float xs;      // h c nu_c / k_B  (x = xs / T)
+    float xs;      // h c nu_c / k_B  (x = xs / T), high part
+    float xs_lo;   // low part of h c nu_c / k_B (float-float)
     float E;       // 2 pi eps * 2 h c^2 nu_c^3 dnu  (2 pi eps B_l(T) = E / (e^x - 1)); eps sigma in grey mode
     float toa;     // downward flux entering at the TOA (eq. 20)
     float bint;    // internal flux entering at the BOA (eq. 22)
@@ -55,7 +56,6 @@ struct BinConst {
     float cl;      // lam * eps / (1 - w0 g0): gradient prefactor of eq. (15) times lam
     float gam;     // D (1 - g0) / 2: pure-scattering coupling, eq. (14)
     int flags;
-    int pad;
 };
 
 struct AtmDesc {
@@ -93,9 +93,9 @@ struct PlanDev {
     double* wT;                 // [points]
     int* row;                   // [points] table offset of corner (iP, iT) for bin 0, g 0
     float4* wq;                 // [points] bilinear weights (00, P+1, T+1, both)
-    float* invT;                // [points] 1/T
+    float2* invT;               // [points] 1/T as a float-float pair
     float* Tf;                  // [points] T (grey mode)
-    float* invT_old;            // [points] 1/T of the previous evaluation
+    float2* invT_old;           // [points] 1/T of the previous evaluation, float-float
     float* dinv_step;           // [points] (T_old - T)/(T_old T)
     float* dT_step;             // [points] T_old - T (grey mode)
     float* dinv_sub;            // [sublayers] (T_a - T_b)/(T_a T_b), a below b
@@ -184,10 +184,29 @@ __device__ __forceinline__ void phi_u_t(float x, float& phi, float& u, float& t)
         u = x * phi;
         t = 1.0f - u;
     } else {
-        t = __expf(-x);
-        u = 1.0f - t;
+        t = expf(-x);                      // accurate to ~1 ulp for any x (the fast intrinsic's
+        u = 1.0f - t;                      // error grows with |x| and compounds through transmissions)
         phi = __fdividef(u, x);
     }
+}
+
+// Two-stream Planck flux E / (e^x - 1) of a bin at 1/T = it (float-float), with x = xs / T
+// formed as an error-free float-float product so that the Wien tail keeps full relative
+// accuracy (B ~ e^{-x} amplifies an error in x by x).  Returns the high part of x in xh.
+__device__ __forceinline__ float planck_ff(const BinConst& b, float2 it, float& xh)
+{
+    const float p = b.xs * it.x;
+    const float lo = fmaf(b.xs, it.y, fmaf(b.xs_lo, it.x, fmaf(b.xs, it.x, -p)));
+    xh = p;
+    if (p > 80.0f) return 0.0f;                       // below 1e-34 E
+    float em;
+    if (p < 0.35f) {
+        em = em1(p + lo);
+    } else {
+        const float ex = expf(p);
+        em = fmaf(ex, lo, ex - 1.0f);                 // e^{p + lo} - 1, |lo| ~ 1e-7 p
+    }
+    return __fdividef(b.E, em);
 }
 
 // ---------------------------------------------------------------------------
@@ -215,9 +234,11 @@ __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const
     P.wq[q] = wq;
     const double To = warm_valid ? P.Tpt[q] : Tn;
     const float Tnf = (float)Tn, Tof = (float)To;
-    P.invT[q] = 1.0f / Tnf;
+    const double in = 1.0 / Tn, io = 1.0 / To;
+    const float inh = (float)in, ioh = (float)io;
+    P.invT[q] = make_float2(inh, (float)(in - (double)inh));
     P.Tf[q] = Tnf;
-    P.invT_old[q] = 1.0f / Tof;
+    P.invT_old[q] = make_float2(ioh, (float)(io - (double)ioh));
     P.dinv_step[q] = (float)(To - Tn) / (Tof * Tnf);
     P.dT_step[q] = (float)(To - Tn);
     P.Tpt[q] = Tn;
@@ -236,7 +257,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
 {
     if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source, G = F
         const float a = b.gam * dtau;
-        const float t = __frcp_rn(1.0f + a);
+        const float t = __fdividef(1.0f, 1.0f + a);
         Ts = t;
         Rs = a * t;
         Ss = 0.0f;
@@ -253,7 +274,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     }
     // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha
     const float t2u = u * (2.0f - u);                                   // 1 - trans^2
-    const float d = __frcp_rn(fmaf(b.q2, t2u, b.omq2));                 // 1 / (1 - q^2 trans^2)
+    const float d = __fdividef(1.0f, fmaf(b.q2, t2u, b.omq2));          // 1 / (1 - q^2 trans^2)
     Ts = b.omq2 * tr * d;
     Rs = b.q * t2u * d;
     const float h = d * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);       // (1 - Ts + Rs) / u
@@ -283,8 +304,7 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
     double* acc = reinterpret_cast<double*>(smem_raw);         // [3][n+1], n+1 <= W/2
     float* kap = reinterpret_cast<float*>(acc + 3 * (W / 2));  // [G][KST]; later per-warp reduction rows
     float* bt = kap + G * KST;                                 // [W] 2 pi eps B at points
-    float* em1n = bt + W;                                      // [W] 1 - e^{-x} at points
-    float* dbs = em1n + W;                                     // [W] warm-start shift B_old - B_new
+    float* dbs = bt + W;                                       // [W] warm-start shift B_old - B_new
     float* dbt = dbs + W;                                      // [W] 2 pi eps (B_a - B_b) per sublayer
     float* dm = dbt + W;                                       // [W] sublayer column mass
     float* bc_toa = dm + W;                                    // [1] TOA value in deviation form
@@ -295,15 +315,21 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
     const float wg = P.gw[g];
     const int p_first = tid / G, g_of = tid - p_first * G;     // gather mapping: consecutive g
     const int p_stride = nthreads / G;
+    // float4 gather over four consecutive g when rows stay 16-byte aligned
+    const bool vec4 = (G & 3) == 0;
+    const int G4 = G >> 2;
+    const int p4_first = vec4 ? tid / G4 : 0, g4_of = vec4 ? tid - p4_first * G4 : 0;
+    const int p4_stride = vec4 ? nthreads / G4 : 1;
     const float* tab = td.kappa;
     float* wbase = P.warm + ad.warm_off;
 
     for (int l = l_begin; l < l_end; ++l) {
         const BinConst bc = P.bins[ad.bin_off + l];
         const bool emits = !(bc.flags & (BIN_GREY_DARK | BIN_PURE_SCAT | BIN_GREY_THERM));
-        // ---- phase 1a: per-point Planck values of this bin
+        // ---- phase 1: per-point Planck values, per-sublayer Planck differences (each thread
+        // evaluates its point and the point above, so no barrier is needed in between) ...
         for (int p = tid; p < W; p += nthreads) {
-            float B = 0.0f, e = 1.0f, sh = 0.0f;
+            float B = 0.0f, sh = 0.0f, d = 0.0f;
             if (p < NP) {
                 const int q = ad.pt_off + p;
                 if (bc.flags & BIN_GREY_THERM) {
@@ -314,45 +340,57 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
                         const float dT = P.dT_step[q], To = T + dT;
                         sh = c * dT * (To + T) * (To * To + T2);
                     }
+                    if (p < NS) {
+                        const float Tb = P.Tf[q + 1];
+                        d = c * P.dT_sub[ad.sub_off + p] * (T + Tb) * (T2 + Tb * Tb);
+                    }
                 } else if (emits) {
-                    const float x = bc.xs * P.invT[q];
-                    B = x > 80.0f ? 0.0f : __fdividef(bc.E, em1(x));   // Wien tail below 1e-34 E
-                    e = -em1(-x);
+                    float x;
+                    B = planck_ff(bc, P.invT[q], x);
                     if (warm_valid) {
                         // B_old - B_new = B_new (e^y - 1) / (1 - e^{-x_old}), y = x_new - x_old
                         const float y = bc.xs * P.dinv_step[q];
-                        const float xo = bc.xs * P.invT_old[q];
-                        if (fabsf(y) < 1.0f) sh = B * em1(y) / (-em1(-xo));
-                        else sh = (xo > 80.0f ? 0.0f : __fdividef(bc.E, em1(xo))) - B;
+                        float xo;
+                        const float Bo = planck_ff(bc, P.invT_old[q], xo);
+                        sh = fabsf(y) < 1.0f ? B * __fdividef(em1(y), -em1(-xo)) : Bo - B;
+                    }
+                    if (p < NS) {
+                        // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
+                        float xb;
+                        const float Bb = planck_ff(bc, P.invT[q + 1], xb);
+                        const float y = bc.xs * P.dinv_sub[ad.sub_off + p];
+                        d = fabsf(y) < 1.0f ? Bb * __fdividef(em1(y), -em1(-x)) : B - Bb;
                     }
                 }
+                if (p == NP - 1) bc_toa[0] = bc.toa - B;
             }
             bt[p] = B;
-            em1n[p] = e;
             dbs[p] = sh;
+            dbt[p] = d;
         }
-        __syncthreads();
-        // ---- phase 1b: per-sublayer Planck differences and the opacity gather
-        for (int s = tid; s < W; s += nthreads) {
-            float d = 0.0f;
-            if (s < NS) {
-                const int q = ad.sub_off + s;
-                if (bc.flags & BIN_GREY_THERM) {
-                    const float Ta = P.Tf[ad.pt_off + s], Tb = P.Tf[ad.pt_off + s + 1];
-                    d = 2.0f * bc.E * P.dT_sub[q] * (Ta + Tb) * (Ta * Ta + Tb * Tb);
-                } else if (emits) {
-                    // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
-                    const float y = bc.xs * P.dinv_sub[q];
-                    d = fabsf(y) < 1.0f ? bt[s + 1] * em1(y) / em1n[s] : bt[s] - bt[s + 1];
-                }
+        // ... and the opacity gather, consecutive threads on consecutive g
+        if (vec4) {
+            const int lg = l * G + 4 * g4_of;
+            for (int p = p4_first; p < NP; p += p4_stride) {
+                const int q = ad.pt_off + p;
+                const float4 w = P.wq[q];
+                const float* r = tab + P.row[q] + lg;
+                const float4 k00 = __ldg(reinterpret_cast<const float4*>(r));
+                const float4 k10 = __ldg(reinterpret_cast<const float4*>(r + td.offP));
+                const float4 k01 = __ldg(reinterpret_cast<const float4*>(r + td.offT));
+                const float4 k11 = __ldg(reinterpret_cast<const float4*>(r + td.offP + td.offT));
+                float* dst = kap + (4 * g4_of) * KST + p;
+                dst[0] = fmaf(w.w, k11.x, fmaf(w.z, k01.x, fmaf(w.y, k10.x, w.x * k00.x)));
+                dst[KST] = fmaf(w.w, k11.y, fmaf(w.z, k01.y, fmaf(w.y, k10.y, w.x * k00.y)));
+                dst[2 * KST] = fmaf(w.w, k11.z, fmaf(w.z, k01.z, fmaf(w.y, k10.z, w.x * k00.z)));
+                dst[3 * KST] = fmaf(w.w, k11.w, fmaf(w.z, k01.w, fmaf(w.y, k10.w, w.x * k00.w)));
             }
-            dbt[s] = d;
-        }
-        if (tid == 0) bc_toa[0] = bc.toa - bt[NP - 1];
-        const int lg = l * G + g_of;
-        for (int p = p_first; p < NP; p += p_stride) {
-            const int q = ad.pt_off + p;
-            kap[g_of * KST + p] = kappa_at(tab, td, P.row[q], P.wq[q], lg);
+        } else {
+            const int lg = l * G + g_of;
+            for (int p = p_first; p < NP; p += p_stride) {
+                const int q = ad.pt_off + p;
+                kap[g_of * KST + p] = kappa_at(tab, td, P.row[q], P.wq[q], lg);
+            }
         }
         __syncthreads();
 
@@ -450,10 +488,12 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
 #pragma unroll
                 for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], fmaf(Rs[k], X[k + 1], Ss[k]));
                 if (last) {
+                    // weighted deviations at the interfaces; the TOA keeps the unweighted value
+                    // so its Gauss sum and the Planck add-back are done in double (emergent spectrum)
 #pragma unroll
                     for (int k = 1; k <= M; ++k) {
                         const int p = lane * M + k;
-                        if (p < NP && !(p & 1)) red_up[p >> 1] = wg * X[k];
+                        if (p < NP && !(p & 1)) red_up[p >> 1] = (p == NS) ? X[k] : wg * X[k];
                     }
                     if (lane == 0) red_up[0] = wg * X[0];
                 }
@@ -464,15 +504,21 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
         __syncthreads();
         // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators
         for (int i = tid; i <= n; i += nthreads) {
-            float su = 0.0f, sd = 0.0f;
-            for (int gg = 0; gg < G; ++gg) {
-                su += kap[gg * KST + (n + 1) + i];
-                sd += kap[gg * KST + i];
+            float sd = 0.0f;
+            double sud;
+            for (int gg = 0; gg < G; ++gg) sd += kap[gg * KST + i];
+            if (i < n) {
+                float su = 0.0f;
+                for (int gg = 0; gg < G; ++gg) su += kap[gg * KST + (n + 1) + i];
+                sud = (double)su;
+            } else {
+                sud = 0.0;
+                for (int gg = 0; gg < G; ++gg) sud += (double)P.gw[gg] * (double)kap[gg * KST + (n + 1) + i];
+                if (Fup_toa) Fup_toa[ad.bin_off + l] = (float)(sud + (double)bt[2 * n]);
             }
-            acc[i] += (double)su;
+            acc[i] += sud;
             acc[(n + 1) + i] += (double)sd;
             acc[2 * (n + 1) + i] += (double)bt[2 * i];
-            if (i == n && Fup_toa) Fup_toa[ad.bin_off + l] = su + bt[2 * n];
         }
         __syncthreads();
     }
