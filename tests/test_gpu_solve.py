@@ -89,3 +89,17 @@ def test_invalid_batches_are_rejected():
     wl = synth.small_scattering(L=4, n=300)            # beyond the supported 239 layers
     with pytest.raises(HeliosError):
         make_plan(wl)
+
+
+def test_full_size_converged_profile_matches_stored_oracle_profile():
+    # 100 layers x 3000 bins x 20 g with scattering, isothermal start; the stored profile was
+    # converged by the FP64 oracle to tol 1e-9 (tests/golden/make_golden.py)
+    import os
+    golden = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "config2_converged_T.txt"))
+    wl = synth.config2()
+    plan = make_plan(wl, max_iter=100000)
+    T = pack([wl.atms[0].T_init])
+    iters, status = plan.solve_re(T)
+    assert status.item() == 1
+    dT = np.abs(T.cpu().numpy() - golden)
+    assert dT.max() < 0.1, (dT.max(), int(np.argmax(dT)))
