@@ -217,6 +217,30 @@ int helios_temp_update(helios_plan* plan, const double* Fup_bol, const double* F
  * Returns HELIOS_ENOCONV if any atmosphere ends NOT_CONVERGED or NONFINITE. */
 int helios_solve_re(helios_plan* plan, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t stream);
 
+/* Allocation-free flux evaluation (the paper has no counterpart; it exists for
+ * callers that cannot allocate device memory -- code running under a framework
+ * that owns the device's memory pool, or in a region where cudaMalloc is not
+ * allowed).  Same computation as helios_flux_sweep from a cold start (the coupled
+ * stream starts from zero) for ONE atmosphere (batch->A == 1, host arrays as in
+ * helios_batch_t), without a plan: the call performs no cudaMalloc, cudaFree or
+ * other allocation, on the device or the host.  Its working memory is one 64 MiB
+ * array held, as a static device object of the library, by every GPU that runs
+ * the library's code until the process exits.
+ *   table   host descriptor; kappa device pointer (as in helios_ktable_t)
+ *   T_layer device double [n]; Fup_bol, Fdn_bol device double [n+1];
+ *   Fup_toa device float [L] or NULL; n_passes as in helios_flux_sweep.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Atmospheres
+ * that do not fit (n_layers > 239, n_bins > 8192, G > 20, or more than 64 MiB of
+ * scratch) are rejected with HELIOS_EINVAL before any GPU work.  All calls share
+ * the array and each call rewrites it entirely before reading it; calls whose GPU
+ * work overlaps (different streams or host threads without ordering) race on it.
+ * Results are identical in value to helios_flux_sweep with warm = 0 up to the
+ * order of the final FP64 sums. */
+int helios_flux_sweep_noalloc(const helios_batch_t* batch, const helios_ktable_t* table,
+                              const helios_params_t* params, const double* T_layer, int n_passes,
+                              double* Fup_bol, double* Fdn_bol, float* Fup_toa, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

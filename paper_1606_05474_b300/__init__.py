@@ -74,6 +74,38 @@ class Context:
             pass
 
 
+def flux_sweep_noalloc(atm, table, kappa, T, out, n_passes=0, params=None, stream=None):
+    """One cold-start flux evaluation of a single atmosphere without a plan and without any
+    allocation inside the library (helios_flux_sweep_noalloc).  For callers that cannot
+    allocate device memory: all outputs are caller-provided tensors in `out` = (Fup_bol
+    [n+1] float64, Fdn_bol [n+1] float64, Fup_toa [L] float32 or None)."""
+    torch = _torch()
+    lib = _lib.load()
+    p = params if params is not None else default_params()
+    host = {
+        "n_layers": np.array([atm.n_layers], np.int32), "n_bins": np.array([atm.n_bins], np.int32),
+        "table_id": np.zeros(1, np.int32), "P_top_bar": np.array([atm.P_top_bar], np.float64),
+        "P_bot_bar": np.array([atm.P_bot_bar], np.float64), "grav": np.array([atm.grav], np.float64),
+        "T_irr": np.array([atm.T_irr], np.float64), "T_int": np.array([atm.T_int], np.float64),
+        "T_star": np.array([atm.T_star], np.float64),
+        "nu_edges": np.ascontiguousarray(atm.nu_edges, np.float64),
+        "omega0": np.ascontiguousarray(atm.omega0, np.float32), "g0": np.ascontiguousarray(atm.g0, np.float32)}
+    b = _lib.Batch()
+    b.A = 1
+    for k, v in host.items():
+        setattr(b, k, v.ctypes.data)
+    if not (kappa.is_cuda and kappa.dtype == torch.float32 and kappa.is_contiguous()):
+        raise ValueError("the k-table must be a contiguous float32 CUDA tensor")
+    t = _lib.KTable()
+    t.nP, t.nT, t.L, t.G = table.nP, table.nT, table.L, table.G
+    t.log10P0, t.dlog10P, t.T0, t.dT = table.log10P0, table.dlog10P, table.T0, table.dT
+    t.kappa = kappa.data_ptr()
+    Fu, Fd, toa = out
+    check(lib.helios_flux_sweep_noalloc(ctypes.byref(b), ctypes.byref(t), ctypes.byref(p), T.data_ptr(),
+                                        int(n_passes), Fu.data_ptr(), Fd.data_ptr(), _ptr(toa), _stream_ptr(stream)))
+    return Fu, Fd, toa
+
+
 class Plan:
     """A validated batch of atmospheres with its device workspace.
 

@@ -42,7 +42,7 @@ class PlanInfo(ctypes.Structure):
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
            "helios_flux_sweep", "helios_temp_update", "helios_solve_re", "helios_plan_set_timing",
-           "helios_plan_last_sweep_ms", "helios_plan_sweep_times"]
+           "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc"]
 
 _lib = None
 
@@ -73,6 +73,7 @@ def load(path: str = SO_PATH):
     lib.helios_plan_set_timing.argtypes = [vp, c_int]
     lib.helios_plan_last_sweep_ms.argtypes = [vp, P(ctypes.c_float)]
     lib.helios_plan_sweep_times.argtypes = [vp, vp, c_int, P(c_int)]
+    lib.helios_flux_sweep_noalloc.argtypes = [P(Batch), P(KTable), P(Params), vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("helios_default_params", "helios_version", "helios_last_error"):
             getattr(lib, name).restype = c_int

@@ -133,6 +133,8 @@ size_t sweep_smem(int M, int G)
 
 }  // namespace
 
+__attribute__((visibility("hidden"))) void helios_set_error_text(const char* msg) { g_err = msg; }
+
 struct helios_ctx {
     int device;
     cudaStream_t stream;

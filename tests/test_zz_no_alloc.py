@@ -1,0 +1,59 @@
+"""The allocation-free flux evaluation, helios_flux_sweep_noalloc, through the C ABI.
+
+Some callers cannot allocate device memory: a framework that owns the whole memory pool of
+the device, or code running where cudaMalloc is not allowed.  This entry point serves them:
+its working memory is a fixed array inside the library, so the call allocates nothing; the
+caller passes the inputs and the output buffers.  The test checks it against the plan-based
+helios_flux_sweep (cold start) on the same atmosphere, on two calls in a row with different
+temperatures, because every call reuses the same array and must not see what the previous
+call left there.  This file is collected last so that a run stopping at the first failure has
+run every other test before it.
+"""
+import numpy as np
+import pytest
+
+import synth
+from helpers import make_plan, pack
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5      # the flux tolerance of the parity tests
+
+
+def _out(plan):
+    import torch
+    n1 = int(plan.info.interfaces)
+    return (torch.empty(n1, dtype=torch.float64, device="cuda"), torch.empty(n1, dtype=torch.float64, device="cuda"),
+            torch.empty(int(plan.info.bins), dtype=torch.float32, device="cuda"))
+
+
+def test_noalloc_matches_plan_sweep_on_two_calls_in_a_row():
+    import paper_1606_05474_b300 as hp
+    import torch
+    wl = synth.config2()
+    atm, tab = wl.atms[0], wl.tables[0]
+    plan = make_plan(wl)
+    kappa = plan.kappa[0]
+    profiles = [synth.perturbed_profile(atm, 21), synth.perturbed_profile(atm, 22, amp=500.0)]
+    for T in profiles:
+        Tg = pack([T])
+        ref = [x.clone() for x in plan.flux_sweep(Tg, warm=False)]
+        got = hp.flux_sweep_noalloc(atm, tab, kappa, Tg, _out(plan))
+        torch.cuda.synchronize()
+        for r, g in zip(ref, got):
+            r = r.cpu().numpy().astype(np.float64); g = g.cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(g - r) / np.maximum(np.abs(r), 1e-30)) < TOL
+
+
+def test_noalloc_rejects_atmospheres_beyond_its_fixed_size():
+    import paper_1606_05474_b300 as hp
+    wl = synth.small_scattering(L=4, n=300)
+    plan_free = wl.atms[0]
+    import torch
+    kappa = torch.from_numpy(wl.tables[0].kappa32).cuda()
+    T = torch.full((300,), 1000.0, dtype=torch.float64, device="cuda")
+    out = (torch.empty(301, dtype=torch.float64, device="cuda"), torch.empty(301, dtype=torch.float64, device="cuda"),
+           None)
+    with pytest.raises(hp.HeliosError) as e:
+        hp.flux_sweep_noalloc(plan_free, wl.tables[0], kappa, T, out)
+    assert e.value.code == -1 and b"n_layers" in hp._lib.load().helios_last_error()
