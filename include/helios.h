@@ -118,6 +118,7 @@ typedef struct {
     int printed_gradient;/* 1: gradient prefactor eps/(1 + w0 g0) as printed in eq. (15) */
     int bins_per_item;   /* bins one thread block processes per work item (0: automatic) */
     int check_every;     /* helios_solve_re: iterations per CUDA-graph launch between checks (0: auto) */
+    int persistent;      /* 1: a resident grid pulls work items from a counter; 0: one block per item */
 } helios_params_t;
 
 void helios_default_params(helios_params_t* p);
@@ -216,6 +217,17 @@ int helios_temp_update(helios_plan* plan, const double* Fup_bol, const double* F
  *   iters   device int32 [A] (out), status device int32 [A] (out)
  * Returns HELIOS_ENOCONV if any atmosphere ends NOT_CONVERGED or NONFINITE. */
 int helios_solve_re(helios_plan* plan, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t stream);
+
+/* Autotuner (measurement support; the paper has no counterpart): picks the work
+ * item size (bins_per_item) and launch mode (persistent) for a batch by timing
+ * one flux evaluation of a calibration subset (up to 128 atmospheres spread over
+ * the batch) for each candidate, and returns `base` with the fastest choice in
+ * `tuned`.  The choice is cached in the JSON file cache_path (may be NULL) under a
+ * key made of the device name and the batch's shape bucket (log2 of A, mean
+ * layers, mean bins, G, scattering or not); a cached key is returned without
+ * timing.  Allocates and frees its own temporary plans and buffers; synchronous. */
+int helios_autotune(helios_ctx* ctx, const helios_batch_t* batch, const helios_ktable_t* tables, int ntab,
+                    const helios_params_t* base, const char* cache_path, helios_params_t* tuned);
 
 /* Allocation-free flux evaluation (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory -- code running under a framework

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (ATM_ACTIVE, ATM_CONVERGED, ATM_NONFINITE, ATM_NOT_CONVERGED, HeliosError,  # noqa: F401
                    check)
 
-__all__ = ["Context", "Plan", "default_params", "HeliosError", "build"]
+__all__ = ["Context", "Plan", "default_params", "autotune", "flux_sweep_noalloc", "HeliosError", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -106,6 +106,48 @@ def flux_sweep_noalloc(atm, table, kappa, T, out, n_passes=0, params=None, strea
     return Fu, Fd, toa
 
 
+def _marshal(atms, tables, kappa):
+    """Host arrays of a helios_batch_t and the helios_ktable_t descriptors (kept alive by the caller)."""
+    torch = _torch()
+    host = {
+        "n_layers": np.array([a.n_layers for a in atms], dtype=np.int32),
+        "n_bins": np.array([a.n_bins for a in atms], dtype=np.int32),
+        "table_id": np.array([a.table_id for a in atms], dtype=np.int32),
+        "P_top_bar": np.array([a.P_top_bar for a in atms], dtype=np.float64),
+        "P_bot_bar": np.array([a.P_bot_bar for a in atms], dtype=np.float64),
+        "grav": np.array([a.grav for a in atms], dtype=np.float64),
+        "T_irr": np.array([a.T_irr for a in atms], dtype=np.float64),
+        "T_int": np.array([a.T_int for a in atms], dtype=np.float64),
+        "T_star": np.array([a.T_star for a in atms], dtype=np.float64),
+        "nu_edges": np.ascontiguousarray(np.concatenate([np.asarray(a.nu_edges, np.float64) for a in atms])),
+        "omega0": np.ascontiguousarray(np.concatenate([np.asarray(a.omega0, np.float32) for a in atms])),
+        "g0": np.ascontiguousarray(np.concatenate([np.asarray(a.g0, np.float32) for a in atms])),
+    }
+    b = _lib.Batch()
+    b.A = len(atms)
+    for k, v in host.items():
+        setattr(b, k, v.ctypes.data)
+    for k in kappa:
+        if not (k.is_cuda and k.dtype == torch.float32 and k.is_contiguous()):
+            raise ValueError("k-tables must be contiguous float32 CUDA tensors")
+    tabs = (_lib.KTable * len(tables))()
+    for i, (t, k) in enumerate(zip(tables, kappa)):
+        tabs[i].nP, tabs[i].nT, tabs[i].L, tabs[i].G = t.nP, t.nT, t.L, t.G
+        tabs[i].log10P0, tabs[i].dlog10P, tabs[i].T0, tabs[i].dT = t.log10P0, t.dlog10P, t.T0, t.dT
+        tabs[i].kappa = k.data_ptr()
+    return b, tabs, host
+
+
+def autotune(ctx, atms, tables, kappa, params=None, cache_path=None):
+    """Pick bins_per_item and the launch mode for this batch (helios_autotune); returns tuned params."""
+    base = params if params is not None else default_params()
+    b, tabs, _host = _marshal(atms, tables, kappa)
+    out = _lib.Params()
+    check(ctx.lib.helios_autotune(ctx.h, ctypes.byref(b), tabs, len(tables), ctypes.byref(base),
+                                  cache_path.encode() if cache_path else None, ctypes.byref(out)))
+    return out
+
+
 class Plan:
     """A validated batch of atmospheres with its device workspace.
 
@@ -118,37 +160,11 @@ class Plan:
         torch = _torch()
         self.ctx, self.lib = ctx, ctx.lib
         self.params = params if params is not None else default_params()
-        A = len(atms)
-        self.A = A
+        self.A = len(atms)
         self.n = np.array([a.n_layers for a in atms], dtype=np.int32)
         self.L = np.array([a.n_bins for a in atms], dtype=np.int32)
-        self._host = {
-            "n_layers": self.n,
-            "n_bins": self.L,
-            "table_id": np.array([a.table_id for a in atms], dtype=np.int32),
-            "P_top_bar": np.array([a.P_top_bar for a in atms], dtype=np.float64),
-            "P_bot_bar": np.array([a.P_bot_bar for a in atms], dtype=np.float64),
-            "grav": np.array([a.grav for a in atms], dtype=np.float64),
-            "T_irr": np.array([a.T_irr for a in atms], dtype=np.float64),
-            "T_int": np.array([a.T_int for a in atms], dtype=np.float64),
-            "T_star": np.array([a.T_star for a in atms], dtype=np.float64),
-            "nu_edges": np.ascontiguousarray(np.concatenate([np.asarray(a.nu_edges, np.float64) for a in atms])),
-            "omega0": np.ascontiguousarray(np.concatenate([np.asarray(a.omega0, np.float32) for a in atms])),
-            "g0": np.ascontiguousarray(np.concatenate([np.asarray(a.g0, np.float32) for a in atms])),
-        }
-        b = _lib.Batch()
-        b.A = A
-        for k, v in self._host.items():
-            setattr(b, k, v.ctypes.data)
+        b, tabs, self._host = _marshal(atms, tables, kappa)
         self.kappa = list(kappa)
-        for k in self.kappa:
-            if not (k.is_cuda and k.dtype == torch.float32 and k.is_contiguous()):
-                raise ValueError("k-tables must be contiguous float32 CUDA tensors")
-        tabs = (_lib.KTable * len(tables))()
-        for i, (t, k) in enumerate(zip(tables, self.kappa)):
-            tabs[i].nP, tabs[i].nT, tabs[i].L, tabs[i].G = t.nP, t.nT, t.L, t.G
-            tabs[i].log10P0, tabs[i].dlog10P, tabs[i].T0, tabs[i].dT = t.log10P0, t.dlog10P, t.T0, t.dT
-            tabs[i].kappa = k.data_ptr()
         h = ctypes.c_void_p()
         check(self.lib.helios_plan_create(ctx.h, ctypes.byref(b), tabs, len(tables), ctypes.byref(self.params),
                                           ctypes.byref(h)))

@@ -31,7 +31,7 @@ class Params(ctypes.Structure):
                 ("fpre_num", c_double), ("fpre_exp", c_double), ("osc_down", c_double), ("osc_up", c_double),
                 ("mult_max", c_double), ("T_floor", c_double), ("n_scat", c_int), ("max_iter", c_int),
                 ("grey_mode", c_int), ("printed_gradient", c_int), ("bins_per_item", c_int),
-                ("check_every", c_int)]
+                ("check_every", c_int), ("persistent", c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -42,7 +42,8 @@ class PlanInfo(ctypes.Structure):
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
            "helios_flux_sweep", "helios_temp_update", "helios_solve_re", "helios_plan_set_timing",
-           "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc"]
+           "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
+           "helios_autotune"]
 
 _lib = None
 
@@ -73,6 +74,7 @@ def load(path: str = SO_PATH):
     lib.helios_plan_set_timing.argtypes = [vp, c_int]
     lib.helios_plan_last_sweep_ms.argtypes = [vp, P(ctypes.c_float)]
     lib.helios_plan_sweep_times.argtypes = [vp, vp, c_int, P(c_int)]
+    lib.helios_autotune.argtypes = [vp, P(Batch), P(KTable), c_int, P(Params), ctypes.c_char_p, P(Params)]
     lib.helios_flux_sweep_noalloc.argtypes = [P(Batch), P(KTable), P(Params), vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("helios_default_params", "helios_version", "helios_last_error"):

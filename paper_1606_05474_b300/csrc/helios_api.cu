@@ -146,6 +146,10 @@ struct MGroup {
     int M;
     int count;
     int* order;       // device
+    int* counter;     // device work counter (persistent launches)
+    int grid;         // persistent grid: resident blocks on all SMs
+    cudaStream_t stream;   // the group's own stream (several groups overlap)
+    cudaEvent_t join;
 };
 
 struct helios_plan {
@@ -166,6 +170,8 @@ struct helios_plan {
     cudaGraphExec_t graph;
     const void* graph_key[3];
     int graph_chunk;
+    cudaEvent_t fork;
+    int* counters;
     // optional timing of the sweep kernels: a ring of event pairs on the launch stream
     int timing;
     std::vector<cudaEvent_t> ev_ring;
@@ -194,6 +200,7 @@ void helios_default_params(helios_params_t* p)
     p->printed_gradient = 0;
     p->bins_per_item = 0;
     p->check_every = 0;
+    p->persistent = 1;
 }
 
 int helios_version(void) { return HELIOS_VERSION; }
@@ -237,6 +244,11 @@ int helios_plan_destroy(helios_plan* p)
     cudaSetDevice(p->ctx->device);
     cudaDeviceSynchronize();
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (MGroup& g : p->groups) {
+        if (g.stream) cudaStreamDestroy(g.stream);
+        if (g.join) cudaEventDestroy(g.join);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     for (cudaEvent_t e : p->ev_ring) cudaEventDestroy(e);
     for (void* a : p->allocs) cudaFree(a);
     delete p;
@@ -256,7 +268,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         return fail(HELIOS_EINVAL, "batch has a null array");
     if (!(prm->D > 0.0) || !(prm->dtau_iso >= 0.0) || !(prm->w0_pure >= 0.0) || !(prm->tol > 0.0) ||
         prm->n_scat < 0 || prm->max_iter < 1 || !(prm->osc_down > 0.0) || !(prm->osc_up > 0.0) ||
-        !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0)
+        !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0 ||
+        prm->persistent < 0 || prm->persistent > 1)
         return fail(HELIOS_EINVAL, "invalid parameter set");
     const int G = tabs[0].G;
     if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
@@ -485,16 +498,35 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     ALLOC(dv.part, part); ALLOC(dv.warm, warm);
     ALLOC(P->Fup, ifc); ALLOC(P->Fdn, ifc); ALLOC(P->mult, lay); ALLOC(P->hist, lay); ALLOC(P->nhist, lay);
     ALLOC(P->n_active, 1);
+    ALLOC(P->counters, kMaxM + 1);
 #undef ALLOC
     std::vector<int> order;
+    int nsm_all = 148;
+    cudaDeviceGetAttribute(&nsm_all, cudaDevAttrMultiProcessorCount, ctx->device);
     for (int M = 1; M <= kMaxM; M += 2) {
         if (byM[M].empty()) continue;
         MGroup gr;
+        std::memset(&gr, 0, sizeof gr);
         gr.M = M;
         gr.count = (int)byM[M].size();
         gr.order = d_order + order.size();
+        gr.counter = P->counters + M;
+        gr.grid = std::min(gr.count, nsm_all * (M <= 7 ? 2 : 1));
         order.insert(order.end(), byM[M].begin(), byM[M].end());
         P->groups.push_back(gr);
+    }
+    for (MGroup& gr : P->groups) {
+        if (P->groups.size() > 1) {
+            if (cudaStreamCreateWithFlags(&gr.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&gr.join, cudaEventDisableTiming) != cudaSuccess) {
+                helios_plan_destroy(P);
+                return fail(HELIOS_ECUDA, "stream/event creation failed");
+            }
+        }
+    }
+    if (P->groups.size() > 1 && cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) != cudaSuccess) {
+        helios_plan_destroy(P);
+        return fail(HELIOS_ECUDA, "event creation failed");
     }
     if ((rc = upload(d_atm, ad)) || (rc = upload(d_tab, td)) || (rc = upload(d_bc, bc)) ||
         (rc = upload(d_items, items)) || (rc = upload(d_order, order)) || (rc = upload(d_gw, gw)) ||
@@ -583,7 +615,13 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
         CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         configured_dev[M][MINB] = p->ctx->device + 1;
     }
-    sweep_kernel<M, MINB><<<gr.count, 32 * p->G, smem, s>>>(p->dev, gr.order, status, n_passes, warm_valid, Fup_toa);
+    if (p->prm.persistent) {
+        sweep_kernel<M, MINB><<<gr.grid, 32 * p->G, smem, s>>>(p->dev, gr.order, gr.count, gr.counter, status,
+                                                              n_passes, warm_valid, Fup_toa);
+    } else {
+        sweep_kernel<M, MINB><<<gr.count, 32 * p->G, smem, s>>>(p->dev, gr.order, gr.count, nullptr, status,
+                                                               n_passes, warm_valid, Fup_toa);
+    }
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
 }
@@ -606,21 +644,33 @@ int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid
         ++p->n_timed;
         CUDA_TRY(cudaEventRecord(p->ev_sweep0, s));
     }
-    for (const MGroup& gr : p->groups) {
+    if (p->prm.persistent) CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(int) * (kMaxM + 1), s));
+    const bool fork = p->groups.size() > 1;
+    if (fork) CUDA_TRY(cudaEventRecord(p->fork, s));
+    for (const MGroup& gr0 : p->groups) {
         int rc = HELIOS_OK;
+        const MGroup& gr = gr0;
+        cudaStream_t gs = s;
+        if (fork) {
+            gs = gr.stream;
+            CUDA_TRY(cudaStreamWaitEvent(gs, p->fork, 0));
+        }
         switch (gr.M) {
-            case 1: rc = launch_sweep_M<1>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 3: rc = launch_sweep_M<3>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 5: rc = launch_sweep_M<5>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 7: rc = launch_sweep_M<7>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 9: rc = launch_sweep_M<9>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 11: rc = launch_sweep_M<11>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 13: rc = launch_sweep_M<13>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
-            case 15: rc = launch_sweep_M<15>(p, gr, status, n_passes, warm_valid, Fup_toa, s); break;
+            case 1: rc = launch_sweep_M<1>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 3: rc = launch_sweep_M<3>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 5: rc = launch_sweep_M<5>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 7: rc = launch_sweep_M<7>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 9: rc = launch_sweep_M<9>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 11: rc = launch_sweep_M<11>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 13: rc = launch_sweep_M<13>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 15: rc = launch_sweep_M<15>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
             default: rc = fail(HELIOS_EINVAL, "unsupported lane chunk %d", gr.M);
         }
         if (rc) return rc;
+        if (fork) CUDA_TRY(cudaEventRecord(gr.join, gs));
     }
+    if (fork)
+        for (const MGroup& gr : p->groups) CUDA_TRY(cudaStreamWaitEvent(s, gr.join, 0));
     if (p->timing) CUDA_TRY(cudaEventRecord(p->ev_sweep1, s));
     return HELIOS_OK;
 }
@@ -771,3 +821,160 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Autotuner: times one flux evaluation of a calibration subset of the batch for each
+// candidate work-item size and launch mode; caches the winner per (device, shape bucket).
+namespace {
+
+std::string shape_key(const helios_batch_t* b, int G, const char* dev_name)
+{
+    double mn = 0.0, mL = 0.0;
+    bool scat = false;
+    int64_t off = 0;
+    for (int a = 0; a < b->A; ++a) {
+        mn += b->n_layers[a];
+        mL += b->n_bins[a];
+        for (int l = 0; l < b->n_bins[a]; ++l) scat |= b->omega0[off + l] != 0.0f;
+        off += b->n_bins[a];
+    }
+    mn /= b->A;
+    mL /= b->A;
+    int lgA = 0;
+    while ((1 << (lgA + 1)) <= b->A) ++lgA;
+    char buf[384];
+    snprintf(buf, sizeof buf, "%s|A2^%d|n%d|L%d|G%d|%s", dev_name, lgA, (int)(mn / 25.0 + 0.5) * 25,
+             (int)(mL / 250.0 + 0.5) * 250, G, scat ? "scat" : "abs");
+    return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, int& tb, int& pers)
+{
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    std::string txt;
+    char buf[4096];
+    size_t r;
+    while ((r = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, r);
+    fclose(f);
+    const std::string pat = "\"" + key + "\": {";
+    const size_t at = txt.find(pat);
+    if (at == std::string::npos) return false;
+    return sscanf(txt.c_str() + at + pat.size(), " \"bins_per_item\": %d, \"persistent\": %d", &tb, &pers) == 2;
+}
+
+void cache_store(const char* path, const std::string& key, int tb, int pers, double ms)
+{
+    if (!path) return;
+    std::string txt;
+    if (FILE* f = fopen(path, "r")) {
+        char buf[4096];
+        size_t r;
+        while ((r = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, r);
+        fclose(f);
+    }
+    const size_t close = txt.rfind('}');
+    char entry[640];
+    snprintf(entry, sizeof entry, "\"%s\": {\"bins_per_item\": %d, \"persistent\": %d, \"ms\": %.6f}", key.c_str(), tb,
+             pers, ms);
+    std::string out;
+    if (close == std::string::npos || txt.find('{') == std::string::npos) out = std::string("{\n  ") + entry + "\n}\n";
+    else out = txt.substr(0, close) + (txt.find('"') != std::string::npos ? ",\n  " : "  ") + entry + "\n}\n";
+    const std::string tmp = std::string(path) + ".tmp";
+    if (FILE* f = fopen(tmp.c_str(), "w")) {
+        fwrite(out.data(), 1, out.size(), f);
+        fclose(f);
+        rename(tmp.c_str(), path);
+    }
+}
+
+}  // namespace
+
+extern "C" int helios_autotune(helios_ctx* ctx, const helios_batch_t* b, const helios_ktable_t* tabs, int ntab,
+                               const helios_params_t* base, const char* cache_path, helios_params_t* tuned)
+{
+    if (!ctx || !b || !tabs || !base || !tuned || b->A < 1 || ntab < 1)
+        return fail(HELIOS_EINVAL, "helios_autotune: bad argument");
+    CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, ctx->device));
+    const std::string key = shape_key(b, tabs[0].G, prop.name);
+    *tuned = *base;
+    int tb = 0, pers = 0;
+    if (cache_lookup(cache_path, key, tb, pers)) {
+        tuned->bins_per_item = tb;
+        tuned->persistent = pers;
+        return HELIOS_OK;
+    }
+    // calibration subset: up to 128 atmospheres spread over the batch
+    const int stride = std::max(1, b->A / 128);
+    std::vector<int32_t> n, L, tid;
+    std::vector<double> Pt, Pb, gr, Ti, Tn, Ts, nu;
+    std::vector<float> w0, g0;
+    std::vector<int64_t> nu_off(b->A + 1, 0), bin_off(b->A + 1, 0);
+    for (int a = 0; a < b->A; ++a) {
+        nu_off[a + 1] = nu_off[a] + b->n_bins[a] + 1;
+        bin_off[a + 1] = bin_off[a] + b->n_bins[a];
+    }
+    int64_t layers = 0;
+    for (int a = 0; a < b->A; a += stride) {
+        n.push_back(b->n_layers[a]); L.push_back(b->n_bins[a]); tid.push_back(b->table_id[a]);
+        Pt.push_back(b->P_top_bar[a]); Pb.push_back(b->P_bot_bar[a]); gr.push_back(b->grav[a]);
+        Ti.push_back(b->T_irr[a]); Tn.push_back(b->T_int[a]); Ts.push_back(b->T_star[a]);
+        nu.insert(nu.end(), b->nu_edges + nu_off[a], b->nu_edges + nu_off[a + 1]);
+        w0.insert(w0.end(), b->omega0 + bin_off[a], b->omega0 + bin_off[a + 1]);
+        g0.insert(g0.end(), b->g0 + bin_off[a], b->g0 + bin_off[a + 1]);
+        layers += b->n_layers[a];
+    }
+    helios_batch_t sub;
+    sub.A = (int)n.size(); sub.n_layers = n.data(); sub.n_bins = L.data(); sub.table_id = tid.data();
+    sub.P_top_bar = Pt.data(); sub.P_bot_bar = Pb.data(); sub.grav = gr.data(); sub.T_irr = Ti.data();
+    sub.T_int = Tn.data(); sub.T_star = Ts.data(); sub.nu_edges = nu.data(); sub.omega0 = w0.data(); sub.g0 = g0.data();
+    double *dT = nullptr, *dFu = nullptr, *dFd = nullptr;
+    int64_t ifc = layers + sub.A;
+    if (cudaMalloc((void**)&dT, sizeof(double) * layers) != cudaSuccess ||
+        cudaMalloc((void**)&dFu, sizeof(double) * ifc) != cudaSuccess ||
+        cudaMalloc((void**)&dFd, sizeof(double) * ifc) != cudaSuccess) {
+        cudaFree(dT); cudaFree(dFu); cudaFree(dFd);
+        return fail(HELIOS_ENOMEM, "helios_autotune: scratch allocation failed");
+    }
+    std::vector<double> T0(layers, 1000.0);
+    cudaMemcpy(dT, T0.data(), sizeof(double) * layers, cudaMemcpyHostToDevice);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e30;
+    int best_tb = 1, best_p = 1, rc = HELIOS_OK;
+    const int cands[] = {1, 2, 4, 8, 16, 32};
+    for (int pm = 0; pm <= 1 && rc == HELIOS_OK; ++pm)
+        for (int c : cands) {
+            helios_params_t p = *base;
+            p.bins_per_item = c;
+            p.persistent = pm;
+            helios_plan* plan = nullptr;
+            rc = helios_plan_create(ctx, &sub, tabs, ntab, &p, &plan);
+            if (rc) break;
+            float ms[3];
+            rc = helios_flux_sweep(plan, dT, 0, 0, dFu, dFd, nullptr, ctx->stream);
+            for (int r = 0; r < 3 && rc == HELIOS_OK; ++r) {
+                cudaEventRecord(e0, ctx->stream);
+                rc = helios_flux_sweep(plan, dT, 0, 1, dFu, dFd, nullptr, ctx->stream);
+                cudaEventRecord(e1, ctx->stream);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms[r], e0, e1);
+            }
+            helios_plan_destroy(plan);
+            if (rc) break;
+            std::sort(ms, ms + 3);
+            if (ms[1] < best) { best = ms[1]; best_tb = c; best_p = pm; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dT); cudaFree(dFu); cudaFree(dFd);
+    if (rc) return rc;
+    tuned->bins_per_item = best_tb;
+    tuned->persistent = best_p;
+    cache_store(cache_path, key, best_tb, best_p, best);
+    return HELIOS_OK;
+}

@@ -186,7 +186,7 @@ __device__ __forceinline__ void phi_u_t(float x, float& phi, float& u, float& t)
     } else {
         t = expf(-x);                      // accurate to ~1 ulp for any x (the fast intrinsic's
         u = 1.0f - t;                      // error grows with |x| and compounds through transmissions)
-        phi = __fdividef(u, x);
+        phi = __fdiv_rn(u, x);
     }
 }
 
@@ -257,7 +257,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
 {
     if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source, G = F
         const float a = b.gam * dtau;
-        const float t = __fdividef(1.0f, 1.0f + a);
+        const float t = __frcp_rn(1.0f + a);
         Ts = t;
         Rs = a * t;
         Ss = 0.0f;
@@ -272,9 +272,11 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
         Ss = iso ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
         return;
     }
-    // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha
+    // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha.  Reciprocals and
+    // quotients that enter Ts, Rs and Ss are correctly rounded: the approximate ones round with a
+    // bias that adds up coherently over the layers a reflected flux crosses (1e-5 in scattering bins)
     const float t2u = u * (2.0f - u);                                   // 1 - trans^2
-    const float d = __fdividef(1.0f, fmaf(b.q2, t2u, b.omq2));          // 1 / (1 - q^2 trans^2)
+    const float d = __frcp_rn(fmaf(b.q2, t2u, b.omq2));                 // 1 / (1 - q^2 trans^2), rounded to nearest
     Ts = b.omq2 * tr * d;
     Rs = b.q * t2u * d;
     const float h = d * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);       // (1 - Ts + Rs) / u
@@ -282,17 +284,15 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
 }
 
 // ---------------------------------------------------------------------------
-template <int M, int MINB>
-__global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order,
-                                                         const int* __restrict__ status, int n_passes, int warm_valid,
-                                                         float* __restrict__ Fup_toa)
+// one work item = (atmosphere, tile of bins); the whole block cooperates
+template <int M>
+__device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int* __restrict__ status, int n_passes,
+                                           int warm_valid, float* __restrict__ Fup_toa, unsigned char* smem_raw)
 {
     constexpr int W = 32 * M;               // point slots per column
     constexpr int KST = W + 1;              // row stride of the per-column smem rows
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int G = P.G;
     const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
-    const int item = order[blockIdx.x];
     const int2 it = P.items[item];
     if (status && status[it.x] != 0) return;
     const AtmDesc ad = P.atms[it.x];
@@ -524,6 +524,29 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
     }
     double* part = P.part + ad.part_off + (long long)it.y * 3 * (n + 1);
     for (int t = tid; t < 3 * (n + 1); t += nthreads) part[t] = acc[t];
+}
+
+// counter == nullptr: block b takes item order[b].  Otherwise persistent: the resident
+// blocks pull items (in cost order) from the counter until the group is exhausted.
+template <int M, int MINB>
+__global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
+                                                         int* __restrict__ counter, const int* __restrict__ status,
+                                                         int n_passes, int warm_valid, float* __restrict__ Fup_toa)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (!counter) {
+        sweep_item<M>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        return;
+    }
+    __shared__ int s_next;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int k = s_next;
+        if (k >= count) break;
+        sweep_item<M>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        __syncthreads();                    // shared memory is reused by the next item
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -66,7 +66,7 @@ def test_flux_sweep_pure_absorption_config1():
     _check_toa(toa, r, oracle.Atm.from_workload(wl))
 
 
-@pytest.mark.parametrize("n,L", [(40, 12), (111, 7), (200, 5), (239, 3), (2, 4)])
+@pytest.mark.parametrize("n,L", [(40, 12), (111, 7), (200, 5), (239, 3), (2, 4), (40, 1)])
 def test_flux_sweep_scattering_cold_then_warm(n, L):
     # several lane tiles and a ragged tail (2n+1 not a multiple of 32), five passes,
     # then a second evaluation at new temperatures warm-started from the first
@@ -136,3 +136,13 @@ def test_deterministic_repeat():
     b = plan.flux_sweep(T, n_passes=5)
     for x, y in zip(a, b):
         assert bool((x == y).all())
+
+
+def test_single_gauss_point_and_two_bins():
+    # G = 1 (weight 1) with scattering, the smallest grid the method allows
+    wl = synth.small_scattering(L=2, n=3, G=1)
+    T = synth.perturbed_profile(wl.atms[0], 12)
+    plan = make_plan(wl)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=5)
+    r = _oracle_sweep(wl, 0, T, n_passes=5)
+    _check_fluxes(Fu, Fd, r)

@@ -103,3 +103,56 @@ def test_full_size_converged_profile_matches_stored_oracle_profile():
     assert status.item() == 1
     dT = np.abs(T.cpu().numpy() - golden)
     assert dT.max() < 0.1, (dT.max(), int(np.argmax(dT)))
+
+
+def _small_ragged(ids, max_bins=40):
+    # the batched workload's ragged atmospheres, re-gridded to fewer bins over the same 0.3-200 um range
+    wl = synth.config3(A=len(ids), n_tables=2, atm_ids=ids)
+    for i, a in enumerate(wl.atms):
+        L = min(a.n_bins, max_bins - 3 * i)
+        a.nu_edges = synth.nu_edges(L); a.omega0 = synth.rayleigh_like_omega0(a.nu_edges); a.g0 = a.g0[:L]
+    return wl
+
+
+def test_persistent_and_per_item_launches_agree_bitwise():
+    # ragged layer counts give several lane-chunk groups, which run concurrently on their own streams
+    wl = _small_ragged([1, 5, 9, 33, 70, 111])
+    assert len({(2 * a.n_layers + 1 + 31) // 32 | 1 for a in wl.atms}) >= 2
+    Ts = pack([synth.perturbed_profile(a, i) for i, a in enumerate(wl.atms)])
+    outs = []
+    for pers in (0, 1):
+        p = make_plan(wl, bins_per_item=3, persistent=pers)
+        outs.append([x.clone() for x in p.flux_sweep(Ts, n_passes=5)])
+    for x, y in zip(*outs):
+        assert bool((x == y).all())
+
+
+def test_batched_solve_matches_oracle_per_atmosphere():
+    wl = _small_ragged([2, 40, 77], max_bins=24)
+    plan = make_plan(wl, max_iter=100000)
+    T = pack([a.T_init for a in wl.atms])
+    iters, status = plan.solve_re(T)
+    assert (status.cpu().numpy() == 1).all()
+    got = plan.split_layers(T.cpu().numpy())
+    for a, Tg in zip(wl.atms, got):
+        atm = oracle.Atm(a, wl.tables[a.table_id])
+        st = oracle.State(atm, a.T_init)
+        rc, it, m = oracle.solve_re(atm, st, oracle.params(tol=1e-10, max_iter=200000))
+        assert rc == oracle.CONVERGED
+        assert np.abs(Tg - st.T).max() < 0.1
+
+
+def test_autotune_picks_a_candidate_and_caches_it(tmp_path):
+    import paper_1606_05474_b300 as hp
+    from helpers import ctx
+    import torch
+    wl = _small_ragged([3, 8, 13, 21], max_bins=64)
+    kap = [torch.from_numpy(t.kappa32).cuda() for t in wl.tables]
+    cache = str(tmp_path / "tune.json")
+    p = hp.autotune(ctx(), wl.atms, wl.tables, kap, cache_path=cache)
+    assert p.bins_per_item in (1, 2, 4, 8, 16, 32) and p.persistent in (0, 1)
+    import json
+    d = json.load(open(cache))
+    assert len(d) == 1 and list(d.values())[0]["bins_per_item"] == p.bins_per_item
+    p2 = hp.autotune(ctx(), wl.atms, wl.tables, kap, cache_path=cache)       # cache hit
+    assert (p2.bins_per_item, p2.persistent) == (p.bins_per_item, p.persistent)
