@@ -82,6 +82,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic (read + write) of one sweep-kernel launch on the full-size single atmosphere, from
+# the ncu capture summarised in profiles/sweep_kernel_full_single_atmosphere.md, valid only for the
+# kernel source it was taken on (sha256 prefix of csrc/helios_kernels.cuh); null otherwise.
+SWEEP_TRAFFIC = {"kernels_sha256": "0813cd5cf0ccad41", "bytes_per_launch": 71076352}
+
+
+def kernel_source_hash():
+    import hashlib
+    p = os.path.join(ROOT, "paper_1606_05474_b300", "csrc", "helios_kernels.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
 def algorithmic_counts(wl, n_passes):
     """Algorithmic work of one RE step (see the design notes, roofline section).
 
@@ -233,7 +245,9 @@ def run_gpu(args):
                    "passes_per_step": n_passes, "cells_per_step_per_gpu": cells, "l2": "flushed before every step",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "frac": round(achieved / hbm, 4),
+                     "traffic": (SWEEP_TRAFFIC["bytes_per_launch"]
+                                 if kernel_source_hash() == SWEEP_TRAFFIC["kernels_sha256"] else None),
                      "kernel": "sweep_kernel<7>", "kernel_ms": round(sweep_avg, 5),
                      "algorithmic_bytes": int(alg_bytes), "peak_source": "measured",
                      "fp32_frac": round(fp32 / (sweep_avg * 1e-3) / 1e12 / fp32_peak, 4),
