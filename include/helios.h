@@ -97,6 +97,15 @@ typedef struct {
     const double* nu_edges;
     const float* omega0;
     const float* g0;
+    /* Optional species mixing (Sect. 2.3, eqs. 34-35): when species_off is not NULL,
+     * atmosphere a's opacity is sum_j species_weight[j] * kappa_{species_table[j]}
+     * over j in [species_off[a], species_off[a+1]) (mass mixing ratios times the
+     * species' k-tables, perfectly correlated as in the paper); every table of an
+     * atmosphere must share its (T, P) grid, L and G; at most 16 species.  NULL:
+     * the single table table_id[a] with weight 1. */
+    const int32_t* species_off;     /* [A+1] or NULL */
+    const int32_t* species_table;
+    const double* species_weight;
 } helios_batch_t;
 
 /* Method parameters; helios_default_params fills the paper's values. */
@@ -217,6 +226,31 @@ int helios_temp_update(helios_plan* plan, const double* Fup_bol, const double* F
  *   iters   device int32 [A] (out), status device int32 [A] (out)
  * Returns HELIOS_ENOCONV if any atmosphere ends NOT_CONVERGED or NONFINITE. */
 int helios_solve_re(helios_plan* plan, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t stream);
+
+/* Learned initialiser (Sect. 2.2.3 starts the iteration from an arbitrary
+ * profile; this network supplies a better one).  A multilayer perceptron
+ * n_in -> hidden_layers x n_hidden (SiLU) -> n_out (linear), FP32 master
+ * parameters; every matrix product rounds both operands to BF16 and accumulates
+ * in FP32 on the tensor cores.  Parameter layout (device, float): for each layer
+ * l, W_l [in][out] row-major then b_l [out].  Initial weights are uniform in
+ * +-1/sqrt(fan_in) from `seed`.  Batches hold up to max_batch rows.
+ *   helios_mlp_forward: y[B][n_out] = net(x[B][n_in]) (device arrays)
+ *   helios_mlp_grad: gradient of the mean squared error mean((net(x) - target)^2)
+ *     into the internal gradient buffer (readable through helios_mlp_params);
+ *     loss (device float, may be NULL)
+ *   helios_mlp_adam: one Adam step (bias-corrected) on the parameters
+ *   helios_mlp_train_step: grad + Adam(lr, 0.9, 0.999, 1e-8)
+ * All calls are asynchronous on `stream`; reductions have a fixed order. */
+typedef struct helios_mlp helios_mlp;
+int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers, int n_out,
+                      unsigned long long seed, int max_batch, helios_mlp** mlp);
+int helios_mlp_destroy(helios_mlp* mlp);
+int helios_mlp_params(helios_mlp* mlp, float** params, float** grads, long long* count);
+int helios_mlp_forward(helios_mlp* mlp, const float* x, float* y, int B, cudaStream_t stream);
+int helios_mlp_grad(helios_mlp* mlp, const float* x, const float* target, int B, float* loss, cudaStream_t stream);
+int helios_mlp_adam(helios_mlp* mlp, float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+int helios_mlp_train_step(helios_mlp* mlp, const float* x, const float* target, int B, float lr, float* loss,
+                          cudaStream_t stream);
 
 /* Autotuner (measurement support; the paper has no counterpart): picks the work
  * item size (bins_per_item) and launch mode (persistent) for a batch by timing

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (ATM_ACTIVE, ATM_CONVERGED, ATM_NONFINITE, ATM_NOT_CONVERGED, HeliosError,  # noqa: F401
                    check)
 
-__all__ = ["Context", "Plan", "default_params", "autotune", "flux_sweep_noalloc", "HeliosError", "build"]
+__all__ = ["Context", "Plan", "MLP", "default_params", "autotune", "flux_sweep_noalloc", "HeliosError", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -123,6 +123,13 @@ def _marshal(atms, tables, kappa):
         "omega0": np.ascontiguousarray(np.concatenate([np.asarray(a.omega0, np.float32) for a in atms])),
         "g0": np.ascontiguousarray(np.concatenate([np.asarray(a.g0, np.float32) for a in atms])),
     }
+    if any(getattr(a, "species", None) for a in atms):
+        # eq. (34) mixing: (table, mass mixing ratio) pairs per atmosphere; plain atmospheres
+        # contribute their own table with weight 1
+        pairs = [list(a.species) if getattr(a, "species", None) else [(a.table_id, 1.0)] for a in atms]
+        host["species_off"] = np.concatenate([[0], np.cumsum([len(p) for p in pairs])]).astype(np.int32)
+        host["species_table"] = np.array([t for p in pairs for t, _ in p], dtype=np.int32)
+        host["species_weight"] = np.array([w for p in pairs for _, w in p], dtype=np.float64)
     b = _lib.Batch()
     b.A = len(atms)
     for k, v in host.items():
@@ -276,3 +283,69 @@ class Plan:
 
     def split_bins(self, x):
         return [x[self.bin_off[a]:self.bin_off[a + 1]] for a in range(self.A)]
+
+
+class _DeviceView:
+    """__cuda_array_interface__ over library-owned device memory (no copy, no allocation)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f4", "data": (int(ptr), False), "version": 3}
+
+
+class MLP:
+    """The learned initialiser's network (helios_mlp_*): n_in -> hidden_layers x n_hidden (SiLU) -> n_out."""
+
+    def __init__(self, ctx: Context, n_in=6, n_hidden=256, hidden_layers=3, n_out=100, seed=0, max_batch=4096):
+        torch = _torch()
+        self.ctx, self.lib = ctx, ctx.lib
+        self.dims = [n_in] + [n_hidden] * hidden_layers + [n_out]
+        self.max_batch = max_batch
+        h = ctypes.c_void_p()
+        check(self.lib.helios_mlp_create(ctx.h, n_in, n_hidden, hidden_layers, n_out, seed, max_batch, ctypes.byref(h)))
+        self.h = h
+        p, g, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_longlong()
+        check(self.lib.helios_mlp_params(h, ctypes.byref(p), ctypes.byref(g), ctypes.byref(n)))
+        dev = torch.device("cuda", ctx.device)
+        self.params = torch.as_tensor(_DeviceView(p.value, n.value), device=dev)
+        self.grads = torch.as_tensor(_DeviceView(g.value, n.value), device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.helios_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layer_views(self):
+        """[(W_l [in, out], b_l [out])] views into the parameter buffer."""
+        out, o = [], 0
+        for a, b in zip(self.dims[:-1], self.dims[1:]):
+            W = self.params[o:o + a * b].view(a, b); o += a * b
+            bb = self.params[o:o + b]; o += b
+            out.append((W, bb))
+        return out
+
+    def forward(self, x, out=None, stream=None):
+        torch = _torch()
+        x = x.contiguous()
+        y = out if out is not None else torch.empty(x.shape[0], self.dims[-1], dtype=torch.float32, device=x.device)
+        check(self.lib.helios_mlp_forward(self.h, x.data_ptr(), y.data_ptr(), x.shape[0], _stream_ptr(stream)))
+        return y
+
+    def grad(self, x, target, stream=None):
+        check(self.lib.helios_mlp_grad(self.h, x.contiguous().data_ptr(), target.contiguous().data_ptr(), x.shape[0],
+                                       self.loss.data_ptr(), _stream_ptr(stream)))
+        return self.loss
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        check(self.lib.helios_mlp_adam(self.h, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+    def train_step(self, x, target, lr=1e-3, stream=None):
+        check(self.lib.helios_mlp_train_step(self.h, x.contiguous().data_ptr(), target.contiguous().data_ptr(),
+                                             x.shape[0], lr, self.loss.data_ptr(), _stream_ptr(stream)))
+        return self.loss

@@ -23,7 +23,8 @@ class Batch(ctypes.Structure):
     _fields_ = [("A", c_int), ("n_layers", c_void_p), ("n_bins", c_void_p), ("table_id", c_void_p),
                 ("P_top_bar", c_void_p), ("P_bot_bar", c_void_p), ("grav", c_void_p), ("T_irr", c_void_p),
                 ("T_int", c_void_p), ("T_star", c_void_p), ("nu_edges", c_void_p), ("omega0", c_void_p),
-                ("g0", c_void_p)]
+                ("g0", c_void_p), ("species_off", c_void_p), ("species_table", c_void_p),
+                ("species_weight", c_void_p)]
 
 
 class Params(ctypes.Structure):
@@ -43,7 +44,8 @@ EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "heli
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
            "helios_flux_sweep", "helios_temp_update", "helios_solve_re", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
-           "helios_autotune"]
+           "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_forward",
+           "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step"]
 
 _lib = None
 
@@ -75,6 +77,13 @@ def load(path: str = SO_PATH):
     lib.helios_plan_last_sweep_ms.argtypes = [vp, P(ctypes.c_float)]
     lib.helios_plan_sweep_times.argtypes = [vp, vp, c_int, P(c_int)]
     lib.helios_autotune.argtypes = [vp, P(Batch), P(KTable), c_int, P(Params), ctypes.c_char_p, P(Params)]
+    lib.helios_mlp_create.argtypes = [vp, c_int, c_int, c_int, c_int, ctypes.c_ulonglong, c_int, P(vp)]
+    lib.helios_mlp_destroy.argtypes = [vp]
+    lib.helios_mlp_params.argtypes = [vp, P(vp), P(vp), P(ctypes.c_longlong)]
+    lib.helios_mlp_forward.argtypes = [vp, vp, vp, c_int, vp]
+    lib.helios_mlp_grad.argtypes = [vp, vp, vp, c_int, vp, vp]
+    lib.helios_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
+    lib.helios_mlp_train_step.argtypes = [vp, vp, vp, c_int, ctypes.c_float, vp, vp]
     lib.helios_flux_sweep_noalloc.argtypes = [P(Batch), P(KTable), P(Params), vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("helios_default_params", "helios_version", "helios_last_error"):

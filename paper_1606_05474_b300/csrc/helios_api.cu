@@ -179,6 +179,8 @@ struct helios_plan {
     cudaEvent_t ev_sweep0, ev_sweep1;   // the pair used by the current evaluation
 };
 
+__attribute__((visibility("hidden"))) int helios_ctx_device(const helios_ctx* c) { return c->device; }
+
 extern "C" {
 
 void helios_default_params(helios_params_t* p)
@@ -329,6 +331,29 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         AtmDesc& d = ad[a];
         std::memset(&d, 0, sizeof d);
         d.n = n; d.L = L; d.M = lane_chunk(n); d.tab = t;
+        if (b->species_off) {
+            const int s0 = b->species_off[a], s1 = b->species_off[a + 1];
+            if (!b->species_table || !b->species_weight || s1 < s0 || s1 - s0 > 16 || s0 < 0) {
+                delete P;
+                return fail(HELIOS_EINVAL, "atmosphere %d: invalid species range", a);
+            }
+            for (int j = s0; j < s1; ++j) {
+                const int tj = b->species_table[j];
+                const double wj = b->species_weight[j];
+                if (tj < 0 || tj >= ntab || !(wj >= 0.0) || !std::isfinite(wj)) {
+                    delete P;
+                    return fail(HELIOS_EINVAL, "atmosphere %d: species %d table %d weight %g invalid", a, j, tj, wj);
+                }
+                const helios_ktable_t &k0 = tabs[t], &kj = tabs[tj];
+                if (kj.nP != k0.nP || kj.nT != k0.nT || kj.L != k0.L || kj.G != k0.G || kj.log10P0 != k0.log10P0 ||
+                    kj.dlog10P != k0.dlog10P || kj.T0 != k0.T0 || kj.dT != k0.dT) {
+                    delete P;
+                    return fail(HELIOS_EINVAL, "atmosphere %d: species table %d does not share table %d's grid", a, tj, t);
+                }
+            }
+            d.n_spec = s1 - s0;
+            d.spec_off = s0;
+        }
         d.lay_off = (int)lay; d.if_off = (int)ifc; d.pt_off = (int)pts; d.sub_off = (int)sub; d.bin_off = (int)bins;
         lay += n; ifc += n + 1; pts += 2 * n + 1; sub += 2 * n; bins += L; nu_off += L + 1;
     }
@@ -479,7 +504,15 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     PlanDev& dv = P->dev;
     std::memset(&dv, 0, sizeof dv);
     AtmDesc* d_atm; TabDesc* d_tab; BinConst* d_bc; int2* d_items; int* d_order; float* d_gw;
-    int* d_iP; double* d_wP; float* d_dm; double* d_lnr; int* d_lay_atm;
+    int* d_iP; double* d_wP; float* d_dm; double* d_lnr; int* d_lay_atm; int* d_spec_tab; float* d_spec_w;
+    std::vector<int> spec_tab;
+    std::vector<float> spec_w;
+    if (b->species_off) {
+        for (int j = 0; j < b->species_off[A]; ++j) {
+            spec_tab.push_back(b->species_table[j]);
+            spec_w.push_back((float)b->species_weight[j]);
+        }
+    }
 #define ALLOC(ptr, cnt)                                              \
     do {                                                             \
         if ((rc = dev_alloc(&ptr, (cnt), tot)) != HELIOS_OK) {       \
@@ -490,7 +523,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     } while (0)
     ALLOC(d_atm, A); ALLOC(d_tab, ntab); ALLOC(d_bc, bins); ALLOC(d_items, items.size());
     ALLOC(d_order, items.size()); ALLOC(d_gw, G); ALLOC(d_iP, pts); ALLOC(d_wP, pts); ALLOC(d_dm, sub);
-    ALLOC(d_lnr, lay); ALLOC(d_lay_atm, lay);
+    ALLOC(d_lnr, lay); ALLOC(d_lay_atm, lay); ALLOC(d_spec_tab, spec_tab.size()); ALLOC(d_spec_w, spec_w.size());
     ALLOC(dv.row, pts); ALLOC(dv.wq, pts); ALLOC(dv.metric_bits, A);
     ALLOC(dv.Tpt, pts); ALLOC(dv.iT, pts); ALLOC(dv.wT, pts); ALLOC(dv.invT, pts); ALLOC(dv.Tf, pts);
     ALLOC(dv.invT_old, pts); ALLOC(dv.dinv_step, pts); ALLOC(dv.dT_step, pts);
@@ -531,7 +564,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     if ((rc = upload(d_atm, ad)) || (rc = upload(d_tab, td)) || (rc = upload(d_bc, bc)) ||
         (rc = upload(d_items, items)) || (rc = upload(d_order, order)) || (rc = upload(d_gw, gw)) ||
         (rc = upload(d_iP, iP)) || (rc = upload(d_wP, wP)) || (rc = upload(d_dm, dm)) || (rc = upload(d_lnr, lnr)) ||
-        (rc = upload(d_lay_atm, lay_atm))) {
+        (rc = upload(d_lay_atm, lay_atm)) || (rc = upload(d_spec_tab, spec_tab)) || (rc = upload(d_spec_w, spec_w))) {
         helios_plan_destroy(P);
         return rc;
     }
@@ -539,6 +572,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     if (ce != cudaSuccess) { helios_plan_destroy(P); return fail(HELIOS_ECUDA, "cudaMemset: %s", cudaGetErrorString(ce)); }
     dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.gw = d_gw;
     dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
+    dv.spec_tab = d_spec_tab; dv.spec_w = d_spec_w;
     dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso;
     P->atms_h = ad;
     P->ws_bytes = (int64_t)tot;
@@ -931,6 +965,7 @@ extern "C" int helios_autotune(helios_ctx* ctx, const helios_batch_t* b, const h
     sub.A = (int)n.size(); sub.n_layers = n.data(); sub.n_bins = L.data(); sub.table_id = tid.data();
     sub.P_top_bar = Pt.data(); sub.P_bot_bar = Pb.data(); sub.grav = gr.data(); sub.T_irr = Ti.data();
     sub.T_int = Tn.data(); sub.T_star = Ts.data(); sub.nu_edges = nu.data(); sub.omega0 = w0.data(); sub.g0 = g0.data();
+    sub.species_off = nullptr; sub.species_table = nullptr; sub.species_weight = nullptr;   // timing only
     double *dT = nullptr, *dFu = nullptr, *dFd = nullptr;
     int64_t ifc = layers + sub.A;
     if (cudaMalloc((void**)&dT, sizeof(double) * layers) != cudaSuccess ||

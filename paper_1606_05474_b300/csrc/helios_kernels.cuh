@@ -61,7 +61,8 @@ struct BinConst {
 struct AtmDesc {
     int n, L, M, tab;
     int lay_off, if_off, pt_off, sub_off;
-    int bin_off, item_off, n_items, pad;
+    int bin_off, item_off, n_items, n_spec;   // n_spec > 1: opacity mixed from several tables
+    int spec_off, pad0, pad1, pad2;
     long long warm_off;     // float offset of this atmosphere's warm-start block
     long long part_off;     // double offset of this atmosphere's partial sums
 };
@@ -87,6 +88,8 @@ struct PlanDev {
     const float* dm;            // [sublayers]  column mass (g cm^-2)
     const double* lnr;          // [layers]  ln(P_int,i / P_int,i+1)
     const int* lay_atm;         // [layers] atmosphere of each layer
+    const int* spec_tab;        // species tables of mixed-opacity atmospheres (eq. 34)
+    const float* spec_w;        // their mass mixing ratios (eq. 35)
     // per-evaluation state written by prep_kernel
     double* Tpt;                // [points] temperature at the point in the previous evaluation
     int* iT;                    // [points]
@@ -369,7 +372,20 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             dbt[p] = d;
         }
         // ... and the opacity gather, consecutive threads on consecutive g
-        if (vec4) {
+        if (ad.n_spec > 1) {
+            // eq. (34): kappa = sum_j X_j kappa_j over species tables sharing the (T, P) grid, so
+            // the corner offsets and weights of a point serve every species
+            const int lg = l * G + g_of;
+            for (int p = p_first; p < NP; p += p_stride) {
+                const int q = ad.pt_off + p;
+                const int row = P.row[q];
+                const float4 w = P.wq[q];
+                float k = 0.0f;
+                for (int j = 0; j < ad.n_spec; ++j)
+                    k = fmaf(P.spec_w[ad.spec_off + j], kappa_at(P.tabs[P.spec_tab[ad.spec_off + j]].kappa, td, row, w, lg), k);
+                kap[g_of * KST + p] = k;
+            }
+        } else if (vec4) {
             const int lg = l * G + 4 * g4_of;
             for (int p = p4_first; p < NP; p += p4_stride) {
                 const int q = ad.pt_off + p;
@@ -689,7 +705,18 @@ __global__ void interp_kernel(PlanDev P, const double* __restrict__ T_layer, int
         float4 wq;
         table_coord(point_T(T, n, p), td.T0, td.dT, td.nT, it, wt);
         point_corners(td, P.iP[q], P.wP[q], it, wt, row, wq);
-        if (kappa_out) kappa_out[kap_off + f] = kappa_at(td.kappa, td, row, wq, l * P.G + g);
+        if (kappa_out) {
+            float k;
+            if (ad.n_spec > 1) {
+                k = 0.0f;
+                for (int j = 0; j < ad.n_spec; ++j)
+                    k = fmaf(P.spec_w[ad.spec_off + j], kappa_at(P.tabs[P.spec_tab[ad.spec_off + j]].kappa, td, row, wq,
+                                                                 l * P.G + g), k);
+            } else {
+                k = kappa_at(td.kappa, td, row, wq, l * P.G + g);
+            }
+            kappa_out[kap_off + f] = k;
+        }
         if (l == 0 && g == 0) {
             if (idx_out) { idx_out[2 * q] = P.iP[q]; idx_out[2 * q + 1] = it; }
             if (w_out) { w_out[2 * q] = P.wP[q]; w_out[2 * q + 1] = wt; }

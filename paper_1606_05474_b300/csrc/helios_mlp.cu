@@ -1,0 +1,424 @@
+// Learned initialiser: a small multilayer perceptron trained on the solver's own
+// radiative-equilibrium solutions (the paper starts the iteration from an arbitrary
+// profile, Sect. 2.2.3; a better start saves iterations).
+//
+// Layers: n_in -> hidden x n_hidden_layers (SiLU) -> n_out (linear).  Parameters are
+// FP32 master copies; every matrix product rounds both operands to BF16 and accumulates in
+// FP32 on the tensor cores (warp-level mma.sync m16n8k16).  Training minimises the mean
+// squared error with Adam.  All reductions have a fixed order (deterministic).
+#include "helios.h"
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+__attribute__((visibility("hidden"))) void helios_set_error_text(const char* msg);
+__attribute__((visibility("hidden"))) int helios_ctx_device(const helios_ctx* ctx);
+
+namespace {
+
+int mfail(int code, const char* fmt, ...)
+{
+    char msg[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof msg, fmt, ap);
+    va_end(ap);
+    helios_set_error_text(msg);
+    return code;
+}
+
+#define MLP_CUDA(call)                                                                                \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return mfail(HELIOS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr int kMaxLayers = 8;
+enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_SILU = 2, EPI_DSILU = 3 };
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// C[M x N] = op(A)[M x K] op(B)[K x N] with both operands rounded to BF16, FP32 accumulation.
+// op(A)[m][k] = TA ? A[k*lda + m] : A[m*lda + k];  op(B)[k][n] = TB ? B[n*ldb + k] : B[k*ldb + n].
+// Block tile 64 x 64 (4 warps of 32 x 32), K step 32; epilogue fused.
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(128) mlp_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+                                                const float* __restrict__ bias, float* __restrict__ Zout,
+                                                const float* __restrict__ Zin, int ldz, float scale)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[64][40];     // [m][k], row stride 80 B: conflict-free fragments
+    __shared__ __align__(16) __nv_bfloat16 Bs[64][40];     // [n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gid = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
+
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        for (int e = tid; e < 64 * 32; e += 128) {
+            int r, c;
+            if (!TA) { r = e >> 5; c = e & 31; } else { c = e >> 6; r = e & 63; }
+            const int gm = m0 + r, gk = k0 + c;
+            float v = 0.0f;
+            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            As[r][c] = __float2bfloat16_rn(v);
+        }
+        for (int e = tid; e < 64 * 32; e += 128) {
+            int r, c;       // r: n offset, c: k offset
+            if (!TB) { c = e >> 6; r = e & 63; } else { r = e >> 5; c = e & 31; }
+            const int gn = n0 + r, gk = k0 + c;
+            float v = 0.0f;
+            if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
+            Bs[r][c] = __float2bfloat16_rn(v);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + gid;
+                a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + tq * 2]);
+                a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + tq * 2]);
+                a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + tq * 2 + 8]);
+                a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + tq * 2 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + gid;
+                b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + tq * 2]);
+                b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + tq * 2 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float* d = acc[i][j];
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int m = m0 + wm + i * 16 + gid + h * 8, n = n0 + wn + j * 8 + tq * 2 + c2;
+                    if (m >= M || n >= N) continue;
+                    const float v = acc[i][j][h * 2 + c2];
+                    float out;
+                    if (EPI == EPI_STORE) {
+                        out = scale * v;
+                    } else if (EPI == EPI_BIAS) {
+                        out = v + bias[n];
+                    } else if (EPI == EPI_BIAS_SILU) {
+                        const float z = v + bias[n];
+                        Zout[(size_t)m * ldz + n] = z;
+                        out = z * sigmoidf_(z);
+                    } else {
+                        const float z = Zin[(size_t)m * ldz + n], s = sigmoidf_(z);
+                        out = v * s * fmaf(z, 1.0f - s, 1.0f);      // d SiLU / dz
+                    }
+                    C[(size_t)m * ldc + n] = out;
+                }
+}
+
+// dOut = 2 (Y - T) / (B * N); per-block partial sums of the squared error (fixed order)
+__global__ void mse_kernel(const float* __restrict__ Y, const float* __restrict__ T, float* __restrict__ dY,
+                           long long count, float scale, double* __restrict__ part)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        const float d = Y[i] - T[i];
+        dY[i] = 2.0f * scale * d;
+        s += (double)d * (double)d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_kernel(const double* __restrict__ part, int n, double scale, float* __restrict__ loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *loss = (float)(s * scale);
+    }
+}
+
+// db[n] = sum_m dZ[m][n] (thread per column, fixed order)
+__global__ void colsum_kernel(const float* __restrict__ dZ, int M, int N, float* __restrict__ db)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.0f;
+    for (int m = 0; m < M; ++m) s += dZ[(size_t)m * N + n];
+    db[n] = s;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct helios_mlp {
+    helios_ctx* ctx;
+    int device;
+    int nl;                  // linear layers
+    int dims[kMaxLayers + 1];
+    int64_t woff[kMaxLayers], boff[kMaxLayers], n_params;
+    int max_B;
+    float *p, *g, *m, *v;
+    float* act;              // per layer: Z (hidden layers) and Y, max_B rows
+    float *dA, *dB;          // backprop ping-pong buffers
+    float* dout;
+    double* part;
+    int64_t t;               // Adam step count
+    std::vector<void*> allocs;
+};
+
+extern "C" {
+
+int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers, int n_out,
+                      unsigned long long seed, int max_batch, helios_mlp** out)
+{
+    if (!out || !ctx) return mfail(HELIOS_EINVAL, "helios_mlp_create: null argument");
+    *out = nullptr;
+    const int device = helios_ctx_device(ctx);
+    if (n_in < 1 || n_hidden < 1 || n_out < 1 || hidden_layers < 1 || hidden_layers + 1 > kMaxLayers || max_batch < 1)
+        return mfail(HELIOS_EINVAL, "helios_mlp_create: invalid shape");
+    MLP_CUDA(cudaSetDevice(device));
+    helios_mlp* m = new helios_mlp();
+    m->ctx = ctx;
+    m->device = device;
+    m->nl = hidden_layers + 1;
+    m->dims[0] = n_in;
+    for (int i = 1; i <= hidden_layers; ++i) m->dims[i] = n_hidden;
+    m->dims[m->nl] = n_out;
+    int64_t off = 0;
+    for (int l = 0; l < m->nl; ++l) {
+        m->woff[l] = off;
+        off += (int64_t)m->dims[l] * m->dims[l + 1];
+        m->boff[l] = off;
+        off += m->dims[l + 1];
+    }
+    m->n_params = off;
+    m->max_B = max_batch;
+    // initial weights: uniform in +-1/sqrt(fan_in) from a counter-based generator
+    std::vector<float> h(off);
+    const uint64_t key = mix64(seed ^ 0x6d6c7000ULL);
+    for (int l = 0; l < m->nl; ++l) {
+        const double bound = 1.0 / std::sqrt((double)m->dims[l]);
+        for (int64_t i = m->woff[l]; i < m->boff[l] + m->dims[l + 1]; ++i) {
+            const double u = (double)(mix64(key + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL) >> 11) * 0x1.0p-53;
+            h[i] = (float)((2.0 * u - 1.0) * bound);
+        }
+    }
+    size_t act_floats = 0;
+    for (int l = 0; l < m->nl; ++l) act_floats += (size_t)2 * max_batch * m->dims[l + 1];
+    int widest = 0;
+    for (int l = 0; l <= m->nl; ++l) widest = std::max(widest, m->dims[l]);
+    float** bufs[] = {&m->p, &m->g, &m->m, &m->v};
+    for (float** b : bufs) {
+        if (cudaMalloc((void**)b, sizeof(float) * off) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp params"); }
+        m->allocs.push_back(*b);
+    }
+    if (cudaMalloc((void**)&m->act, sizeof(float) * act_floats) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp activations"); }
+    m->allocs.push_back(m->act);
+    const size_t wide = (size_t)max_batch * widest;
+    if (cudaMalloc((void**)&m->dA, sizeof(float) * wide) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp grads"); }
+    m->allocs.push_back(m->dA);
+    if (cudaMalloc((void**)&m->dB, sizeof(float) * wide) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp grads"); }
+    m->allocs.push_back(m->dB);
+    if (cudaMalloc((void**)&m->dout, sizeof(float) * (size_t)max_batch * n_out) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp out"); }
+    m->allocs.push_back(m->dout);
+    if (cudaMalloc((void**)&m->part, sizeof(double) * 1024) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp loss"); }
+    m->allocs.push_back(m->part);
+    MLP_CUDA(cudaMemcpy(m->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice));
+    MLP_CUDA(cudaMemset(m->m, 0, sizeof(float) * off));
+    MLP_CUDA(cudaMemset(m->v, 0, sizeof(float) * off));
+    MLP_CUDA(cudaMemset(m->g, 0, sizeof(float) * off));
+    m->t = 0;
+    *out = m;
+    return HELIOS_OK;
+}
+
+int helios_mlp_destroy(helios_mlp* m)
+{
+    if (!m) return HELIOS_OK;
+    cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    for (void* a : m->allocs) cudaFree(a);
+    delete m;
+    return HELIOS_OK;
+}
+
+int helios_mlp_params(helios_mlp* m, float** params, float** grads, long long* count)
+{
+    if (!m || !params || !count) return mfail(HELIOS_EINVAL, "helios_mlp_params: null argument");
+    *params = m->p;
+    if (grads) *grads = m->g;
+    *count = m->n_params;
+    return HELIOS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+float* Zbuf(helios_mlp* m, int l) { size_t o = 0; for (int k = 0; k < l; ++k) o += (size_t)2 * m->max_B * m->dims[k + 1]; return m->act + o; }
+float* Ybuf(helios_mlp* m, int l) { return Zbuf(m, l) + (size_t)m->max_B * m->dims[l + 1]; }
+
+template <bool TA, bool TB, int EPI>
+int gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, const float* bias,
+         float* Zout, const float* Zin, int ldz, float scale, cudaStream_t s)
+{
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    mlp_gemm<TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Zout, Zin, ldz, scale);
+    MLP_CUDA(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+// forward pass; hidden activations kept for the backward pass; output to `y`
+int forward(helios_mlp* m, const float* x, float* y, int B, cudaStream_t s)
+{
+    const float* in = x;
+    for (int l = 0; l < m->nl; ++l) {
+        const int K = m->dims[l], N = m->dims[l + 1];
+        const float* W = m->p + m->woff[l];
+        const float* b = m->p + m->boff[l];
+        int rc;
+        if (l + 1 < m->nl)
+            rc = gemm<false, false, EPI_BIAS_SILU>(B, N, K, in, K, W, N, Ybuf(m, l), N, b, Zbuf(m, l), nullptr, N, 1.0f, s);
+        else
+            rc = gemm<false, false, EPI_BIAS>(B, N, K, in, K, W, N, y, N, b, nullptr, nullptr, N, 1.0f, s);
+        if (rc) return rc;
+        in = Ybuf(m, l);
+    }
+    return HELIOS_OK;
+}
+
+// gradients of the mean squared error into m->g; loss (float, device) if requested
+int backward(helios_mlp* m, const float* x, const float* target, int B, float* loss, cudaStream_t s)
+{
+    const int nout = m->dims[m->nl];
+    int rc = forward(m, x, m->dout, B, s);
+    if (rc) return rc;
+    const long long count = (long long)B * nout;
+    const int blocks = (int)std::min<long long>(1024, (count + 255) / 256);
+    mse_kernel<<<blocks, 256, 0, s>>>(m->dout, target, m->dA, count, 1.0f / (float)count, m->part);
+    MLP_CUDA(cudaGetLastError());
+    if (loss) {
+        loss_kernel<<<1, 32, 0, s>>>(m->part, blocks, 1.0 / (double)count, loss);
+        MLP_CUDA(cudaGetLastError());
+    }
+    float* dcur = m->dA;      // dL/dZ of layer l (for the last layer: dL/dOut)
+    float* dnext = m->dB;
+    for (int l = m->nl - 1; l >= 0; --l) {
+        const int K = m->dims[l], N = m->dims[l + 1];
+        const float* inp = l ? Ybuf(m, l - 1) : x;
+        // dW_l = in^T dZ_l, db_l = colsum dZ_l
+        rc = gemm<true, false, EPI_STORE>(K, N, B, inp, K, dcur, N, m->g + m->woff[l], N, nullptr, nullptr, nullptr, 0,
+                                          1.0f, s);
+        if (rc) return rc;
+        colsum_kernel<<<(N + 127) / 128, 128, 0, s>>>(dcur, B, N, m->g + m->boff[l]);
+        MLP_CUDA(cudaGetLastError());
+        if (l > 0) {
+            // dZ_{l-1} = (dZ_l W_l^T) * SiLU'(Z_{l-1})
+            rc = gemm<false, true, EPI_DSILU>(B, K, N, dcur, N, m->p + m->woff[l], N, dnext, K, nullptr, nullptr,
+                                              Zbuf(m, l - 1), K, 1.0f, s);
+            if (rc) return rc;
+            std::swap(dcur, dnext);
+        }
+    }
+    return HELIOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int helios_mlp_forward(helios_mlp* m, const float* x, float* y, int B, cudaStream_t s)
+{
+    if (!m || !x || !y) return mfail(HELIOS_EINVAL, "helios_mlp_forward: null argument");
+    if (B < 1 || B > m->max_B) return mfail(HELIOS_EINVAL, "helios_mlp_forward: batch %d outside [1, %d]", B, m->max_B);
+    MLP_CUDA(cudaSetDevice(m->device));
+    return forward(m, x, y, B, s);
+}
+
+int helios_mlp_grad(helios_mlp* m, const float* x, const float* target, int B, float* loss, cudaStream_t s)
+{
+    if (!m || !x || !target) return mfail(HELIOS_EINVAL, "helios_mlp_grad: null argument");
+    if (B < 1 || B > m->max_B) return mfail(HELIOS_EINVAL, "helios_mlp_grad: batch %d outside [1, %d]", B, m->max_B);
+    MLP_CUDA(cudaSetDevice(m->device));
+    return backward(m, x, target, B, loss, s);
+}
+
+int helios_mlp_adam(helios_mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s)
+{
+    if (!m) return mfail(HELIOS_EINVAL, "helios_mlp_adam: null argument");
+    MLP_CUDA(cudaSetDevice(m->device));
+    m->t += 1;
+    const float c1 = (float)(1.0 - std::pow((double)beta1, (double)m->t));
+    const float c2 = (float)(1.0 - std::pow((double)beta2, (double)m->t));
+    adam_kernel<<<256, 256, 0, s>>>(m->p, m->g, m->m, m->v, m->n_params, lr, beta1, beta2, eps, c1, c2);
+    MLP_CUDA(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+int helios_mlp_train_step(helios_mlp* m, const float* x, const float* target, int B, float lr, float* loss,
+                          cudaStream_t s)
+{
+    int rc = helios_mlp_grad(m, x, target, B, loss, s);
+    if (rc) return rc;
+    return helios_mlp_adam(m, lr, 0.9f, 0.999f, 1e-8f, s);
+}
+
+}  // extern "C"

@@ -141,6 +141,8 @@ class Atmosphere:
     g0: np.ndarray       # float32 [L]
     table_id: int
     T_init: np.ndarray   # float64 [n_layers], bottom layer first
+    species: Optional[list] = None   # [(table index, mass mixing ratio)] to mix tables, or None
+    params: Optional[dict] = None    # generator parameters (for the learned initialiser's features)
 
     @property
     def n_bins(self) -> int:
@@ -309,3 +311,46 @@ def grey_two_band(n: int = 50, gamma: float = 0.25, kappa_th: float = 1e-2, T_ir
                      table_id=0, T_init=np.full(n, 1000.0))
     return Workload(name=f"grey-two-band-{n}", atms=[atm], tables=[tab], n_scat=0, grey=True,
                     meta={"gamma": gamma, "kappa_th": kappa_th})
+
+
+def learned_dataset(n_samples: int, L: int = 300, n: int = 100, first: int = 0) -> Workload:
+    """Planet parameters for the learned initialiser, on the full-size atmosphere's geometry
+    (100 layers, 1e-6..1e3 bar, 20 g, Rayleigh-like scattering) with L bins.
+
+    Per sample: T_irr ~ U[500, 3000] K, T_int ~ U[50, 400] K, log10(g / m s^-2) ~ U[0.5, 1.5],
+    [M/H] ~ U[-1, 1], C/O ~ U[0.3, 1.5].  The opacity mixes two seeded tables A and B:
+    kappa = 10^[M/H] (kappa_A/(1 + C/O) + kappa_B (C/O)/(1 + C/O)) -- a synthetic stand-in
+    (not a chemistry model) that makes [M/H] and C/O matter.  Start: isothermal at T_irr."""
+    seed = SEED_BASE + 4
+    G = 20
+    tabA = make_ktable(seed, 0, L, G, -6.0, 3.0)
+    tabB = make_ktable(seed, 1, L, G, -6.0, 3.0)
+    e = nu_edges(L)
+    w0 = rayleigh_like_omega0(e)
+    g0 = (0.5 * uniform(stream_key(seed, STREAM_G0), 0, L)).astype(np.float32)
+    meanA, meanB = float(tabA.kappa32.astype(np.float64).mean()), float(tabB.kappa32.astype(np.float64).mean())
+    key = stream_key(seed, STREAM_MIX)
+    atms = []
+    for i in range(first, first + n_samples):
+        u = uniform(key, 8 * i, 8)
+        T_irr = 500.0 + 2500.0 * u[0]
+        T_int = 50.0 + 350.0 * u[1]
+        lg = 0.5 + u[2]
+        mh = -1.0 + 2.0 * u[3]
+        co = 0.3 + 1.2 * u[4]
+        cA = 10.0 ** mh / (1.0 + co)
+        cB = 10.0 ** mh * co / (1.0 + co)
+        atms.append(Atmosphere(n_layers=n, P_top_bar=1e-6, P_bot_bar=1e3, grav=100.0 * 10.0 ** lg, T_irr=T_irr,
+                               T_int=T_int, T_star=5000.0, nu_edges=e, omega0=w0, g0=g0, table_id=0,
+                               T_init=np.full(n, T_irr), species=[(0, cA), (1, cB)],
+                               params={"T_irr": T_irr, "T_int": T_int, "log10g": lg, "MH": mh, "CO": co,
+                                       "log10_mean_kappa": float(np.log10(cA * meanA + cB * meanB))}))
+    return Workload(name=f"learned-{n_samples}x{n}x{L}x{G}", atms=atms, tables=[tabA, tabB], n_scat=4)
+
+
+def mixed_table64(wl: Workload, atm: Atmosphere) -> np.ndarray:
+    """The element-wise mixed table of a species-mixing atmosphere, float64 (for the oracle)."""
+    k = np.zeros(wl.tables[0].kappa32.shape)
+    for t, w in atm.species:
+        k += w * wl.tables[t].kappa32.astype(np.float64)
+    return k

@@ -146,3 +146,17 @@ def test_single_gauss_point_and_two_bins():
     Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=5)
     r = _oracle_sweep(wl, 0, T, n_passes=5)
     _check_fluxes(Fu, Fd, r)
+
+
+def test_species_mixing_matches_mixed_table():
+    # eq. (34): the opacity of a mixed atmosphere is the weighted sum of its species' tables;
+    # bilinear interpolation is linear, so the oracle interpolates the element-wise mixed table
+    wl = synth.learned_dataset(3, L=40, n=60)
+    plan = make_plan(wl)
+    Ts = [synth.perturbed_profile(a, 30 + i) for i, a in enumerate(wl.atms)]
+    Fu, Fd, toa = plan.flux_sweep(pack(Ts), n_passes=5)
+    Fus, Fds = plan.split_interfaces(Fu.cpu().numpy()), plan.split_interfaces(Fd.cpu().numpy())
+    for i, a in enumerate(wl.atms):
+        atm = oracle.Atm(a, wl.tables[0], kappa64=synth.mixed_table64(wl, a))
+        r = oracle.flux_sweep(atm, Ts[i], n_passes=5)
+        assert rel_err(Fus[i], r["Fup"]) < FLUX_TOL and rel_err(Fds[i], r["Fdn"]) < FLUX_TOL
