@@ -89,6 +89,8 @@ def _load():
     lib.ref_layer_exact.argtypes = [d, d, d, d, d, d, P(ctypes.c_double), P(ctypes.c_double)]
     lib.ref_flux_sweep.restype = i
     lib.ref_flux_sweep.argtypes = [P(RefAtm), P(RefParams), vp, i, i, vp, i, vp, vp, vp, vp, vp]
+    lib.ref_flux_sweep_iso.restype = i
+    lib.ref_flux_sweep_iso.argtypes = [P(RefAtm), P(RefParams), vp, i, vp, vp, vp]
     lib.ref_temp_update.restype = i
     lib.ref_temp_update.argtypes = [P(RefAtm), P(RefParams), vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ref_solve_re.restype = i
@@ -236,6 +238,20 @@ def flux_sweep(atm: Atm, T: np.ndarray, n_passes: int = None, p: RefParams = Non
     if spectra:
         out["up_spec"] = us; out["dn_spec"] = ds
     return out
+
+
+def flux_sweep_iso(atm: Atm, T: np.ndarray, n_passes: int = None, p: RefParams = None):
+    """One flux evaluation on the isothermal-layer grid (ref_flux_sweep_iso).
+    Returns dict(Fup, Fdn, toa)."""
+    p = p or params()
+    if n_passes is None:
+        n_passes = passes(atm, p)
+    n = atm.n
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    Fu = np.empty(n + 1); Fd = np.empty(n + 1); toa = np.empty(atm.L)
+    rc = _load().ref_flux_sweep_iso(ctypes.byref(atm.s), ctypes.byref(p), T.ctypes.data, n_passes,
+                                    Fu.ctypes.data, Fd.ctypes.data, toa.ctypes.data)
+    return {"Fup": Fu, "Fdn": Fd, "toa": toa, "rc": rc}
 
 
 class State:

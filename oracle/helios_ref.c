@@ -500,6 +500,130 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
 }
 
 /* ------------------------------------------------------------------------ */
+/* Two-stream fluxes across one isothermal layer of Planck intensity B,
+ * Sect. 2.1.3: eq. (9) without scattering (omega0 = 0), eq. (10) with the
+ * coefficients of eq. (12) and the coupling coefficients of eq. (13) otherwise,
+ * and the pure-scattering form eq. (14) when 1 - omega0 < w0_pure.  Inputs and
+ * outputs as ref_layer_twostream. */
+static void iso_layer(double F1up, double F2dn, double B, double dtau, double w0, double g0,
+                      const ref_params* p, double* F2up, double* F1dn)
+{
+    const double D = p->D, eps = 1.0 / D;
+    if (1.0 - w0 < p->w0_pure) {
+        double a = D * (1.0 - g0) * dtau;
+        double x = a * (F1up - F2dn) / (2.0 + a);
+        *F2up = F1up - x;
+        *F1dn = F2dn + x;
+        return;
+    }
+    double trans = exp(-D * sqrt((1.0 - w0 * g0) * (1.0 - w0)) * dtau);        /* eq. (8) */
+    if (w0 == 0.0) {                                                            /* eq. (9) */
+        *F2up = trans * F1up + 2.0 * PI * eps * B * (1.0 - trans);
+        *F1dn = trans * F2dn + 2.0 * PI * eps * B * (1.0 - trans);
+        return;
+    }
+    double r = sqrt((1.0 - w0) / (1.0 - w0 * g0));
+    double zp = 0.5 * (1.0 + r), zm = 0.5 * (1.0 - r);                          /* eq. (13) */
+    double alpha = zm * zm * trans * trans - zp * zp;                           /* eq. (12) */
+    double beta = zp * zm * (1.0 - trans * trans);
+    double xi = (zm * zm - zp * zp) * trans;
+    double ups = (zm * zm * trans + zp * zp) * (1.0 - trans);
+    *F2up = (xi * F1up - beta * F2dn + 2.0 * PI * eps * B * (beta - ups)) / alpha;   /* eq. (10) */
+    *F1dn = (xi * F2dn - beta * F1up + 2.0 * PI * eps * B * (beta - ups)) / alpha;
+}
+
+/* One flux evaluation on the grid of isothermal layers (Sect. 2.2.1, first
+ * part), the grid of the emission spectra computed after convergence (Sect. 3:
+ * a post-processing step).  Layer i has the temperature T[i] and the pressure
+ * of its centre (the same centres as the non-isothermal grid), its opacity is
+ * interpolated there (Sect. 2.3), and its optical thickness is kappa_i dm_i with
+ * dm_i = (P_i - P_{i+1})/g between its interfaces (eq. 18).  Layer fluxes from
+ * eqs. (9), (10) or (14) with B_i = B(T_i).  Passes, boundary conditions (eqs.
+ * 20, 22) and the Gauss-point and bin sums as ref_flux_sweep, each pass from
+ * the previous pass's upward fluxes, the first from zero.  Fup_bol, Fdn_bol:
+ * [n+1] at the interfaces; Fup_toa: [L] (optional).  Returns 0, or -1 on a
+ * non-finite flux. */
+int ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, int n_passes,
+                       double* Fup_bol, double* Fdn_bol, double* Fup_toa)
+{
+    const int n = a->n, np = 2 * n + 1, L = a->L, G = a->G;
+    double* lp = (double*)malloc(sizeof(double) * np);
+    double* Pp = (double*)malloc(sizeof(double) * np);
+    double* gx = (double*)malloc(sizeof(double) * G);
+    double* gw = (double*)malloc(sizeof(double) * G);
+    double* toa = (double*)malloc(sizeof(double) * L);
+    double* bint = (double*)malloc(sizeof(double) * L);
+    double* dm = (double*)malloc(sizeof(double) * n);
+    int* iP = (int*)malloc(sizeof(int) * n);
+    int* iT = (int*)malloc(sizeof(int) * n);
+    double* wP = (double*)malloc(sizeof(double) * n);
+    double* wT = (double*)malloc(sizeof(double) * n);
+    double* up_bin = (double*)calloc((size_t)L * (n + 1), sizeof(double));
+    double* dn_bin = (double*)calloc((size_t)L * (n + 1), sizeof(double));
+    int bad = 0;
+
+    ref_grid(a, lp, Pp, NULL, NULL);              /* points 2i: interfaces, 2i+1: centres */
+    ref_gauss_legendre(G, gx, gw);
+    ref_boundary_spectra(a, toa, bint);
+    for (int i = 0; i < n; ++i) {
+        dm[i] = (Pp[2 * i] - Pp[2 * i + 2]) / a->grav;
+        ref_table_coord(lp[2 * i + 1], a->log10P0, a->dlog10P, a->nP, &iP[i], &wP[i]);
+        ref_table_coord(T[i], a->T0, a->dT, a->nT, &iT[i], &wT[i]);
+    }
+
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+    for (int l = 0; l < L; ++l) {
+        double* B = (double*)malloc(sizeof(double) * n);
+        double* dtau = (double*)malloc(sizeof(double) * n);
+        double* Fup = (double*)malloc(sizeof(double) * (n + 1));
+        double* Fdn = (double*)malloc(sizeof(double) * (n + 1));
+        const double w0 = a->omega0[l], g0 = a->g0[l];
+        for (int i = 0; i < n; ++i) B[i] = bin_planck(a, l, T[i]);
+        if (Fup_toa) Fup_toa[l] = 0.0;
+        for (int g = 0; g < G; ++g) {
+            const double wg = 0.5 * gw[g];
+            for (int i = 0; i < n; ++i) {
+                int i1 = a->nP > 1 ? iP[i] + 1 : iP[i], j1 = a->nT > 1 ? iT[i] + 1 : iT[i];
+                double k00 = table_value(a, iP[i], iT[i], l, g), k10 = table_value(a, i1, iT[i], l, g);
+                double k01 = table_value(a, iP[i], j1, l, g), k11 = table_value(a, i1, j1, l, g);
+                double kap = (1.0 - wT[i]) * ((1.0 - wP[i]) * k00 + wP[i] * k10)
+                           + wT[i] * ((1.0 - wP[i]) * k01 + wP[i] * k11);
+                dtau[i] = kap * dm[i];
+            }
+            for (int i = 0; i <= n; ++i) Fup[i] = 0.0;
+            for (int pass = 0; pass < n_passes; ++pass) {
+                double dummy;
+                Fdn[n] = toa[l];
+                for (int i = n - 1; i >= 0; --i)
+                    iso_layer(Fup[i], Fdn[i + 1], B[i], dtau[i], w0, g0, p, &dummy, &Fdn[i]);
+                Fup[0] = Fdn[0] + bint[l];
+                for (int i = 0; i < n; ++i)
+                    iso_layer(Fup[i], Fdn[i + 1], B[i], dtau[i], w0, g0, p, &Fup[i + 1], &dummy);
+            }
+            for (int i = 0; i <= n; ++i) {
+                up_bin[(size_t)l * (n + 1) + i] += wg * Fup[i];
+                dn_bin[(size_t)l * (n + 1) + i] += wg * Fdn[i];
+                if (!isfinite(Fup[i]) || !isfinite(Fdn[i])) bad = 1;
+            }
+            if (Fup_toa) Fup_toa[l] += wg * Fup[n];
+        }
+        free(B); free(dtau); free(Fup); free(Fdn);
+    }
+    for (int i = 0; i <= n; ++i) {
+        double su = 0.0, sd = 0.0;
+        for (int l = 0; l < L; ++l) {
+            su += up_bin[(size_t)l * (n + 1) + i];
+            sd += dn_bin[(size_t)l * (n + 1) + i];
+        }
+        Fup_bol[i] = su;
+        Fdn_bol[i] = sd;
+    }
+    free(lp); free(Pp); free(gx); free(gw); free(toa); free(bint); free(dm);
+    free(iP); free(iT); free(wP); free(wT); free(up_bin); free(dn_bin);
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One radiative-equilibrium temperature step, Sects. 2.2.3-2.2.4.
  *
  * Net flux F_- = F_up - F_dn at each interface; divergence of layer i

@@ -92,6 +92,8 @@ void   ref_layer_exact(double F1up, double F2dn, double B1, double B2, double dt
 int    ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n_passes, int exact,
                       double* warm, int warm_valid, double* Fup_bol, double* Fdn_bol, double* Fup_toa,
                       double* Fup_spec, double* Fdn_spec);
+int    ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, int n_passes,
+                          double* Fup_bol, double* Fdn_bol, double* Fup_toa);
 int    ref_temp_update(const ref_atm* a, const ref_params* p, const double* Fup_bol, const double* Fdn_bol,
                        double* T, double* mult, int* hist, int* nhist, double* metric, double* dT);
 int    ref_solve_re(const ref_atm* a, const ref_params* p, double* T, double* mult, int* hist, int* nhist,

@@ -229,6 +229,14 @@ class Plan:
                                          Fd.data_ptr(), _ptr(toa), _stream_ptr(stream)))
         return Fu, Fd, toa
 
+    def emission_spectrum(self, T, n_passes=81, stream=None):
+        """Emergent spectrum of converged temperatures T (Sect. 3: computed as a post-processing
+        step, on a plan made with iso_layers=1 and the spectrum's bins; Sect. 2.2.3: 80
+        additional scattering passes).  One cold-start evaluation; returns (Fup_toa per bin,
+        Fup_bol, Fdn_bol)."""
+        Fu, Fd, toa = self.flux_sweep(T, n_passes=n_passes, warm=False, want_toa=True, stream=stream)
+        return toa, Fu, Fd
+
     def new_state(self):
         torch = _torch()
         L = int(self.info.layers)

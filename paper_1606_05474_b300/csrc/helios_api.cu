@@ -203,6 +203,7 @@ void helios_default_params(helios_params_t* p)
     p->bins_per_item = 0;
     p->check_every = 0;
     p->persistent = 1;
+    p->iso_layers = 0;
 }
 
 int helios_version(void) { return HELIOS_VERSION; }
@@ -271,7 +272,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     if (!(prm->D > 0.0) || !(prm->dtau_iso >= 0.0) || !(prm->w0_pure >= 0.0) || !(prm->tol > 0.0) ||
         prm->n_scat < 0 || prm->max_iter < 1 || !(prm->osc_down > 0.0) || !(prm->osc_up > 0.0) ||
         !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0 ||
-        prm->persistent < 0 || prm->persistent > 1)
+        prm->persistent < 0 || prm->persistent > 1 || prm->iso_layers < 0 || prm->iso_layers > 1)
         return fail(HELIOS_EINVAL, "invalid parameter set");
     const int G = tabs[0].G;
     if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
@@ -418,9 +419,16 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         for (int p = 0; p <= 2 * n; ++p) {
             const double lp = (lb + 0.5 * h) - (0.5 * h) * (double)p;
             Pp[p] = 1e6 * std::pow(10.0, lp);
-            host_table_coord(lp, k.log10P0, k.dlog10P, k.nP, iP[d.pt_off + p], wP[d.pt_off + p]);
+            // isothermal layers: both points of layer i sit at its centre pressure (Sect. 2.3)
+            const double lq = prm->iso_layers ? lb - h * (double)std::min(p >> 1, n - 1) : lp;
+            host_table_coord(lq, k.log10P0, k.dlog10P, k.nP, iP[d.pt_off + p], wP[d.pt_off + p]);
         }
-        for (int s = 0; s < 2 * n; ++s) dm[d.sub_off + s] = (float)((Pp[s] - Pp[s + 1]) / b->grav[a]);
+        for (int s = 0; s < 2 * n; ++s) {
+            // isothermal layers: sublayer 2i is layer i between its interfaces (eq. 18), sublayer
+            // 2i+1 the zero-thickness step to layer i+1
+            const double dP = prm->iso_layers ? ((s & 1) ? 0.0 : Pp[s] - Pp[s + 2]) : Pp[s] - Pp[s + 1];
+            dm[d.sub_off + s] = (float)(dP / b->grav[a]);
+        }
         for (int i = 0; i < n; ++i) {
             lnr[d.lay_off + i] = std::log(Pp[2 * i] / Pp[2 * i + 2]);
             lay_atm[d.lay_off + i] = a;
@@ -573,7 +581,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.gw = d_gw;
     dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
     dv.spec_tab = d_spec_tab; dv.spec_w = d_spec_w;
-    dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso;
+    dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso; dv.iso_layers = prm->iso_layers;
     P->atms_h = ad;
     P->ws_bytes = (int64_t)tot;
     *out = P;

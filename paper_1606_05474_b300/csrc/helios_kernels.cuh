@@ -108,6 +108,7 @@ struct PlanDev {
     unsigned long long* metric_bits;   // [A] max |dF|/(sigma T^4) as ordered bits
     int G, TB, A;
     float dtau_iso;
+    int iso_layers;             // 1: isothermal-layer grid (both points of layer i at T_i)
 };
 
 // ---------------------------------------------------------------------------
@@ -128,8 +129,11 @@ __device__ __forceinline__ void table_coord(double x, double x0, double dx, int 
 
 // temperature at point p of an n-layer column (Sect. 2.2.1; outer interfaces take the
 // nearest centre)
-__device__ __forceinline__ double point_T(const double* T, int n, int p)
+__device__ __forceinline__ double point_T(const double* T, int n, int p, int iso_layers)
 {
+    // isothermal layers (Sect. 2.2.1): points 2i and 2i+1 bound layer i and carry its
+    // temperature; the last point repeats the top layer
+    if (iso_layers) return T[min(p >> 1, n - 1)];
     if (p & 1) return T[p >> 1];
     int i = p >> 1;
     if (i == 0) return T[0];
@@ -173,24 +177,36 @@ __device__ __forceinline__ float em1(float x)
 }
 
 // phi(x) = (1 - e^{-x})/x for x >= 0 (Taylor series below 0.35, else direct), with
-// u = 1 - e^{-x} = x phi and t = e^{-x}
+// u = 1 - e^{-x} = x phi and t = e^{-x}.  Both forms are evaluated and selected: a lane's
+// sublayers lie at every depth of the column, so a branch would split every warp.  phi enters
+// only the source term, where a rounding bias does not compound along the column, so the
+// quotient may use the approximate divide
 __device__ __forceinline__ void phi_u_t(float x, float& phi, float& u, float& t)
 {
-    if (x < 0.35f) {
-        float p = fmaf(x, -2.4801587e-5f, 1.9841270e-4f);     // (-1)^k x^k / (k+1)!
-        p = fmaf(x, p, -1.3888889e-3f);
-        p = fmaf(x, p, 8.3333333e-3f);
-        p = fmaf(x, p, -4.1666667e-2f);
-        p = fmaf(x, p, 1.6666667e-1f);
-        p = fmaf(x, p, -0.5f);
-        phi = fmaf(x, p, 1.0f);
-        u = x * phi;
-        t = 1.0f - u;
-    } else {
-        t = expf(-x);                      // accurate to ~1 ulp for any x (the fast intrinsic's
-        u = 1.0f - t;                      // error grows with |x| and compounds through transmissions)
-        phi = __fdiv_rn(u, x);
-    }
+    float p = fmaf(x, -2.4801587e-5f, 1.9841270e-4f);         // (-1)^k x^k / (k+1)!
+    p = fmaf(x, p, -1.3888889e-3f);
+    p = fmaf(x, p, 8.3333333e-3f);
+    p = fmaf(x, p, -4.1666667e-2f);
+    p = fmaf(x, p, 1.6666667e-1f);
+    p = fmaf(x, p, -0.5f);
+    const float ph = fmaf(x, p, 1.0f);
+    const float te = expf(-x);             // accurate to ~1 ulp for any x (the fast intrinsic's
+    const float ue = 1.0f - te;            // error grows with |x| and compounds through transmissions)
+    const bool small = x < 0.35f;
+    u = small ? x * ph : ue;
+    t = small ? 1.0f - u : te;
+    phi = small ? ph : __fdividef(ue, x);
+}
+
+// a + b for float-float values (hi, lo): Knuth's error-free two-sum of the high parts plus the
+// low parts, renormalised
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float v = s - a.x;
+    const float e = ((a.x - (s - v)) + (b.x - v)) + (a.y + b.y);
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
 }
 
 // Two-stream Planck flux E / (e^x - 1) of a bin at 1/T = it (float-float), with x = xs / T
@@ -225,7 +241,7 @@ __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const
     const TabDesc td = P.tabs[ad.tab];
     const double* T = T_layer + ad.lay_off;
     const int q = ad.pt_off + p;
-    const double Tn = point_T(T, n, p);
+    const double Tn = point_T(T, n, p, P.iso_layers);
     int it, row;
     double w;
     float4 wq;
@@ -246,7 +262,7 @@ __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const
     P.dT_step[q] = (float)(To - Tn);
     P.Tpt[q] = Tn;
     if (p < 2 * n) {
-        const double Tb = point_T(T, n, p + 1);
+        const double Tb = point_T(T, n, p + 1, P.iso_layers);
         const float Tbf = (float)Tb;
         P.dinv_sub[ad.sub_off + p] = (float)(Tn - Tb) / (Tnf * Tbf);
         P.dT_sub[ad.sub_off + p] = (float)(Tn - Tb);
@@ -272,7 +288,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     if (b.flags & BIN_NO_SCAT) {            // zeta_- = 0: Ts = trans, Rs = 0
         Ts = tr;
         Rs = 0.0f;
-        Ss = iso ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
+        Ss = (iso || dtau == 0.0f) ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
         return;
     }
     // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha.  Reciprocals and
@@ -284,6 +300,12 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     Rs = b.q * t2u * d;
     const float h = d * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);       // (1 - Ts + Rs) / u
     Ss = iso ? 0.5f * dB * fmaf(-h, u, 2.0f) : b.cl * dB * phi * h;
+    // zero thickness (the step between two isothermal layers): the flux passes unchanged, so
+    // the deviation from the local Planck flux steps by the Planck difference (exact 1, 0, dB)
+    const bool step = dtau == 0.0f;
+    Ts = step ? 1.0f : Ts;
+    Rs = step ? 0.0f : Rs;
+    Ss = step ? dB : Ss;
 }
 
 // ---------------------------------------------------------------------------
@@ -518,23 +540,44 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 #pragma unroll
         for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = X[k];
         __syncthreads();
-        // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators
-        for (int i = tid; i <= n; i += nthreads) {
-            float sd = 0.0f;
-            double sud;
-            for (int gg = 0; gg < G; ++gg) sd += kap[gg * KST + i];
-            if (i < n) {
-                float su = 0.0f;
-                for (int gg = 0; gg < G; ++gg) su += kap[gg * KST + (n + 1) + i];
-                sud = (double)su;
+        // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators.
+        // Thread t sums column t of the per-warp rows (downward interfaces 0..n, then upward
+        // interfaces 0..n); the threads after them add the Planck fluxes at the interfaces
+        const int NI = n + 1;
+        for (int t = tid; t < 3 * NI; t += nthreads) {
+            if (t == 2 * NI - 1) continue;                 // TOA upward: summed below
+            double v;
+            int a;
+            if (t < 2 * NI) {
+                float sg = 0.0f;
+                for (int gg = 0; gg < G; ++gg) sg += kap[gg * KST + t];
+                v = (double)sg;
+                a = t < NI ? NI + t : t - NI;
             } else {
-                sud = 0.0;
-                for (int gg = 0; gg < G; ++gg) sud += (double)P.gw[gg] * (double)kap[gg * KST + (n + 1) + i];
-                if (Fup_toa) Fup_toa[ad.bin_off + l] = (float)(sud + (double)bt[2 * n]);
+                v = (double)bt[2 * (t - 2 * NI)];
+                a = t;
             }
-            acc[i] += sud;
-            acc[(n + 1) + i] += (double)sd;
-            acc[2 * (n + 1) + i] += (double)bt[2 * i];
+            acc[a] += v;
+        }
+        // the emergent bin: sum_g w_g G_up(TOA) as a float-float reduction over the lanes of the
+        // last warp (exact products, fixed butterfly), then the Planck add-back in double
+        if (tid >= nthreads - 32) {
+            float2 sv = make_float2(0.0f, 0.0f);
+            if (lane < G) {
+                const float w = P.gw[lane], x = kap[lane * KST + 2 * NI - 1];
+                const float pr = w * x;
+                sv = make_float2(pr, fmaf(w, x, -pr));
+            }
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) {
+                const float2 o = make_float2(__shfl_xor_sync(FULL, sv.x, d), __shfl_xor_sync(FULL, sv.y, d));
+                sv = ff_add(sv, o);
+            }
+            if (lane == 0) {
+                const double sud = (double)sv.x + (double)sv.y;
+                if (Fup_toa) Fup_toa[ad.bin_off + l] = (float)(sud + (double)bt[2 * n]);
+                acc[n] += sud;
+            }
         }
         __syncthreads();
     }
@@ -703,7 +746,7 @@ __global__ void interp_kernel(PlanDev P, const double* __restrict__ T_layer, int
         int it, row;
         double wt;
         float4 wq;
-        table_coord(point_T(T, n, p), td.T0, td.dT, td.nT, it, wt);
+        table_coord(point_T(T, n, p, P.iso_layers), td.T0, td.dT, td.nT, it, wt);
         point_corners(td, P.iP[q], P.wP[q], it, wt, row, wq);
         if (kappa_out) {
             float k;

@@ -175,6 +175,7 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
         !(b->T_irr[0] >= 0.0) || !(b->T_int[0] >= 0.0) || !(b->T_star[0] > 0.0))
         return err(HELIOS_EINVAL, "invalid pressure range, gravity or temperatures");
     if (prm->grey_mode && L != 2) return err(HELIOS_EINVAL, "grey mode needs 2 bins");
+    if (prm->iso_layers) return err(HELIOS_EINVAL, "isothermal layers are not supported without a plan");
     for (int l = 0; l <= L; ++l)
         if (!(b->nu_edges[l] > 0.0) || (l > 0 && !(b->nu_edges[l] > b->nu_edges[l - 1])))
             return err(HELIOS_EINVAL, "bin edges must be positive and increasing");

@@ -160,3 +160,36 @@ def test_species_mixing_matches_mixed_table():
         atm = oracle.Atm(a, wl.tables[0], kappa64=synth.mixed_table64(wl, a))
         r = oracle.flux_sweep(atm, Ts[i], n_passes=5)
         assert rel_err(Fus[i], r["Fup"]) < FLUX_TOL and rel_err(Fds[i], r["Fdn"]) < FLUX_TOL
+
+
+@pytest.mark.parametrize("n,L,passes", [(40, 12, 1), (40, 12, 81), (101, 9, 81), (239, 3, 5)])
+def test_isothermal_layer_grid_emission_spectrum(n, L, passes):
+    # the grid of the post-processing spectra (isothermal layers, Sect. 2.2.1 and Sect. 3),
+    # cold start, up to 1 + 80 scattering passes (Sect. 2.2.3)
+    wl = synth.small_scattering(L=L, n=n)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 9)
+    plan = make_plan(wl, iso_layers=1)
+    toa, Fu, Fd = plan.emission_spectrum(pack([T]), n_passes=passes)
+    r = oracle.flux_sweep_iso(atm, T, n_passes=passes)
+    assert r["rc"] == 0
+    _check_fluxes(Fu, Fd, r)
+    _check_toa(toa, r, atm)
+
+
+def test_isothermal_layer_grid_temperature_step():
+    # the radiative-equilibrium step runs unchanged on the isothermal grid: one step from the
+    # oracle's fluxes on that grid
+    wl = synth.small_scattering(L=10, n=30)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 3)
+    plan = make_plan(wl, iso_layers=1)
+    Tg = pack([T])
+    Fu, Fd, _ = plan.flux_sweep(Tg, n_passes=5, want_toa=False)
+    r = oracle.flux_sweep_iso(atm, T, n_passes=5)
+    _check_fluxes(Fu, Fd, r)
+    st = oracle.State(atm, T)
+    oracle.temp_update(atm, st, Fu.cpu().numpy(), Fd.cpu().numpy())
+    state = plan.new_state()
+    plan.temp_update(Fu, Fd, Tg, state)
+    assert rel_err(Tg.cpu().numpy(), st.T) < 1e-12
