@@ -133,6 +133,10 @@ typedef struct {
                             temperature and pressure, opacity at the centre, optical thickness over
                             the whole layer -- the grid of the emission spectra computed as a
                             post-processing step (Sect. 3; with n_passes = 81, Sect. 2.2.3) */
+    int device_loop;     /* helios_solve_re: 1: the whole iteration is one CUDA graph whose conditional
+                            WHILE node repeats check_every steps until no atmosphere is active (no host
+                            round trip); 0: the host relaunches a graph of check_every steps and reads
+                            the active count in between */
 } helios_params_t;
 
 void helios_default_params(helios_params_t* p);

@@ -170,6 +170,8 @@ struct helios_plan {
     cudaGraphExec_t graph;
     const void* graph_key[3];
     int graph_chunk;
+    int graph_device_loop;
+    int* chunks_left;   // device budget of WHILE-node iterations (device_loop)
     cudaEvent_t fork;
     int* counters;
     // optional timing of the sweep kernels: a ring of event pairs on the launch stream
@@ -204,6 +206,7 @@ void helios_default_params(helios_params_t* p)
     p->check_every = 0;
     p->persistent = 1;
     p->iso_layers = 0;
+    p->device_loop = 1;
 }
 
 int helios_version(void) { return HELIOS_VERSION; }
@@ -272,7 +275,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     if (!(prm->D > 0.0) || !(prm->dtau_iso >= 0.0) || !(prm->w0_pure >= 0.0) || !(prm->tol > 0.0) ||
         prm->n_scat < 0 || prm->max_iter < 1 || !(prm->osc_down > 0.0) || !(prm->osc_up > 0.0) ||
         !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0 ||
-        prm->persistent < 0 || prm->persistent > 1 || prm->iso_layers < 0 || prm->iso_layers > 1)
+        prm->persistent < 0 || prm->persistent > 1 || prm->iso_layers < 0 || prm->iso_layers > 1 ||
+        prm->device_loop < 0 || prm->device_loop > 1)
         return fail(HELIOS_EINVAL, "invalid parameter set");
     const int G = tabs[0].G;
     if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
@@ -538,7 +542,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     ALLOC(dv.dinv_sub, sub); ALLOC(dv.dT_sub, sub);
     ALLOC(dv.part, part); ALLOC(dv.warm, warm);
     ALLOC(P->Fup, ifc); ALLOC(P->Fdn, ifc); ALLOC(P->mult, lay); ALLOC(P->hist, lay); ALLOC(P->nhist, lay);
-    ALLOC(P->n_active, 1);
+    ALLOC(P->n_active, 1); ALLOC(P->chunks_left, 1);
     ALLOC(P->counters, kMaxM + 1);
 #undef ALLOC
     std::vector<int> order;
@@ -646,6 +650,15 @@ int helios_plan_info(const helios_plan* p, helios_plan_info_t* info)
 
 // ---------------------------------------------------------------------------
 namespace {
+
+// the condition of the WHILE node of the radiative-equilibrium graph: loop while any atmosphere is
+// active and the chunk budget lasts (the budget bounds the loop whatever the device state)
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle h, const int* n_active, int* chunks_left)
+{
+    const int left = *chunks_left - 1;
+    *chunks_left = left;
+    cudaGraphSetConditional(h, (*n_active > 0 && left > 0) ? 1u : 0u);
+}
 
 template <int M, int MINB>
 int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
@@ -820,35 +833,76 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
     if (rc) return rc;
     rc = launch_temp(p, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr, p->n_active, w);
     if (rc) return rc;
-    // later steps start from the previous step's fluxes; captured as a graph of `chunk` steps
+    // later steps start from the previous step's fluxes; captured as a graph of `chunk` steps,
+    // either inside a conditional WHILE node that the device keeps looping (device_loop) or
+    // relaunched by the host between reads of the active count
     const int chunk = p->prm.check_every > 0 ? p->prm.check_every : 16;
+    const int dloop = p->prm.device_loop;
     const void* key[3] = {T_layer, iters, status};
-    if (!p->graph || p->graph_chunk != chunk || std::memcmp(key, p->graph_key, sizeof key) != 0) {
+    if (!p->graph || p->graph_chunk != chunk || p->graph_device_loop != dloop ||
+        std::memcmp(key, p->graph_key, sizeof key) != 0) {
         if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
-        cudaGraph_t g;
-        CUDA_TRY(cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        cudaGraphConditionalHandle h = 0;
+        if (dloop) {
+            CUDA_TRY(cudaGraphCreate(&g, 0));
+            // zero-filled storage: the parameter union has no default constructor
+            alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)] = {};
+            cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+            cudaGraphNode_t node;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess) {
+                np.type = cudaGraphNodeTypeConditional;
+                np.conditional.handle = h;
+                np.conditional.type = cudaGraphCondTypeWhile;
+                np.conditional.size = 1;
+                e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+            }
+            if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(w, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                                   cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return fail(HELIOS_ECUDA, "conditional graph: %s", cudaGetErrorString(e));
+            }
+        } else {
+            CUDA_TRY(cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal));
+        }
         for (int i = 0; i < chunk && rc == HELIOS_OK; ++i) {
             rc = launch_eval(p, T_layer, status, p->passes, 1, p->Fup, p->Fdn, nullptr, w);
             if (rc == HELIOS_OK)
                 rc = launch_temp(p, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr,
                                  p->n_active, w);
         }
-        cudaError_t ec = cudaStreamEndCapture(w, &g);
-        if (rc) { if (ec == cudaSuccess) cudaGraphDestroy(g); return rc; }
-        if (ec != cudaSuccess) return fail(HELIOS_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+        if (rc == HELIOS_OK && dloop) {
+            loop_cond_kernel<<<1, 1, 0, w>>>(h, p->n_active, p->chunks_left);
+            if (cudaGetLastError() != cudaSuccess) rc = fail(HELIOS_ECUDA, "loop condition launch failed");
+        }
+        cudaGraph_t captured = nullptr;
+        cudaError_t ec = cudaStreamEndCapture(w, &captured);
+        if (!dloop) g = captured;
+        if (rc || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : fail(HELIOS_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+        }
         cudaError_t ei = cudaGraphInstantiate(&p->graph, g, 0);
         cudaGraphDestroy(g);
         if (ei != cudaSuccess) { p->graph = nullptr; return fail(HELIOS_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei)); }
         std::memcpy(p->graph_key, key, sizeof key);
         p->graph_chunk = chunk;
+        p->graph_device_loop = dloop;
     }
-    int done = 1;   // the kernel itself retires atmospheres at max_iter; this bound is only a backstop
-    while (done < p->prm.max_iter + chunk) {
+    // the kernel itself retires atmospheres at max_iter; the chunk budget is only a backstop
+    const int budget = (p->prm.max_iter + chunk - 1) / chunk + 1;
+    if (dloop) {
+        CUDA_TRY(cudaMemcpyAsync(p->chunks_left, &budget, sizeof(int), cudaMemcpyHostToDevice, w));
         CUDA_TRY(cudaGraphLaunch(p->graph, w));
-        done += chunk;
-        CUDA_TRY(cudaMemcpyAsync(c->h_active, p->n_active, sizeof(int), cudaMemcpyDeviceToHost, w));
-        CUDA_TRY(cudaStreamSynchronize(w));
-        if (*c->h_active <= 0) break;
+    } else {
+        for (int k = 0; k < budget; ++k) {
+            CUDA_TRY(cudaGraphLaunch(p->graph, w));
+            CUDA_TRY(cudaMemcpyAsync(c->h_active, p->n_active, sizeof(int), cudaMemcpyDeviceToHost, w));
+            CUDA_TRY(cudaStreamSynchronize(w));
+            if (*c->h_active <= 0) break;
+        }
     }
     p->warm_ready = true;
     CUDA_TRY(cudaEventRecord(c->ev_out, w));

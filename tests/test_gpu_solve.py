@@ -156,3 +156,26 @@ def test_autotune_picks_a_candidate_and_caches_it(tmp_path):
     assert len(d) == 1 and list(d.values())[0]["bins_per_item"] == p.bins_per_item
     p2 = hp.autotune(ctx(), wl.atms, wl.tables, kap, cache_path=cache)       # cache hit
     assert (p2.bins_per_item, p2.persistent) == (p.bins_per_item, p.persistent)
+
+
+def test_device_while_loop_and_host_loop_agree_bitwise():
+    # the conditional-WHILE graph runs the same kernels in the same order as the host-checked
+    # chunks, so temperatures, iteration counts and statuses agree bit for bit; a small chunk
+    # makes both loops go round many times, and a low cap retires one atmosphere at max_iter
+    wl = _small_ragged([3, 20, 41], max_bins=16)
+    outs = []
+    for dl in (1, 0):
+        p = make_plan(wl, device_loop=dl, check_every=3, max_iter=400)
+        T = pack([a.T_init for a in wl.atms])
+        iters, status = p.solve_re(T)
+        outs.append((T.clone(), iters.clone(), status.clone()))
+    for x, y in zip(*outs):
+        assert bool((x == y).all())
+    st = outs[0][2].cpu().numpy()
+    assert set(st.tolist()) <= {1, 2}
+    # a second solve on the same plan relaunches the cached graph with a fresh budget
+    p = make_plan(wl, device_loop=1, check_every=3, max_iter=400)
+    for _ in range(2):
+        T = pack([a.T_init for a in wl.atms])
+        iters, status = p.solve_re(T)
+        assert bool((T == outs[0][0]).all()) and bool((iters == outs[0][1]).all())
