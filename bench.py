@@ -357,6 +357,92 @@ def run_gpu_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_gpu_learned(args):
+    """Batched radiative-equilibrium solves of held-out planets from the isothermal start (plain)
+    and from the learned initial profile (surrogate): RE-converged atmospheres per second.  The
+    planets are the learned-initialiser family (100 layers 1e-6..1e3 bar, 20 g, Rayleigh-like
+    scattering, opacity a metallicity- and C/O-weighted mixture of two seeded tables) on the
+    paper's radiative-equilibrium resolution of 300 bins (Sect. 3).  The surrogate is trained on
+    converged plain solutions of other planets of the family; its inference is inside the timed
+    region, plan set-up is not."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import synth
+    import paper_1606_05474_b300 as hp
+    from paper_1606_05474_b300.learned import LearnedInitializer, features
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n_tr, n_te = args.train, args.test
+    wl = synth.learned_dataset(n_tr + n_te, L=args.bins, n=100, first=rank * (n_tr + n_te))
+    ctx = hp.Context(local)
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    prm = hp.default_params(max_iter=20000)
+    tr_atms, te_atms = wl.atms[:n_tr], wl.atms[n_tr:]
+
+    def solve(atms, starts):
+        plan = hp.Plan(ctx, atms, wl.tables, kap, prm)
+        T = torch.from_numpy(np.concatenate(starts)).to(dev)
+        torch.cuda.synchronize()
+        t = time.time()
+        iters, status = plan.solve_re(T)
+        torch.cuda.synchronize()
+        dt = time.time() - t
+        return np.array(plan.split_layers(T.cpu().numpy())), iters.cpu().numpy(), status.cpu().numpy(), dt
+
+    Ttr, it_tr, st_tr, t_tr = solve(tr_atms, [a.T_init for a in tr_atms])
+    ok = st_tr == 1
+    init = LearnedInitializer(ctx, seed=1, max_batch=max(256, n_te))
+    t = time.time()
+    losses = init.fit(features(tr_atms)[ok], Ttr[ok], epochs=args.epochs, batch=256, lr=2e-3)
+    torch.cuda.synchronize()
+    t_fit = time.time() - t
+    Tp, it_p, st_p, t_plain = solve(te_atms, [a.T_init for a in te_atms])
+    t = time.time()
+    starts, used = init.initial_profiles(features(te_atms), [a.n_layers for a in te_atms],
+                                         [a.T_init for a in te_atms])
+    t_inf = time.time() - t
+    Ts, it_s, st_s, t_sur = solve(te_atms, starts)
+    t_sur += t_inf
+    if rank != 0:
+        return
+    both = (st_p == 1) & (st_s == 1)
+    T0 = np.array([a.T_init for a in te_atms])
+    rms_iso = np.sqrt(((T0 - Tp) ** 2).mean(axis=1))[both]
+    rms_ml = np.sqrt(((np.array(starts) - Tp) ** 2).mean(axis=1))[both]
+    dT = np.abs(Ts - Tp)[both]
+    flop_fwd = 2 * (6 * 256 + 2 * 256 * 256 + 256 * 100)
+    n_fit = int(ok.sum()) * args.epochs
+    line = {
+        "metric": "RE-converged atmospheres/s, batched + surrogate vs plain", "value": round(int((st_s == 1).sum()) / t_sur, 3),
+        "unit": "atm/s", "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step / bf16 MLP", "data": "synthetic",
+        "config": {"workload": f"learned-initialiser family: {n_te} held-out planets, 100 layers x {args.bins} bins x 20 g, "
+                               f"scattering, 2-table mixtures; surrogate trained on {int(ok.sum())} converged planets",
+                   "tol": prm.tol, "max_iter": prm.max_iter, "parallelism": f"replicas x{world}"},
+        "plain": {"atm_per_s": round(int((st_p == 1).sum()) / t_plain, 3), "wall_s": round(t_plain, 3),
+                  "converged": int((st_p == 1).sum()), "iters_median": float(np.median(it_p)),
+                  "iters_mean": round(float(it_p.mean()), 1)},
+        "surrogate": {"atm_per_s": round(int((st_s == 1).sum()) / t_sur, 3), "wall_s": round(t_sur, 3),
+                      "inference_s": round(t_inf, 4), "converged": int((st_s == 1).sum()),
+                      "iters_median": float(np.median(it_s)), "iters_mean": round(float(it_s.mean()), 1),
+                      "used_learned_start": int(used.sum())},
+        "initial_guess_rms_K": {"isothermal_median": round(float(np.median(rms_iso)), 2),
+                                "learned_median": round(float(np.median(rms_ml)), 2),
+                                "learned_max": round(float(rms_ml.max()), 2)},
+        "final_T_agreement_K": {"median_of_max": round(float(np.median(dT.max(axis=1))), 4),
+                                "p95_all_layers": round(float(np.quantile(dT, 0.95)), 4),
+                                "max": round(float(dT.max()), 3)},
+        "training": {"solve_s": round(t_tr, 2), "fit_s": round(t_fit, 2), "loss_first": float(losses[0]),
+                     "loss_last": float(losses[-1]), "samples": int(ok.sum()), "epochs": args.epochs,
+                     "mlp_tflops": round(3 * flop_fwd * n_fit / t_fit / 1e12, 4)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(seconds=12.0, wl=None):
     """The FP64 oracle on the same workload on the host cores: whole RE steps, as many as fit."""
     import oracle
@@ -424,11 +510,15 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned"])
     ap.add_argument("--atmospheres", type=int, default=4096)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--train", type=int, default=2048, help="learned workload: training planets")
+    ap.add_argument("--test", type=int, default=512, help="learned workload: held-out planets")
+    ap.add_argument("--bins", type=int, default=300, help="learned workload: bins per planet")
+    ap.add_argument("--epochs", type=int, default=300, help="learned workload: training epochs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -436,6 +526,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_gpu_batched(args)
+    elif args.workload == "learned":
+        run_gpu_learned(args)
     else:
         run_gpu(args)
 

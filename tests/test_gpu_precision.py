@@ -1,0 +1,61 @@
+"""Precision stress: the float32 sweep against the FP64 oracle at high resolution.
+
+Two atmospheres of the precision-stress workload (200 layers, 1e-6..1e3 bar, 30000 bins over
+0.3-200 um, 20 Gauss points, Rayleigh-like scattering, one shared 20x20x30000x20 table) are
+iterated to radiative equilibrium on the GPU; at the converged profiles both sides then evaluate
+the fluxes from a cold start with the default 1 + 4 passes.  Tables of the errors (bolometric
+fluxes per interface, net flux, emergent spectrum per bin) are written as JSON to the path in
+HELIOS_PRECISION_REPORT when it is set.  Bounds: the parity tolerances of the smaller cases
+(1e-5), which the 30000-bin sums must keep.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import make_plan, pack
+
+pytestmark = pytest.mark.gpu
+
+
+def test_precision_stress_error_tables():
+    wl = synth.config5(atm_ids=[0, 41])
+    plan = make_plan(wl, max_iter=20000)
+    T = pack([a.T_init for a in wl.atms])
+    iters, status = plan.solve_re(T)
+    st = status.cpu().numpy()
+    assert (st == 1).all(), st
+    Tg = plan.split_layers(T.cpu().numpy())
+    Fu, Fd, toa = plan.flux_sweep(T, n_passes=5, warm=False)
+    Fus = plan.split_interfaces(Fu.cpu().numpy())
+    Fds = plan.split_interfaces(Fd.cpu().numpy())
+    toas = plan.split_bins(toa.cpu().numpy().astype(np.float64))
+    k64 = wl.tables[0].kappa_for_oracle()
+    rows = []
+    for i, a in enumerate(wl.atms):
+        atm = oracle.Atm(a, wl.tables[0], kappa64=k64)
+        r = oracle.flux_sweep(atm, Tg[i], n_passes=5)
+        assert r["rc"] == 0
+        inc, _ = oracle.boundary_spectra(atm)
+        up_err = np.abs(Fus[i] / r["Fup"] - 1.0)
+        dn_err = np.abs(Fds[i] / r["Fdn"] - 1.0)
+        scale = np.maximum(r["Fup"], r["Fdn"])
+        net_err = np.abs((Fus[i] - Fds[i]) - (r["Fup"] - r["Fdn"])) / scale
+        spec_err = np.abs(toas[i] - r["toa"]) / np.maximum(np.abs(r["toa"]), inc)
+        rows.append({"atmosphere": i, "T_irr": a.T_irr, "T_int": a.T_int, "iterations": int(iters[i].item()),
+                     "T_min": float(Tg[i].min()), "T_max": float(Tg[i].max()),
+                     "Fup_rel_max": float(up_err.max()), "Fup_rel_median": float(np.median(up_err)),
+                     "Fdn_rel_max": float(dn_err.max()), "Fdn_rel_median": float(np.median(dn_err)),
+                     "net_rel_max": float(net_err.max()),
+                     "spectrum_rel_max": float(spec_err.max()), "spectrum_rel_median": float(np.median(spec_err)),
+                     "spectrum_rel_p99": float(np.quantile(spec_err, 0.99))})
+    path = os.environ.get("HELIOS_PRECISION_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump({"workload": wl.name, "passes": 5, "rows": rows}, f, indent=1)
+    for r in rows:
+        assert r["Fup_rel_max"] < 1e-5 and r["Fdn_rel_max"] < 1e-5 and r["net_rel_max"] < 1e-5, r
+        assert r["spectrum_rel_max"] < 1e-5, r
