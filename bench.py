@@ -160,7 +160,7 @@ def run_gpu(args):
     for _ in range(args.warmup - 1):
         step(True)
     torch.cuda.synchronize()
-    n_launch_per_step = 2 + len({a.n_layers for a in wl.atms}) + 1     # prep, sweep groups, finalize, temp
+    n_launch_per_step = 3 + len({(2 * a.n_layers + 1 + 31) // 32 | 1 for a in wl.atms})   # prep, sweep groups, finalize, temp
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
@@ -349,7 +349,7 @@ def run_gpu_batched(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "sweep_kernel (all lane chunks)",
                      "kernel_ms": round(sweep_ms, 3), "algorithmic_bytes": int(alg_bytes), "peak_source": "measured"},
-        "gpu_launches": (5 + groups) * args.steps,
+        "gpu_launches": (3 + groups) * args.steps,               # prep, sweep groups, finalize, temp
         "clocks": clk,
         "setup_s": {"inputs": round(t_gen, 2), "autotune": round(t_tune, 2), "plan": round(t_plan, 2)},
         "workspace_gb": round(plan.info.workspace_bytes / 1e9, 2),

@@ -131,6 +131,36 @@ size_t sweep_smem(int M, int G)
     return 3 * (W / 2) * sizeof(double) + (G * KST + 4 * W + 1) * sizeof(float);
 }
 
+// lane chunks up to 7 fit two 640-thread blocks per SM within the register file (48 registers)
+template <int M> constexpr int sweep_minb() { return M <= 7 ? 2 : 1; }
+
+template <int M>
+int sweep_occupancy_M(int threads, size_t smem)
+{
+    auto k = sweep_kernel<M, sweep_minb<M>()>;
+    int nb = 0;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+// resident sweep blocks per SM for lane chunk M, block size and dynamic shared memory (0 on error)
+int sweep_occupancy(int M, int threads, size_t smem)
+{
+    switch (M) {
+        case 1: return sweep_occupancy_M<1>(threads, smem);
+        case 3: return sweep_occupancy_M<3>(threads, smem);
+        case 5: return sweep_occupancy_M<5>(threads, smem);
+        case 7: return sweep_occupancy_M<7>(threads, smem);
+        case 9: return sweep_occupancy_M<9>(threads, smem);
+        case 11: return sweep_occupancy_M<11>(threads, smem);
+        case 13: return sweep_occupancy_M<13>(threads, smem);
+        case 15: return sweep_occupancy_M<15>(threads, smem);
+        default: return 0;
+    }
+}
+
 }  // namespace
 
 __attribute__((visibility("hidden"))) void helios_set_error_text(const char* msg) { g_err = msg; }
@@ -171,6 +201,7 @@ struct helios_plan {
     const void* graph_key[3];
     int graph_chunk;
     int graph_device_loop;
+    int threads;        // sweep block size: one warp per Gauss point
     int* chunks_left;   // device budget of WHILE-node iterations (device_loop)
     cudaEvent_t fork;
     int* counters;
@@ -373,13 +404,15 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     // ---- work items: tiles of TB bins
     // bins per work item: one resident wave of blocks (one block per SM at this register
     // budget) for a single atmosphere, capped for long batches so the tail stays short
+    // block: one warp per Gauss point
+    P->threads = 32 * G;
+    int maxM = 1;
+    for (int a = 0; a < A; ++a) maxM = std::max(maxM, ad[a].M);
     int TB = prm->bins_per_item;
     if (TB <= 0) {
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        int maxM = 1;
-        for (int a = 0; a < A; ++a) maxM = std::max(maxM, ad[a].M);
-        const int per_sm = maxM <= 7 ? 2 : 1;      // resident sweep blocks per SM (register budget)
+        const int per_sm = std::max(1, sweep_occupancy(maxM, P->threads, sweep_smem(maxM, G)));
         TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + (int64_t)nsm * per_sm - 1) / ((int64_t)nsm * per_sm)));
     }
     P->TB = TB;
@@ -536,7 +569,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     ALLOC(d_atm, A); ALLOC(d_tab, ntab); ALLOC(d_bc, bins); ALLOC(d_items, items.size());
     ALLOC(d_order, items.size()); ALLOC(d_gw, G); ALLOC(d_iP, pts); ALLOC(d_wP, pts); ALLOC(d_dm, sub);
     ALLOC(d_lnr, lay); ALLOC(d_lay_atm, lay); ALLOC(d_spec_tab, spec_tab.size()); ALLOC(d_spec_w, spec_w.size());
-    ALLOC(dv.row, pts); ALLOC(dv.wq, pts); ALLOC(dv.metric_bits, A);
+    ALLOC(dv.row, pts); ALLOC(dv.wq, pts);
     ALLOC(dv.Tpt, pts); ALLOC(dv.iT, pts); ALLOC(dv.wT, pts); ALLOC(dv.invT, pts); ALLOC(dv.Tf, pts);
     ALLOC(dv.invT_old, pts); ALLOC(dv.dinv_step, pts); ALLOC(dv.dT_step, pts);
     ALLOC(dv.dinv_sub, sub); ALLOC(dv.dT_sub, sub);
@@ -556,7 +589,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         gr.count = (int)byM[M].size();
         gr.order = d_order + order.size();
         gr.counter = P->counters + M;
-        gr.grid = std::min(gr.count, nsm_all * (M <= 7 ? 2 : 1));
+        gr.grid = std::min(gr.count, nsm_all * std::max(1, sweep_occupancy(M, P->threads, sweep_smem(M, G))));
         order.insert(order.end(), byM[M].begin(), byM[M].end());
         P->groups.push_back(gr);
     }
@@ -671,23 +704,21 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
         configured_dev[M][MINB] = p->ctx->device + 1;
     }
     if (p->prm.persistent) {
-        sweep_kernel<M, MINB><<<gr.grid, 32 * p->G, smem, s>>>(p->dev, gr.order, gr.count, gr.counter, status,
+        sweep_kernel<M, MINB><<<gr.grid, p->threads, smem, s>>>(p->dev, gr.order, gr.count, gr.counter, status,
                                                               n_passes, warm_valid, Fup_toa);
     } else {
-        sweep_kernel<M, MINB><<<gr.count, 32 * p->G, smem, s>>>(p->dev, gr.order, gr.count, nullptr, status,
+        sweep_kernel<M, MINB><<<gr.count, p->threads, smem, s>>>(p->dev, gr.order, gr.count, nullptr, status,
                                                                n_passes, warm_valid, Fup_toa);
     }
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
 }
 
-// lane chunks up to 7 fit two 640-thread blocks per SM within the register file
 template <int M>
 int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
                    float* Fup_toa, cudaStream_t s)
 {
-    if constexpr (M <= 7) return launch_sweep_MB<M, 2>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
-    else return launch_sweep_MB<M, 1>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+    return launch_sweep_MB<M, sweep_minb<M>()>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
 }
 
 int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, float* Fup_toa, cudaStream_t s)
@@ -755,11 +786,8 @@ int launch_temp(helios_plan* p, const double* Fup, const double* Fdn, double* T,
                 uint8_t* nhist, int* status, int* iters, double* metric, int* n_active, cudaStream_t s)
 {
     const TempArgs ta = temp_args(p);
-    const int L = (int)p->layers, blocks = (L + 127) / 128;
-    CUDA_TRY(cudaMemsetAsync(p->dev.metric_bits, 0, sizeof(unsigned long long) * p->A, s));
-    metric_kernel<<<blocks, 128, 0, s>>>(p->dev, ta, Fup, Fdn, T, status, L);
-    CUDA_TRY(cudaGetLastError());
-    step_kernel<<<blocks, 128, 0, s>>>(p->dev, ta, Fup, Fdn, T, mult, hist, nhist, status, iters, metric, n_active, L);
+    const int threads = 32 * ((p->max_n + 31) / 32);          // one block per atmosphere, a thread per layer
+    temp_kernel<<<p->A, threads, 0, s>>>(p->dev, ta, Fup, Fdn, T, mult, hist, nhist, status, iters, metric, n_active);
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
 }

@@ -1,6 +1,6 @@
 // Device kernels of the radiative-equilibrium hot path (sm_103a).
 //
-// One flux evaluation + temperature step is five launches:
+// One flux evaluation + temperature step is four launches:
 //   prep_kernel      one thread per point: point temperatures (Sect. 2.2.1),
 //                    temperature-table coordinates in IEEE double (Sect. 2.3), the
 //                    table row offset and the four bilinear weights of the point, and
@@ -14,10 +14,10 @@
 //                    scan (lane-local composition, 5 shuffle levels, lane-local apply).
 //   finalize_kernel  one warp per interface: fixed-order FP64 sums of the per-item
 //                    partials -> bolometric fluxes (deterministic).
-//   metric_kernel    one thread per layer: net-flux divergence and the convergence
-//                    metric of eq. (29), reduced per atmosphere with an order-free max.
-//   step_kernel      one thread per layer: convergence decision and the FP64 temperature
-//                    step of eqs. (24)-(28) with the oscillation rule.
+//   temp_kernel      one block per atmosphere, a thread per layer: net-flux divergence,
+//                    the convergence metric of eq. (29) reduced with an exact max, the
+//                    convergence decision and the FP64 temperature step of eqs. (24)-(28)
+//                    with the oscillation rule.
 //
 // Fluxes are carried in the sweep as deviations from the local two-stream Planck flux,
 // G = F - 2 pi eps B_l(T_p).  With per-sublayer transmission Ts, reflection Rs and
@@ -105,7 +105,6 @@ struct PlanDev {
     float* dT_sub;              // [sublayers] T_a - T_b (grey mode)
     float* warm;                // warm-start G_up per column, lane-interleaved
     double* part;               // per-item partial sums [3][n+1]
-    unsigned long long* metric_bits;   // [A] max |dF|/(sigma T^4) as ordered bits
     int G, TB, A;
     float dtau_iso;
     int iso_layers;             // 1: isothermal-layer grid (both points of layer i at T_i)
@@ -623,6 +622,7 @@ __global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, doubl
     if (i > n) return;
     const double* part = P.part + ad.part_off;
     double su = 0.0, sd = 0.0, sb = 0.0;
+#pragma unroll 4
     for (int t = lane; t < ad.n_items; t += 32) {
         su += part[t * stride + i];
         sd += part[t * stride + (n + 1) + i];
@@ -652,40 +652,49 @@ __device__ __forceinline__ double layer_divergence(const double* fu, const doubl
     return (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
 }
 
-// metric of eq. (29) per layer, max-reduced per atmosphere (non-negative doubles order like
-// their bit patterns, NaN above +inf, so an integer atomicMax is an exact, order-free max)
-__global__ void metric_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
-                              const double* __restrict__ T_layer, const int* __restrict__ status, int total_layers)
-{
-    const int li = blockIdx.x * blockDim.x + threadIdx.x;
-    if (li >= total_layers) return;
-    const int a = P.lay_atm[li];
-    if (status[a] != 0) return;
-    const AtmDesc ad = P.atms[a];
-    const int i = li - ad.lay_off;
-    const double dF = layer_divergence(Fup + ad.if_off, Fdn + ad.if_off, i);
-    const double Ti = T_layer[li];
-    double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
-    if (!(m == m) || !isfinite(Ti) || isinf(m)) m = __longlong_as_double(0x7ff8000000000000ll);
-    atomicMax(P.metric_bits + a, (unsigned long long)__double_as_longlong(m));
-}
-
-// one thread per layer; iters/status of each atmosphere are written by its layer-0 thread
-// only after every layer has read them (iters is read here, advanced by the next launch's
-// reader only), so no layer sees a half-updated state
-__global__ void step_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
+// metric (eq. 29) and temperature step (eqs. 23-28, Sect. 2.2.4) of one atmosphere per block
+// (blockDim >= n, a multiple of 32): the block reduces the metric itself, so no separate
+// reduction launch and no atomics are needed
+__global__ void temp_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
                             double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
                             uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
-                            double* __restrict__ metric_out, int* __restrict__ n_active, int total_layers)
+                            double* __restrict__ metric_out, int* __restrict__ n_active)
 {
-    const int li = blockIdx.x * blockDim.x + threadIdx.x;
-    if (li >= total_layers) return;
-    const int a = P.lay_atm[li];
-    const int st0 = status[a];
-    if (st0 != 0) return;
+    __shared__ unsigned long long s_max[32];
+    const int a = blockIdx.x;
+    if (status[a] != 0) return;
     const AtmDesc ad = P.atms[a];
-    const int i = li - ad.lay_off;
-    const double worst = __longlong_as_double((long long)P.metric_bits[a]);
+    const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+    const bool mine = i < ad.n;
+    const int li = ad.lay_off + i;
+    double dF = 0.0, Ti = 1.0;
+    unsigned long long bits = 0ull;
+    if (mine) {
+        dF = layer_divergence(Fup + ad.if_off, Fdn + ad.if_off, i);
+        Ti = T_layer[li];
+        double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
+        if (!(m == m) || !isfinite(Ti) || isinf(m)) m = __longlong_as_double(0x7ff8000000000000ll);
+        bits = (unsigned long long)__double_as_longlong(m);
+    }
+    // non-negative doubles order like their bit patterns (NaN above +inf): an exact max
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, bits, d);
+        bits = o > bits ? o : bits;
+    }
+    if (lane == 0) s_max[w] = bits;
+    __syncthreads();
+    if (w == 0) {
+        bits = lane < (int)(blockDim.x >> 5) ? s_max[lane] : 0ull;
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, bits, d);
+            bits = o > bits ? o : bits;
+        }
+        if (lane == 0) s_max[0] = bits;
+    }
+    __syncthreads();
+    const double worst = __longlong_as_double((long long)s_max[0]);
     const bool bad = !(worst == worst);
     if (i == 0) {
         const int itn = (iters ? iters[a] : 0) + 1;
@@ -700,11 +709,7 @@ __global__ void step_kernel(PlanDev P, TempArgs targ, const double* __restrict__
             if (n_active) atomicSub(n_active, 1);
         }
     }
-    if (bad || worst < targ.tol) return;
-    // eqs. (24)-(28): rho, c_p, dz, t_rad and g cancel, leaving
-    // dT_i = -m_i fpre_num sgn(dF) |dF|^(1 - fpre_exp) / (sigma T_i^3 ln(P_int,i/P_int,i+1))
-    const double dF = layer_divergence(Fup + ad.if_off, Fdn + ad.if_off, i);
-    const double Ti = T_layer[li];
+    if (!mine || bad || worst < targ.tol) return;
     double step = 0.0;
     if (dF != 0.0) {
         const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) / (targ.sigma * Ti * Ti * Ti * P.lnr[li]);

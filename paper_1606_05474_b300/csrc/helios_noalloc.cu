@@ -225,7 +225,6 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     P.wq = c.take<float4>(NP); P.invT = c.take<float2>(NP); P.Tf = c.take<float>(NP);
     P.invT_old = c.take<float2>(NP); P.dinv_step = c.take<float>(NP); P.dT_step = c.take<float>(NP);
     P.dinv_sub = c.take<float>(NS); P.dT_sub = c.take<float>(NS);
-    P.metric_bits = c.take<unsigned long long>(1);
     P.part = c.take<double>((size_t)items * 3 * (n + 1));
     P.warm = c.take<float>((size_t)L * G * W);
     if (c.off > kScratchBytes)
