@@ -89,6 +89,10 @@ def _load():
     lib.ref_layer_exact.argtypes = [d, d, d, d, d, d, P(ctypes.c_double), P(ctypes.c_double)]
     lib.ref_flux_sweep.restype = i
     lib.ref_flux_sweep.argtypes = [P(RefAtm), P(RefParams), vp, i, i, vp, i, vp, vp, vp, vp, vp]
+    lib.ref_flux_direct.restype = i
+    lib.ref_flux_direct.argtypes = [P(RefAtm), P(RefParams), vp, i, vp, vp, vp]
+    lib.ref_layer_affine.restype = None
+    lib.ref_layer_affine.argtypes = [d, d, d, d, d, P(RefParams), vp]
     lib.ref_flux_sweep_iso.restype = i
     lib.ref_flux_sweep_iso.argtypes = [P(RefAtm), P(RefParams), vp, i, vp, vp, vp]
     lib.ref_temp_update.restype = i
@@ -252,6 +256,25 @@ def flux_sweep_iso(atm: Atm, T: np.ndarray, n_passes: int = None, p: RefParams =
     rc = _load().ref_flux_sweep_iso(ctypes.byref(atm.s), ctypes.byref(p), T.ctypes.data, n_passes,
                                     Fu.ctypes.data, Fd.ctypes.data, toa.ctypes.data)
     return {"Fup": Fu, "Fdn": Fd, "toa": toa, "rc": rc}
+
+
+def flux_direct(atm: Atm, T: np.ndarray, iso: bool = False, p: RefParams = None):
+    """Exact solution of the coupled two-stream column equations (ref_flux_direct): the limit of
+    infinitely many scattering passes.  Returns dict(Fup, Fdn, toa)."""
+    p = p or params()
+    n = atm.n
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    Fu = np.empty(n + 1); Fd = np.empty(n + 1); toa = np.empty(atm.L)
+    rc = _load().ref_flux_direct(ctypes.byref(atm.s), ctypes.byref(p), T.ctypes.data, 1 if iso else 0,
+                                 Fu.ctypes.data, Fd.ctypes.data, toa.ctypes.data)
+    return {"Fup": Fu, "Fdn": Fd, "toa": toa, "rc": rc}
+
+
+def layer_affine(B1, B2, dtau, w0, g0, p: RefParams = None):
+    p = p or params()
+    c = np.empty(6)
+    _load().ref_layer_affine(B1, B2, dtau, w0, g0, ctypes.byref(p), c.ctypes.data)
+    return c
 
 
 class State:

@@ -624,6 +624,215 @@ int ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* The layer solutions of Sect. 2.1.3 are affine in the incoming fluxes:
+ *     F2up = c[0] F1up + c[1] F2dn + c[2],   F1dn = c[3] F2dn + c[4] F1up + c[5].
+ * ref_layer_affine returns the six coefficients of ref_layer_twostream's layer
+ * (eq. 14 for pure scattering, eq. 11 below dtau_iso, else eq. 15, with the same
+ * readings); iso_affine those of an isothermal layer of Planck intensity B
+ * (eq. 9 without scattering, eq. 10 with it, eq. 14 for pure scattering). */
+void ref_layer_affine(double B1, double B2, double dtau, double w0, double g0, const ref_params* p, double* c)
+{
+    const double D = p->D, eps = 1.0 / D;
+    if (1.0 - w0 < p->w0_pure) {                                                /* eq. (14) */
+        double a = D * (1.0 - g0) * dtau;
+        c[0] = c[3] = 2.0 / (2.0 + a);
+        c[1] = c[4] = a / (2.0 + a);
+        c[2] = c[5] = 0.0;
+        return;
+    }
+    double trans = exp(-D * sqrt((1.0 - w0 * g0) * (1.0 - w0)) * dtau);        /* eq. (8) */
+    double r = sqrt((1.0 - w0) / (1.0 - w0 * g0));
+    double zp = 0.5 * (1.0 + r), zm = 0.5 * (1.0 - r);                          /* eq. (13) */
+    double alpha = zm * zm * trans * trans - zp * zp;                           /* eq. (12) */
+    double beta = zp * zm * (1.0 - trans * trans);
+    double xi = (zm * zm - zp * zp) * trans;
+    c[0] = c[3] = xi / alpha;
+    c[1] = c[4] = -beta / alpha;
+    if (dtau < p->dtau_iso) {                                                   /* eq. (11) */
+        double ups = (zm * zm * trans + zp * zp) * (1.0 - trans);
+        double B = 0.5 * (B1 + B2);
+        c[2] = c[5] = 2.0 * PI * eps * B * (beta - ups) / alpha;
+        return;
+    }
+    double Bp = (B1 - B2) / dtau;                                               /* eq. (15) */
+    double g = eps * Bp / (p->printed_gradient ? (1.0 + w0 * g0) : (1.0 - w0 * g0));
+    c[2] = 2.0 * PI * eps * (B2 * (alpha + beta) - B1 * xi + g * (alpha - xi - beta)) / alpha;
+    c[5] = 2.0 * PI * eps * (B1 * (alpha + beta) - B2 * xi + g * (xi - alpha + beta)) / alpha;
+}
+
+static void iso_affine(double B, double dtau, double w0, double g0, const ref_params* p, double* c)
+{
+    const double D = p->D, eps = 1.0 / D;
+    if (1.0 - w0 < p->w0_pure) {                                                /* eq. (14) */
+        double a = D * (1.0 - g0) * dtau;
+        c[0] = c[3] = 2.0 / (2.0 + a);
+        c[1] = c[4] = a / (2.0 + a);
+        c[2] = c[5] = 0.0;
+        return;
+    }
+    double trans = exp(-D * sqrt((1.0 - w0 * g0) * (1.0 - w0)) * dtau);        /* eq. (8) */
+    if (w0 == 0.0) {                                                            /* eq. (9) */
+        c[0] = c[3] = trans;
+        c[1] = c[4] = 0.0;
+        c[2] = c[5] = 2.0 * PI * eps * B * (1.0 - trans);
+        return;
+    }
+    double r = sqrt((1.0 - w0) / (1.0 - w0 * g0));
+    double zp = 0.5 * (1.0 + r), zm = 0.5 * (1.0 - r);
+    double alpha = zm * zm * trans * trans - zp * zp;
+    double beta = zp * zm * (1.0 - trans * trans);
+    double xi = (zm * zm - zp * zp) * trans;
+    double ups = (zm * zm * trans + zp * zp) * (1.0 - trans);
+    c[0] = c[3] = xi / alpha;                                                   /* eq. (10) */
+    c[1] = c[4] = -beta / alpha;
+    c[2] = c[5] = 2.0 * PI * eps * B * (beta - ups) / alpha;
+}
+
+/* Solve A x = b for a square matrix whose nonzeros lie within kl sub- and ku
+ * super-diagonals: Gaussian elimination with partial pivoting, the loops limited
+ * to the band (pivoting widens the upper band to ku + kl).  A is dense, row-major,
+ * overwritten; x returned in b.  Returns -1 on a zero pivot. */
+static int band_solve(int N, int kl, int ku, double* A, double* b)
+{
+    for (int j = 0; j < N; ++j) {
+        int piv = j;
+        int last = j + kl < N - 1 ? j + kl : N - 1;
+        for (int i = j + 1; i <= last; ++i)
+            if (fabs(A[(size_t)i * N + j]) > fabs(A[(size_t)piv * N + j])) piv = i;
+        if (A[(size_t)piv * N + j] == 0.0) return -1;
+        int cmax = j + ku + kl < N - 1 ? j + ku + kl : N - 1;
+        if (piv != j) {
+            for (int k = j; k <= cmax; ++k) {
+                double t = A[(size_t)j * N + k]; A[(size_t)j * N + k] = A[(size_t)piv * N + k]; A[(size_t)piv * N + k] = t;
+            }
+            double t = b[j]; b[j] = b[piv]; b[piv] = t;
+        }
+        for (int i = j + 1; i <= last; ++i) {
+            double f = A[(size_t)i * N + j] / A[(size_t)j * N + j];
+            if (f == 0.0) continue;
+            for (int k = j; k <= cmax; ++k) A[(size_t)i * N + k] -= f * A[(size_t)j * N + k];
+            b[i] -= f * b[j];
+        }
+    }
+    for (int j = N - 1; j >= 0; --j) {
+        int cmax = j + ku + kl < N - 1 ? j + ku + kl : N - 1;
+        double s = b[j];
+        for (int k = j + 1; k <= cmax; ++k) s -= A[(size_t)j * N + k] * b[k];
+        b[j] = s / A[(size_t)j * N + j];
+    }
+    return 0;
+}
+
+/* The exact solution of the coupled two-stream equations of every column: the
+ * limit that the scattering passes of Sect. 2.2.3 approach (each pass is one
+ * sweep of a block Gauss-Seidel iteration on this system).  Per (bin, g) the
+ * unknowns are the upward and downward fluxes at the N points of the column
+ * (x[2k] = F_up,k, x[2k+1] = F_dn,k); the equations are the BOA condition
+ * F_up,0 - F_dn,0 = pi B_int (eq. 22), the two layer equations of every
+ * (sub)layer in affine form, and the TOA condition F_dn,N-1 = TOA (eq. 20);
+ * solved by banded Gaussian elimination.  iso = 0: the sublayered grid of
+ * ref_flux_sweep; iso = 1: the isothermal-layer grid of ref_flux_sweep_iso.
+ * Outputs as those functions.  Returns 0, or -1 on a non-finite flux or a
+ * singular system. */
+int ref_flux_direct(const ref_atm* a, const ref_params* p, const double* T, int iso,
+                    double* Fup_bol, double* Fdn_bol, double* Fup_toa)
+{
+    const int n = a->n, L = a->L, G = a->G, np = 2 * n + 1;
+    const int N = iso ? n + 1 : np;               /* points of a column */
+    double* lp = (double*)malloc(sizeof(double) * np);
+    double* Pp = (double*)malloc(sizeof(double) * np);
+    double* dm = (double*)malloc(sizeof(double) * (np - 1));
+    double* Tq = (double*)malloc(sizeof(double) * np);
+    double* gx = (double*)malloc(sizeof(double) * G);
+    double* gw = (double*)malloc(sizeof(double) * G);
+    double* toa = (double*)malloc(sizeof(double) * L);
+    double* bint = (double*)malloc(sizeof(double) * L);
+    int* iP = (int*)malloc(sizeof(int) * np);
+    int* iT = (int*)malloc(sizeof(int) * np);
+    double* wP = (double*)malloc(sizeof(double) * np);
+    double* wT = (double*)malloc(sizeof(double) * np);
+    double* dml = (double*)malloc(sizeof(double) * N);
+    double* up_bin = (double*)calloc((size_t)L * (n + 1), sizeof(double));
+    double* dn_bin = (double*)calloc((size_t)L * (n + 1), sizeof(double));
+    int bad = 0;
+
+    ref_grid(a, lp, Pp, dm, NULL);
+    ref_gauss_legendre(G, gx, gw);
+    ref_boundary_spectra(a, toa, bint);
+    /* opacity sample points: the column's points (sublayered grid) or the layer
+     * centres (isothermal grid) */
+    const int nq = iso ? n : np;
+    if (iso) {
+        for (int i = 0; i < n; ++i) {
+            Tq[i] = T[i];
+            dml[i] = (Pp[2 * i] - Pp[2 * i + 2]) / a->grav;
+            ref_table_coord(lp[2 * i + 1], a->log10P0, a->dlog10P, a->nP, &iP[i], &wP[i]);
+        }
+    } else {
+        ref_point_temperatures(n, T, Tq);
+        for (int q = 0; q < np; ++q) ref_table_coord(lp[q], a->log10P0, a->dlog10P, a->nP, &iP[q], &wP[q]);
+    }
+    for (int q = 0; q < nq; ++q) ref_table_coord(Tq[q], a->T0, a->dT, a->nT, &iT[q], &wT[q]);
+
+#pragma omp parallel for schedule(dynamic, 2) reduction(| : bad)
+    for (int l = 0; l < L; ++l) {
+        const int M2 = 2 * N;
+        double* B = (double*)malloc(sizeof(double) * nq);
+        double* kap = (double*)malloc(sizeof(double) * nq);
+        double* A = (double*)malloc(sizeof(double) * (size_t)M2 * M2);
+        double* x = (double*)malloc(sizeof(double) * M2);
+        const double w0 = a->omega0[l], g0 = a->g0[l];
+        for (int q = 0; q < nq; ++q) B[q] = bin_planck(a, l, Tq[q]);
+        if (Fup_toa) Fup_toa[l] = 0.0;
+        for (int g = 0; g < G; ++g) {
+            const double wg = 0.5 * gw[g];
+            for (int q = 0; q < nq; ++q) {
+                int i1 = a->nP > 1 ? iP[q] + 1 : iP[q], j1 = a->nT > 1 ? iT[q] + 1 : iT[q];
+                double k00 = table_value(a, iP[q], iT[q], l, g), k10 = table_value(a, i1, iT[q], l, g);
+                double k01 = table_value(a, iP[q], j1, l, g), k11 = table_value(a, i1, j1, l, g);
+                kap[q] = (1.0 - wT[q]) * ((1.0 - wP[q]) * k00 + wP[q] * k10)
+                       + wT[q] * ((1.0 - wP[q]) * k01 + wP[q] * k11);
+            }
+            memset(A, 0, sizeof(double) * (size_t)M2 * M2);
+            A[0] = 1.0; A[1] = -1.0; x[0] = bint[l];                    /* eq. (22) */
+            for (int s = 0; s < N - 1; ++s) {
+                double c[6];
+                if (iso) iso_affine(B[s], kap[s] * dml[s], w0, g0, p, c);
+                else ref_layer_affine(B[s], B[s + 1], 0.5 * (kap[s] + kap[s + 1]) * dm[s], w0, g0, p, c);
+                double* ru = A + (size_t)(2 * s + 1) * M2;              /* F_up,s+1 equation */
+                ru[2 * s + 2] = 1.0; ru[2 * s] = -c[0]; ru[2 * s + 3] = -c[1]; x[2 * s + 1] = c[2];
+                double* rd = A + (size_t)(2 * s + 2) * M2;              /* F_dn,s equation */
+                rd[2 * s + 1] = 1.0; rd[2 * s + 3] = -c[3]; rd[2 * s] = -c[4]; x[2 * s + 2] = c[5];
+            }
+            A[(size_t)(M2 - 1) * M2 + (M2 - 1)] = 1.0; x[M2 - 1] = toa[l];    /* eq. (20) */
+            if (band_solve(M2, 2, 2, A, x) != 0) { bad = 1; continue; }
+            /* interface fluxes: every point of the isothermal grid, the even points
+             * of the sublayered grid */
+            for (int i = 0; i <= n; ++i) {
+                const int k = iso ? i : 2 * i;
+                up_bin[(size_t)l * (n + 1) + i] += wg * x[2 * k];
+                dn_bin[(size_t)l * (n + 1) + i] += wg * x[2 * k + 1];
+                if (!isfinite(x[2 * k]) || !isfinite(x[2 * k + 1])) bad = 1;
+            }
+            if (Fup_toa) Fup_toa[l] += wg * x[2 * (N - 1)];
+        }
+        free(B); free(kap); free(A); free(x);
+    }
+    for (int i = 0; i <= n; ++i) {
+        double su = 0.0, sd = 0.0;
+        for (int l = 0; l < L; ++l) {
+            su += up_bin[(size_t)l * (n + 1) + i];
+            sd += dn_bin[(size_t)l * (n + 1) + i];
+        }
+        Fup_bol[i] = su;
+        Fdn_bol[i] = sd;
+    }
+    free(lp); free(Pp); free(dm); free(Tq); free(gx); free(gw); free(toa); free(bint);
+    free(iP); free(iT); free(wP); free(wT); free(dml); free(up_bin); free(dn_bin);
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One radiative-equilibrium temperature step, Sects. 2.2.3-2.2.4.
  *
  * Net flux F_- = F_up - F_dn at each interface; divergence of layer i

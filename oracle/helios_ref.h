@@ -94,6 +94,9 @@ int    ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, in
                       double* Fup_spec, double* Fdn_spec);
 int    ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, int n_passes,
                           double* Fup_bol, double* Fdn_bol, double* Fup_toa);
+void   ref_layer_affine(double B1, double B2, double dtau, double w0, double g0, const ref_params* p, double* c);
+int    ref_flux_direct(const ref_atm* a, const ref_params* p, const double* T, int iso,
+                       double* Fup_bol, double* Fdn_bol, double* Fup_toa);
 int    ref_temp_update(const ref_atm* a, const ref_params* p, const double* Fup_bol, const double* Fdn_bol,
                        double* T, double* mult, int* hist, int* nhist, double* metric, double* dT);
 int    ref_solve_re(const ref_atm* a, const ref_params* p, double* T, double* mult, int* hist, int* nhist,
