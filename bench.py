@@ -226,6 +226,36 @@ def run_gpu(args):
         solve = {"wall_s": round(dt, 4), "iters": int(iters.item()), "status": int(status.item()),
                  "atm_per_s": round(1.0 / dt, 3), "tol": 1e-7}
 
+    # ---- the exact column solve (the limit of the passes, Sect. 2.2.3) against 1 + 4 passes, the
+    # RE solve with it, and the post-processing spectrum (isothermal layers, Sect. 3) with
+    # 1 + 80 passes against the exact solve; each sweep timed cold-start after an L2 flush
+    direct = None
+    if not args.no_solve:
+        def time_sweeps(pl, Tt, npass, reps=20):
+            pl.flux_sweep(Tt, n_passes=npass, warm=False, want_toa=True)
+            pl.set_timing(reps)
+            for _ in range(reps):
+                flush.zero_()
+                pl.flux_sweep(Tt, n_passes=npass, warm=False, want_toa=True)
+            torch.cuda.synchronize()
+            return round(float(np.median(pl.sweep_times(reps))), 5)
+        Tc = Ts.clone()
+        ms_dir, ms_pass = time_sweeps(plan, Tc, hp.DIRECT), time_sweeps(plan, Tc, n_passes)
+        pd = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(direct=1))
+        Td = T0.clone()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        it_d, st_d = pd.solve_re(Td)
+        torch.cuda.synchronize()
+        dt_d = time.time() - t0
+        pp = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(iso_layers=1))
+        direct = {"sweep_ms_exact": ms_dir, "sweep_ms_passes": ms_pass, "passes": n_passes,
+                  "re_solve_exact": {"wall_s": round(dt_d, 4), "iters": int(it_d.item()), "status": int(st_d.item()),
+                                     "max_dT_vs_passes_K": round(float((Td - Ts).abs().max()), 4)},
+                  "post_processing_spectrum_ms": {"isothermal_layers_81_passes": time_sweeps(pp, Tc, 81),
+                                                  "isothermal_layers_exact": time_sweeps(pp, Tc, hp.DIRECT)}}
+        del pd, pp
+
     if rank != 0:
         return
     P = peaks()
@@ -257,6 +287,7 @@ def run_gpu(args):
         "gpu_launches": n_launch_per_step * args.steps,
         "clocks": clk,
         "re_solve": solve,
+        "exact_column_solve": direct,
         "wall_s": round(wall, 3),
     }
     if not args.no_cpu_baseline:

@@ -48,6 +48,11 @@ enum {
     HELIOS_ENOCONV = -5     /* helios_solve_re: some atmosphere did not converge (see status[]) */
 };
 
+/* n_passes value of helios_flux_sweep: instead of a number of scattering passes, solve each
+ * column's coupled two-stream equations exactly -- the limit the passes of Sect. 2.2.3
+ * approach (the adding method, warp-parallel; fluxes then do not depend on a warm start). */
+#define HELIOS_DIRECT (-1)
+
 /* Per-atmosphere status of the radiative-equilibrium iteration. */
 enum {
     HELIOS_ATM_ACTIVE = 0,        /* still iterating */
@@ -137,6 +142,9 @@ typedef struct {
                             WHILE node repeats check_every steps until no atmosphere is active (no host
                             round trip); 0: the host relaunches a graph of check_every steps and reads
                             the active count in between */
+    int direct;          /* 1: evaluations with the plan's default passes (n_passes = 0, and every step
+                            of helios_solve_re) solve each column's coupled equations exactly instead of
+                            making 1 + n_scat passes (HELIOS_DIRECT below) */
 } helios_params_t;
 
 void helios_default_params(helios_params_t* p);
@@ -198,7 +206,8 @@ int helios_interp_opacity(helios_plan* plan, const double* T_layer, float* kappa
  * pure scattering eq. 14), n_passes down/up passes with the boundary
  * conditions of eqs. 20 and 22, Gauss-point sum (eq. 31) and bin sum.
  *   T_layer  device, double [layers]
- *   n_passes >= 1, or 0 for the plan's default (1 + n_scat with scattering)
+ *   n_passes >= 1, or 0 for the plan's default (1 + n_scat with scattering, or
+ *            HELIOS_DIRECT when the plan's params.direct is set), or HELIOS_DIRECT
  *   warm     0: the coupled stream starts from zero (first temperature step);
  *            1: it starts from the upward fluxes of this plan's previous
  *               evaluation (later temperature steps, Sect. 2.2.3)

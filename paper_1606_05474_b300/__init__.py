@@ -24,6 +24,9 @@ def build(force: bool = False) -> str:
     return _b(force=force)
 
 
+DIRECT = _lib.HELIOS_DIRECT
+
+
 def default_params(**overrides) -> _lib.Params:
     p = _lib.Params()
     _lib.load().helios_default_params(ctypes.byref(p))
@@ -232,8 +235,8 @@ class Plan:
     def emission_spectrum(self, T, n_passes=81, stream=None):
         """Emergent spectrum of converged temperatures T (Sect. 3: computed as a post-processing
         step, on a plan made with iso_layers=1 and the spectrum's bins; Sect. 2.2.3: 80
-        additional scattering passes).  One cold-start evaluation; returns (Fup_toa per bin,
-        Fup_bol, Fdn_bol)."""
+        additional scattering passes, or n_passes=DIRECT for their limit).  One cold-start
+        evaluation; returns (Fup_toa per bin, Fup_bol, Fdn_bol)."""
         Fu, Fd, toa = self.flux_sweep(T, n_passes=n_passes, warm=False, want_toa=True, stream=stream)
         return toa, Fu, Fd
 

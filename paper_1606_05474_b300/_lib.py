@@ -8,6 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SO_PATH = os.path.join(HERE, "libhelios.so")
 
 HELIOS_OK, HELIOS_EINVAL, HELIOS_ENOMEM, HELIOS_ECUDA, HELIOS_ENOCONV = 0, -1, -2, -3, -5
+HELIOS_DIRECT = -1          # n_passes: the exact column solve instead of scattering passes
 ATM_ACTIVE, ATM_CONVERGED, ATM_NOT_CONVERGED, ATM_NONFINITE = 0, 1, 2, 3
 
 c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
@@ -32,7 +33,7 @@ class Params(ctypes.Structure):
                 ("fpre_num", c_double), ("fpre_exp", c_double), ("osc_down", c_double), ("osc_up", c_double),
                 ("mult_max", c_double), ("T_floor", c_double), ("n_scat", c_int), ("max_iter", c_int),
                 ("grey_mode", c_int), ("printed_gradient", c_int), ("bins_per_item", c_int),
-                ("check_every", c_int), ("persistent", c_int), ("iso_layers", c_int), ("device_loop", c_int)]
+                ("check_every", c_int), ("persistent", c_int), ("iso_layers", c_int), ("device_loop", c_int), ("direct", c_int)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -132,12 +132,13 @@ size_t sweep_smem(int M, int G)
 }
 
 // lane chunks up to 7 fit two 640-thread blocks per SM within the register file (48 registers)
-template <int M> constexpr int sweep_minb() { return M <= 7 ? 2 : 1; }
+// (the direct column solve holds more per-lane arrays: one block per SM, 96 registers)
+template <int M, bool DIRECT> constexpr int sweep_minb() { return (M <= 7 && !DIRECT) ? 2 : 1; }
 
-template <int M>
-int sweep_occupancy_M(int threads, size_t smem)
+template <int M, bool DIRECT>
+int sweep_occupancy_MD(int threads, size_t smem)
 {
-    auto k = sweep_kernel<M, sweep_minb<M>()>;
+    auto k = sweep_kernel<M, sweep_minb<M, DIRECT>(), DIRECT>;
     int nb = 0;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess)
@@ -145,18 +146,24 @@ int sweep_occupancy_M(int threads, size_t smem)
     return nb;
 }
 
-// resident sweep blocks per SM for lane chunk M, block size and dynamic shared memory (0 on error)
-int sweep_occupancy(int M, int threads, size_t smem)
+template <int M>
+int sweep_occupancy_M(int threads, size_t smem, bool direct)
+{
+    return direct ? sweep_occupancy_MD<M, true>(threads, smem) : sweep_occupancy_MD<M, false>(threads, smem);
+}
+
+// resident sweep blocks per SM for lane chunk M, block size, dynamic shared memory and mode (0 on error)
+int sweep_occupancy(int M, int threads, size_t smem, bool direct = false)
 {
     switch (M) {
-        case 1: return sweep_occupancy_M<1>(threads, smem);
-        case 3: return sweep_occupancy_M<3>(threads, smem);
-        case 5: return sweep_occupancy_M<5>(threads, smem);
-        case 7: return sweep_occupancy_M<7>(threads, smem);
-        case 9: return sweep_occupancy_M<9>(threads, smem);
-        case 11: return sweep_occupancy_M<11>(threads, smem);
-        case 13: return sweep_occupancy_M<13>(threads, smem);
-        case 15: return sweep_occupancy_M<15>(threads, smem);
+        case 1: return sweep_occupancy_M<1>(threads, smem, direct);
+        case 3: return sweep_occupancy_M<3>(threads, smem, direct);
+        case 5: return sweep_occupancy_M<5>(threads, smem, direct);
+        case 7: return sweep_occupancy_M<7>(threads, smem, direct);
+        case 9: return sweep_occupancy_M<9>(threads, smem, direct);
+        case 11: return sweep_occupancy_M<11>(threads, smem, direct);
+        case 13: return sweep_occupancy_M<13>(threads, smem, direct);
+        case 15: return sweep_occupancy_M<15>(threads, smem, direct);
         default: return 0;
     }
 }
@@ -178,6 +185,7 @@ struct MGroup {
     int* order;       // device
     int* counter;     // device work counter (persistent launches)
     int grid;         // persistent grid: resident blocks on all SMs
+    int grid_direct;  // the same for the direct column solve
     cudaStream_t stream;   // the group's own stream (several groups overlap)
     cudaEvent_t join;
 };
@@ -238,6 +246,7 @@ void helios_default_params(helios_params_t* p)
     p->persistent = 1;
     p->iso_layers = 0;
     p->device_loop = 1;
+    p->direct = 0;
 }
 
 int helios_version(void) { return HELIOS_VERSION; }
@@ -307,7 +316,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         prm->n_scat < 0 || prm->max_iter < 1 || !(prm->osc_down > 0.0) || !(prm->osc_up > 0.0) ||
         !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0 ||
         prm->persistent < 0 || prm->persistent > 1 || prm->iso_layers < 0 || prm->iso_layers > 1 ||
-        prm->device_loop < 0 || prm->device_loop > 1)
+        prm->device_loop < 0 || prm->device_loop > 1 || prm->direct < 0 || prm->direct > 1)
         return fail(HELIOS_EINVAL, "invalid parameter set");
     const int G = tabs[0].G;
     if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
@@ -520,7 +529,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         }
         nu_off += d.L + 1;
     }
-    P->passes = any_scat ? 1 + prm->n_scat : 1;
+    P->passes = prm->direct ? HELIOS_DIRECT : (any_scat ? 1 + prm->n_scat : 1);
 
     // ---- Gauss weights on [0, 1]
     std::vector<double> gy, gwd;
@@ -590,6 +599,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         gr.order = d_order + order.size();
         gr.counter = P->counters + M;
         gr.grid = std::min(gr.count, nsm_all * std::max(1, sweep_occupancy(M, P->threads, sweep_smem(M, G))));
+        gr.grid_direct = std::min(gr.count, nsm_all * std::max(1, sweep_occupancy(M, P->threads, sweep_smem(M, G), true)));
         order.insert(order.end(), byM[M].begin(), byM[M].end());
         P->groups.push_back(gr);
     }
@@ -693,22 +703,23 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, const int* n_acti
     cudaGraphSetConditional(h, (*n_active > 0 && left > 0) ? 1u : 0u);
 }
 
-template <int M, int MINB>
+template <int M, int MINB, bool DIRECT>
 int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
                     float* Fup_toa, cudaStream_t s)
 {
     const size_t smem = sweep_smem(M, p->G);
-    static thread_local int configured_dev[kMaxM + 1][3] = {};
-    if (configured_dev[M][MINB] != p->ctx->device + 1) {
-        CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        configured_dev[M][MINB] = p->ctx->device + 1;
+    static thread_local int configured_dev[kMaxM + 1][3][2] = {};
+    if (configured_dev[M][MINB][DIRECT] != p->ctx->device + 1) {
+        CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+        configured_dev[M][MINB][DIRECT] = p->ctx->device + 1;
     }
     if (p->prm.persistent) {
-        sweep_kernel<M, MINB><<<gr.grid, p->threads, smem, s>>>(p->dev, gr.order, gr.count, gr.counter, status,
-                                                              n_passes, warm_valid, Fup_toa);
+        sweep_kernel<M, MINB, DIRECT><<<DIRECT ? gr.grid_direct : gr.grid, p->threads, smem, s>>>(
+            p->dev, gr.order, gr.count, gr.counter, status, n_passes, warm_valid, Fup_toa);
     } else {
-        sweep_kernel<M, MINB><<<gr.count, p->threads, smem, s>>>(p->dev, gr.order, gr.count, nullptr, status,
-                                                               n_passes, warm_valid, Fup_toa);
+        sweep_kernel<M, MINB, DIRECT><<<gr.count, p->threads, smem, s>>>(p->dev, gr.order, gr.count, nullptr, status,
+                                                                       n_passes, warm_valid, Fup_toa);
     }
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
@@ -718,7 +729,9 @@ template <int M>
 int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
                    float* Fup_toa, cudaStream_t s)
 {
-    return launch_sweep_MB<M, sweep_minb<M>()>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+    if (n_passes == HELIOS_DIRECT)
+        return launch_sweep_MB<M, sweep_minb<M, true>(), true>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+    return launch_sweep_MB<M, sweep_minb<M, false>(), false>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
 }
 
 int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, float* Fup_toa, cudaStream_t s)
@@ -817,7 +830,7 @@ int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int w
                       double* Fdn_bol, float* Fup_toa, cudaStream_t s)
 {
     if (!p || !T_layer || !Fup_bol || !Fdn_bol) return fail(HELIOS_EINVAL, "helios_flux_sweep: null argument");
-    if (n_passes < 0) return fail(HELIOS_EINVAL, "helios_flux_sweep: n_passes = %d", n_passes);
+    if (n_passes < HELIOS_DIRECT) return fail(HELIOS_EINVAL, "helios_flux_sweep: n_passes = %d", n_passes);
     if (n_passes == 0) n_passes = p->passes;
     CUDA_TRY(cudaSetDevice(p->ctx->device));
     const int warm_valid = (warm && p->warm_ready) ? 1 : 0;

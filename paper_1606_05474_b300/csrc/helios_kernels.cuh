@@ -270,8 +270,12 @@ __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const
 
 // Two-stream coefficients of one sublayer in deviation form (see file header).
 // dB = 2 pi eps (B_bottom - B_top).
+// With WANT_E the absorption Es = 1 - Ts - Rs of the sublayer is returned too, formed without
+// cancellation: expanding eqs. (12)-(13), 1 - Ts - Rs = (1 - q)(1 - trans)(1 - q trans) d
+// (zero for pure scattering); omq = 1 - q of the bin.
+template <bool WANT_E = false>
 __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
-                                           float& Ts, float& Rs, float& Ss)
+                                           float& Ts, float& Rs, float& Ss, float* Es = nullptr, float omq = 0.0f)
 {
     if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source, G = F
         const float a = b.gam * dtau;
@@ -279,6 +283,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
         Ts = t;
         Rs = a * t;
         Ss = 0.0f;
+        if constexpr (WANT_E) *Es = 0.0f;
         return;
     }
     float phi, u, tr;
@@ -288,6 +293,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
         Ts = tr;
         Rs = 0.0f;
         Ss = (iso || dtau == 0.0f) ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
+        if constexpr (WANT_E) *Es = u;
         return;
     }
     // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha.  Reciprocals and
@@ -305,11 +311,135 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     Ts = step ? 1.0f : Ts;
     Rs = step ? 0.0f : Rs;
     Ss = step ? dB : Ss;
+    if constexpr (WANT_E) *Es = step ? 0.0f : omq * u * fmaf(-b.q, tr, 1.0f) * d;
+}
+
+// ---------------------------------------------------------------------------
+// 2^-floor(log2 m) for m > 0: scaling by it is exact (projective normalisation)
+__device__ __forceinline__ float pow2_recip(float m)
+{
+    const int e = (__float_as_int(m) >> 23) & 0xff;
+    return __int_as_float((254 - max(1, min(e, 253))) << 23);
+}
+
+// Exact solution of one column's coupled equations (the limit of the passes, Sect. 2.2.3) by
+// the adding method, in deviation form.  With rho_s the reflectance of everything below point s
+// (surface included: rho_0 = 1, since F_up,0 = F_dn,0 + pi B_int) and u_s the upward deviation
+// that stack emits, G_up,s = rho_s G_dn,s + u_s and, per sublayer s,
+//     kappa_s = 1 / (1 - Rs rho_s),  rho_{s+1} = Rs + Ts^2 rho_s kappa_s,
+//     u_{s+1} = Ts kappa_s (u_s - rho_s Ss) + Ss,  G_dn,s = kappa_s (Ts G_dn,s+1 + Rs u_s - Ss).
+// rho is carried in homogeneous coordinates (rho_h, sigma_h), rho = rho_h / (rho_h + sigma_h),
+// sigma = 1 - rho, with the sublayer absorption Es = 1 - Ts - Rs.  Using Ts + Rs + Es = 1 the
+// recurrence becomes the linear map
+//     rho_h' = a rho_h + Rs sigma_h,  sigma_h' = b rho_h + (Ts + Es) sigma_h,
+//     a = Ts (Ts + Rs) + Rs Es,  b = Es (2 Ts + Es),
+// whose entries are all non-negative: neither rho nor 1 - rho is formed by a difference, for
+// conservative scattering over the reflecting surface (rho = 1) as for an absorbing column
+// (rho small); with rho_h + sigma_h = 1 the new sum is 1 - Rs rho = 1/kappa.  Each of the three
+// recurrences (rho up, u up, G_dn down) is a warp scan: lane-local composition of its M
+// sublayers, five shuffle levels (2x2 non-negative matrices, rescaled by powers of two, for rho;
+// affine maps for u and G_dn), lane-local application.  Outputs per point lane*M + k:
+// U[k] = G_up, Dn[k] = G_dn.
+template <int M>
+__device__ __forceinline__ void direct_column(const float (&Ts)[M], const float (&Rs)[M], const float (&Es)[M],
+                                              const float (&Ss)[M], float (&U)[M], float (&Dn)[M], float toa_g,
+                                              float bint, int lane)
+{
+    // (i) (rho_h, sigma_h), upwards from (1, 0)
+    float p00 = 1.0f, p01 = 0.0f, p10 = 0.0f, p11 = 1.0f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float a = fmaf(Ts[k], Ts[k] + Rs[k], Rs[k] * Es[k]), b = Es[k] * fmaf(2.0f, Ts[k], Es[k]);
+        const float r = Rs[k], d = Ts[k] + Es[k];
+        const float n00 = fmaf(a, p00, r * p10), n01 = fmaf(a, p01, r * p11);
+        const float n10 = fmaf(b, p00, d * p10), n11 = fmaf(b, p01, d * p11);
+        p00 = n00; p01 = n01; p10 = n10; p11 = n11;
+    }
+    {
+        const float sc = pow2_recip(fmaxf(fmaxf(p00, p01), fmaxf(p10, p11)));
+        p00 *= sc; p01 *= sc; p10 *= sc; p11 *= sc;
+    }
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+        const int dd = 1 << lv;
+        const float q00 = __shfl_up_sync(FULL, p00, dd), q01 = __shfl_up_sync(FULL, p01, dd);
+        const float q10 = __shfl_up_sync(FULL, p10, dd), q11 = __shfl_up_sync(FULL, p11, dd);
+        if (lane >= dd) {                                   // P <- P . Q (the lanes below act first)
+            const float n00 = fmaf(p00, q00, p01 * q10), n01 = fmaf(p00, q01, p01 * q11);
+            const float n10 = fmaf(p10, q00, p11 * q10), n11 = fmaf(p10, q01, p11 * q11);
+            const float sc = pow2_recip(fmaxf(fmaxf(n00, n01), fmaxf(n10, n11)));
+            p00 = n00 * sc; p01 = n01 * sc; p10 = n10 * sc; p11 = n11 * sc;
+        }
+    }
+    float rh, sh;
+    {
+        const float x = __shfl_up_sync(FULL, p00, 1), y = __shfl_up_sync(FULL, p10, 1);   // P_below (1, 0)
+        const float inv = __frcp_rn(x + y);
+        rh = lane == 0 ? 1.0f : x * inv;
+        sh = lane == 0 ? 0.0f : y * inv;
+    }
+    float rho[M], kap[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float a = fmaf(Ts[k], Ts[k] + Rs[k], Rs[k] * Es[k]), b = Es[k] * fmaf(2.0f, Ts[k], Es[k]);
+        const float d = Ts[k] + Es[k];
+        rho[k] = rh;
+        kap[k] = __frcp_rn(fmaf(d, rh, sh));
+        const float rn = fmaf(a, rh, Rs[k] * sh) * kap[k];
+        sh = fmaf(b, rh, d * sh) * kap[k];
+        rh = rn;
+    }
+    // (ii) u, upwards from u_0 = pi B_int: u' = al u + be, al = Ts kappa, be = Ss (1 - al rho)
+    float A = 1.0f, B = 0.0f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const float al = Ts[k] * kap[k];
+        B = fmaf(al, B, Ss[k] * fmaf(-al, rho[k], 1.0f));
+        A *= al;
+    }
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+        const int dd = 1 << lv;
+        const float Ao = __shfl_up_sync(FULL, A, dd), Bo = __shfl_up_sync(FULL, B, dd);
+        if (lane >= dd) { B = fmaf(A, Bo, B); A *= Ao; }
+    }
+    {
+        const float Ae = __shfl_up_sync(FULL, A, 1), Be = __shfl_up_sync(FULL, B, 1);
+        float uu = lane == 0 ? bint : fmaf(Ae, bint, Be);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            U[k] = uu;                                      // u at point lane*M + k (reused below)
+            const float al = Ts[k] * kap[k];
+            uu = fmaf(al, uu, Ss[k] * fmaf(-al, rho[k], 1.0f));
+        }
+    }
+    // (iii) G_dn, downwards from the TOA: G_dn,s = al G_dn,s+1 + ga, ga = kappa (Rs u - Ss)
+    A = 1.0f; B = 0.0f;
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+        const float al = Ts[k] * kap[k];
+        B = fmaf(al, B, kap[k] * fmaf(Rs[k], U[k], -Ss[k]));
+        A *= al;
+    }
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+        const int dd = 1 << lv;
+        const float Ao = __shfl_down_sync(FULL, A, dd), Bo = __shfl_down_sync(FULL, B, dd);
+        if (lane + dd < 32) { B = fmaf(A, Bo, B); A *= Ao; }
+    }
+    const float Ae = __shfl_down_sync(FULL, A, 1), Be = __shfl_down_sync(FULL, B, 1);
+    float dn = lane == 31 ? toa_g : fmaf(Ae, toa_g, Be);
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+        dn = fmaf(Ts[k] * kap[k], dn, kap[k] * fmaf(Rs[k], U[k], -Ss[k]));
+        Dn[k] = dn;
+        U[k] = fmaf(rho[k], dn, U[k]);                      // G_up = rho G_dn + u
+    }
 }
 
 // ---------------------------------------------------------------------------
 // one work item = (atmosphere, tile of bins); the whole block cooperates
-template <int M>
+template <int M, bool DIRECT>
 __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int* __restrict__ status, int n_passes,
                                            int warm_valid, float* __restrict__ Fup_toa, unsigned char* smem_raw)
 {
@@ -432,112 +562,148 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         __syncthreads();
 
         // ---- phase 2: one warp per Gauss point; lane holds sublayers lane*M .. lane*M+M-1
-        float Ts[M], Rs[M], Ss[M], X[M + 1];
-        float Ap = 1.0f;
-        const float* krow = kap + g * KST;
+        if constexpr (DIRECT) {
+            // the exact column solution (no passes, no warm start needed)
+            float Ts[M], Rs[M], Ss[M], Es[M], U[M], Dn[M];
+            const float* krow = kap + g * KST;
+            const float omq = __fdiv_rn(bc.omq2, 1.0f + bc.q);     // 1 - q
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-            const int s = lane * M + k;
-            float t = 1.0f, r = 0.0f, src = 0.0f;
-            if (s < NS) {
-                const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
+            for (int k = 0; k < M; ++k) {
+                const int s = lane * M + k;
+                float t = 1.0f, r = 0.0f, src = 0.0f, e = 0.0f;
+                if (s < NS) {
+                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                    layer_coef<true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, &e, omq);
+                }
+                Ts[k] = t;
+                Rs[k] = r;
+                Ss[k] = src;
+                Es[k] = e;
             }
-            Ts[k] = t;
-            Rs[k] = r;
-            Ss[k] = src;
-            Ap *= t;
-        }
-        // scan multipliers (depend on the transmissions only)
-        float adn[5], aup[5], adn_fin, aup_fin;
-        {
-            float a = Ap;
+            const float toa_g = bc_toa[0];
+            __syncwarp();                                           // the warp's row is free now
+            direct_column<M>(Ts, Rs, Es, Ss, U, Dn, toa_g, bc.bint, lane);
+            float* red_dn = kap + g * KST;
+            float* red_up = red_dn + (n + 1);
 #pragma unroll
-            for (int lv = 0; lv < 5; ++lv) {
-                const int d = 1 << lv;
-                const float ao = __shfl_down_sync(FULL, a, d);
-                const bool ok = lane + d < 32;
-                adn[lv] = ok ? a : 0.0f;
-                a = ok ? a * ao : a;
+            for (int k = 0; k < M; ++k) {
+                const int p = lane * M + k;
+                if (p < NP && !(p & 1)) {
+                    red_dn[p >> 1] = wg * Dn[k];
+                    red_up[p >> 1] = (p == NS) ? U[k] : wg * U[k];  // TOA: unweighted (double sum)
+                }
             }
-            adn_fin = a;
-            a = Ap;
+            const long long col = (long long)(l * G + g) * W;
 #pragma unroll
-            for (int lv = 0; lv < 5; ++lv) {
-                const int d = 1 << lv;
-                const float ao = __shfl_up_sync(FULL, a, d);
-                const bool ok = lane >= d;
-                aup[lv] = ok ? a : 0.0f;
-                a = ok ? a * ao : a;
+            for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = U[k];
+        } else {
+            float Ts[M], Rs[M], Ss[M], X[M + 1];
+            float Ap = 1.0f;
+            const float* krow = kap + g * KST;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const int s = lane * M + k;
+                float t = 1.0f, r = 0.0f, src = 0.0f;
+                if (s < NS) {
+                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                    layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
+                }
+                Ts[k] = t;
+                Rs[k] = r;
+                Ss[k] = src;
+                Ap *= t;
             }
-            aup_fin = a;
-        }
-        // initial upward deviation: previous evaluation shifted to the new Planck values, or
-        // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero)
-        const long long col = (long long)(l * G + g) * W;
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            const int p = lane * M + k;
-            X[k] = warm_valid ? wbase[col + k * 32 + lane] + dbs[p] : -bt[p];
-        }
-        X[M] = 0.0f;
-        const float toa_g = bc_toa[0];
-        const float bint = bc.bint;
-        __syncwarp();
-        float* red_dn = kap + g * KST;          // this warp's row is free now
-        float* red_up = red_dn + (n + 1);
-        const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
-        for (int pass = 0; pass < K; ++pass) {
-            const bool last = pass == K - 1;
-            // downward sweep: G_dn[s] = Ts G_dn[s+1] + (Rs G_up[s] - Ss), from the TOA
+            // scan multipliers (depend on the transmissions only)
+            float adn[5], aup[5], adn_fin, aup_fin;
             {
-                float b = 0.0f;
+                float a = Ap;
 #pragma unroll
-                for (int k = M - 1; k >= 0; --k) b = fmaf(Ts[k], b, fmaf(Rs[k], X[k], -Ss[k]));
+                for (int lv = 0; lv < 5; ++lv) {
+                    const int d = 1 << lv;
+                    const float ao = __shfl_down_sync(FULL, a, d);
+                    const bool ok = lane + d < 32;
+                    adn[lv] = ok ? a : 0.0f;
+                    a = ok ? a * ao : a;
+                }
+                adn_fin = a;
+                a = Ap;
 #pragma unroll
-                for (int lv = 0; lv < 5; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv), b);
-                const float outv = fmaf(adn_fin, toa_g, b);
-                float inv = __shfl_down_sync(FULL, outv, 1);
-                if (lane == 31) inv = toa_g;
-                X[M] = inv;
+                for (int lv = 0; lv < 5; ++lv) {
+                    const int d = 1 << lv;
+                    const float ao = __shfl_up_sync(FULL, a, d);
+                    const bool ok = lane >= d;
+                    aup[lv] = ok ? a : 0.0f;
+                    a = ok ? a * ao : a;
+                }
+                aup_fin = a;
+            }
+            // initial upward deviation: previous evaluation shifted to the new Planck values, or
+            // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero)
+            const long long col = (long long)(l * G + g) * W;
 #pragma unroll
-                for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], fmaf(Rs[k], X[k], -Ss[k]));
-                if (last) {
+            for (int k = 0; k < M; ++k) {
+                const int p = lane * M + k;
+                X[k] = warm_valid ? wbase[col + k * 32 + lane] + dbs[p] : -bt[p];
+            }
+            X[M] = 0.0f;
+            const float toa_g = bc_toa[0];
+            const float bint = bc.bint;
+            __syncwarp();
+            float* red_dn = kap + g * KST;          // this warp's row is free now
+            float* red_up = red_dn + (n + 1);
+            const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
+            for (int pass = 0; pass < K; ++pass) {
+                const bool last = pass == K - 1;
+                // downward sweep: G_dn[s] = Ts G_dn[s+1] + (Rs G_up[s] - Ss), from the TOA
+                {
+                    float b = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        const int p = lane * M + k;
-                        if (p < NP && !(p & 1)) red_dn[p >> 1] = wg * X[k];
+                    for (int k = M - 1; k >= 0; --k) b = fmaf(Ts[k], b, fmaf(Rs[k], X[k], -Ss[k]));
+#pragma unroll
+                    for (int lv = 0; lv < 5; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv), b);
+                    const float outv = fmaf(adn_fin, toa_g, b);
+                    float inv = __shfl_down_sync(FULL, outv, 1);
+                    if (lane == 31) inv = toa_g;
+                    X[M] = inv;
+#pragma unroll
+                    for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], fmaf(Rs[k], X[k], -Ss[k]));
+                    if (last) {
+#pragma unroll
+                        for (int k = 0; k < M; ++k) {
+                            const int p = lane * M + k;
+                            if (p < NP && !(p & 1)) red_dn[p >> 1] = wg * X[k];
+                        }
+                    }
+                }
+                // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
+                {
+                    float c = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < M; ++k) c = fmaf(Ts[k], c, fmaf(Rs[k], X[k + 1], Ss[k]));
+#pragma unroll
+                    for (int lv = 0; lv < 5; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv), c);
+                    const float boa = __shfl_sync(FULL, X[0], 0) + bint;
+                    const float outv = fmaf(aup_fin, boa, c);
+                    float inv = __shfl_up_sync(FULL, outv, 1);
+                    if (lane == 0) inv = boa;
+                    X[0] = inv;
+#pragma unroll
+                    for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], fmaf(Rs[k], X[k + 1], Ss[k]));
+                    if (last) {
+                        // weighted deviations at the interfaces; the TOA keeps the unweighted value
+                        // so its Gauss sum and the Planck add-back are done in double (emergent spectrum)
+#pragma unroll
+                        for (int k = 1; k <= M; ++k) {
+                            const int p = lane * M + k;
+                            if (p < NP && !(p & 1)) red_up[p >> 1] = (p == NS) ? X[k] : wg * X[k];
+                        }
+                        if (lane == 0) red_up[0] = wg * X[0];
                     }
                 }
             }
-            // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
-            {
-                float c = 0.0f;
 #pragma unroll
-                for (int k = 0; k < M; ++k) c = fmaf(Ts[k], c, fmaf(Rs[k], X[k + 1], Ss[k]));
-#pragma unroll
-                for (int lv = 0; lv < 5; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv), c);
-                const float boa = __shfl_sync(FULL, X[0], 0) + bint;
-                const float outv = fmaf(aup_fin, boa, c);
-                float inv = __shfl_up_sync(FULL, outv, 1);
-                if (lane == 0) inv = boa;
-                X[0] = inv;
-#pragma unroll
-                for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], fmaf(Rs[k], X[k + 1], Ss[k]));
-                if (last) {
-                    // weighted deviations at the interfaces; the TOA keeps the unweighted value
-                    // so its Gauss sum and the Planck add-back are done in double (emergent spectrum)
-#pragma unroll
-                    for (int k = 1; k <= M; ++k) {
-                        const int p = lane * M + k;
-                        if (p < NP && !(p & 1)) red_up[p >> 1] = (p == NS) ? X[k] : wg * X[k];
-                    }
-                    if (lane == 0) red_up[0] = wg * X[0];
-                }
-            }
+            for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = X[k];
         }
-#pragma unroll
-        for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = X[k];
         __syncthreads();
         // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators.
         // Thread t sums column t of the per-warp rows (downward interfaces 0..n, then upward
@@ -586,14 +752,14 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 
 // counter == nullptr: block b takes item order[b].  Otherwise persistent: the resident
 // blocks pull items (in cost order) from the counter until the group is exhausted.
-template <int M, int MINB>
+template <int M, int MINB, bool DIRECT = false>
 __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
                                                          int* __restrict__ counter, const int* __restrict__ status,
                                                          int n_passes, int warm_valid, float* __restrict__ Fup_toa)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!counter) {
-        sweep_item<M>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        sweep_item<M, DIRECT>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
         return;
     }
     __shared__ int s_next;
@@ -602,7 +768,7 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
         __syncthreads();
         const int k = s_next;
         if (k >= count) break;
-        sweep_item<M>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        sweep_item<M, DIRECT>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
         __syncthreads();                    // shared memory is reused by the next item
     }
 }

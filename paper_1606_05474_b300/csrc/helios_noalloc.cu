@@ -279,7 +279,8 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
         q.cl = (float)(lam * eps / (prm->printed_gradient ? (1.0 + w0 * g0) : one_wg));
         q.gam = (float)(D * (1.0 - g0) / 2.0);
     }
-    if (n_passes < 0) return err(HELIOS_EINVAL, "n_passes = %d", n_passes);
+    if (n_passes < 0) return err(HELIOS_EINVAL, "n_passes = %d (the direct column solve needs a plan)", n_passes);
+    if (prm->direct) return err(HELIOS_EINVAL, "the direct column solve needs a plan");
     if (n_passes == 0) n_passes = any_scat ? 1 + prm->n_scat : 1;
     for (int t = 0; t < items; ++t) { h_items[t] = make_int2(0, t); h_order[t] = t; }
     gauss_weights(G, h_gw);

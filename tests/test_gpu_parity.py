@@ -193,3 +193,35 @@ def test_isothermal_layer_grid_temperature_step():
     state = plan.new_state()
     plan.temp_update(Fu, Fd, Tg, state)
     assert rel_err(Tg.cpu().numpy(), st.T) < 1e-12
+
+
+@pytest.mark.parametrize("n,L,iso", [(40, 12, 0), (111, 7, 0), (239, 3, 0), (2, 4, 0), (40, 9, 1), (101, 5, 1)])
+def test_direct_column_solve_matches_oracle(n, L, iso):
+    # the exact solution of the coupled column equations (the limit of the passes of Sect. 2.2.3):
+    # warp-parallel adding method vs the oracle's banded elimination
+    import paper_1606_05474_b300 as hp
+    wl = synth.small_scattering(L=L, n=n)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 6)
+    plan = make_plan(wl, iso_layers=iso)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=hp.DIRECT)
+    r = oracle.flux_direct(atm, T, iso=bool(iso))
+    assert r["rc"] == 0
+    _check_fluxes(Fu, Fd, r)
+    _check_toa(toa, r, atm)
+
+
+def test_direct_column_solve_conservative_scattering():
+    # pure-scattering bins over the reflecting lower boundary: the regime where the reflectance
+    # stays 1 and a naive formulation cancels
+    import paper_1606_05474_b300 as hp
+    wl = synth.small_scattering(L=6, n=60)
+    a = wl.atms[0]
+    a.omega0 = np.ones(a.n_bins, np.float32)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(a, 8)
+    plan = make_plan(wl)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=hp.DIRECT)
+    r = oracle.flux_direct(atm, T)
+    _check_fluxes(Fu, Fd, r)
+    _check_toa(toa, r, atm)

@@ -179,3 +179,16 @@ def test_device_while_loop_and_host_loop_agree_bitwise():
         T = pack([a.T_init for a in wl.atms])
         iters, status = p.solve_re(T)
         assert bool((T == outs[0][0]).all()) and bool((iters == outs[0][1]).all())
+
+
+def test_direct_column_solve_reaches_the_same_equilibrium():
+    # every temperature step with the exact column solution instead of 1 + 4 passes: the same
+    # fixed point (at convergence the warm-started passes reach the exact solution too)
+    wl = synth.small_scattering(L=30, n=40)
+    Tref, _ = _oracle_solve(wl, 0)
+    plan = make_plan(wl, max_iter=100000, direct=1)
+    assert plan.info.passes == -1
+    T = pack([wl.atms[0].T_init])
+    iters, status = plan.solve_re(T)
+    assert status.item() == 1
+    assert np.abs(T.cpu().numpy() - Tref).max() < 0.1

@@ -57,3 +57,16 @@ def test_noalloc_rejects_atmospheres_beyond_its_fixed_size():
     with pytest.raises(hp.HeliosError) as e:
         hp.flux_sweep_noalloc(plan_free, wl.tables[0], kappa, T, out)
     assert e.value.code == -1 and b"n_layers" in hp._lib.load().helios_last_error()
+
+
+def test_no_alloc_rejects_the_direct_solve():
+    import paper_1606_05474_b300 as hp
+    from paper_1606_05474_b300 import HeliosError
+    import synth
+    import torch
+    wl = synth.small_scattering(L=4, n=10)
+    kap = torch.from_numpy(wl.tables[0].kappa32).cuda()
+    T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).cuda()
+    Fu = torch.empty(11, dtype=torch.float64, device="cuda"); Fd = torch.empty_like(Fu)
+    with pytest.raises(HeliosError):
+        hp.flux_sweep_noalloc(wl.atms[0], wl.tables[0], kap, T, (Fu, Fd, None), n_passes=hp.DIRECT)
