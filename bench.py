@@ -35,6 +35,51 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+# ---- replicas: one process per GPU, each with its own atmospheres; the process group carries
+# only the barriers around the timed region and the max-over-ranks time (atmospheres are
+# independent, so there is no collective on the data path)
+def init_replicas(world, local, backend="nccl"):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    """The largest of every rank's value of x (the job's time is its slowest rank's)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device):
+    """The sum of every rank's value of x (units processed by the whole job)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_ids(rank, per_rank):
+    """The atmospheres rank `rank` owns: disjoint shards of per_rank consecutive seeds."""
+    return list(range(rank * per_rank, (rank + 1) * per_rank))
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -128,10 +173,7 @@ def touched_table_bytes(plan, wl, T):
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    init_replicas(world, local)
     import synth
     import paper_1606_05474_b300 as hp
     dev = torch.device("cuda", local)
@@ -165,8 +207,7 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)                                     # let the sampler attach before timing
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     t_wall = time.time()
     for k in range(args.steps):
@@ -176,16 +217,12 @@ def run_gpu(args):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     sweep_ms = list(plan.sweep_times(args.steps))
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     wall = time.time() - t_wall
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
 
     cells, pts, fp32, sfu = algorithmic_counts(wl, n_passes)
     value = cells * args.steps * world / (total_ms * 1e-3) / 1e9
@@ -208,10 +245,7 @@ def run_gpu(args):
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_total = float(np.sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, world, dev)
     e2e_value = cells * e2e_steps * world / (e2e_total * 1e-3) / 1e9
 
     # ---- one full radiative-equilibrium solve from the start profile (context)
@@ -301,16 +335,13 @@ def run_gpu_batched(args):
     The working set (warm-start fluxes of every column, tens of GB) is far larger than L2."""
     import torch
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    init_replicas(world, local)
     import synth
     import paper_1606_05474_b300 as hp
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     t0 = time.time()
-    ids = list(range(rank * args.atmospheres, (rank + 1) * args.atmospheres))
+    ids = replica_ids(rank, args.atmospheres)
     wl = synth.config3(A=len(ids), atm_ids=ids)
     t_gen = time.time() - t0
     ctx = hp.Context(local)
@@ -341,8 +372,7 @@ def run_gpu_batched(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(args.steps):
@@ -351,10 +381,7 @@ def run_gpu_batched(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = a.elapsed_time(b)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     sweep_ms = float(np.mean(plan.sweep_times(args.steps)))
     n_passes = plan.info.passes
     cells, pts, fp32, sfu = algorithmic_counts(wl, n_passes)
@@ -398,10 +425,7 @@ def run_gpu_learned(args):
     region, plan set-up is not."""
     import torch
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    init_replicas(world, local)
     import synth
     import paper_1606_05474_b300 as hp
     from paper_1606_05474_b300.learned import LearnedInitializer, features
@@ -438,6 +462,11 @@ def run_gpu_learned(args):
     t_inf = time.time() - t
     Ts, it_s, st_s, t_sur = solve(te_atms, starts)
     t_sur += t_inf
+    # whole job: atmospheres converged on every rank over the slowest rank's time
+    n_conv_p = sum_over_ranks(int((st_p == 1).sum()), world, dev)
+    n_conv_s = sum_over_ranks(int((st_s == 1).sum()), world, dev)
+    t_plain_job = max_over_ranks(t_plain, world, dev)
+    t_sur_job = max_over_ranks(t_sur, world, dev)
     if rank != 0:
         return
     both = (st_p == 1) & (st_s == 1)
@@ -448,16 +477,16 @@ def run_gpu_learned(args):
     flop_fwd = 2 * (6 * 256 + 2 * 256 * 256 + 256 * 100)
     n_fit = int(ok.sum()) * args.epochs
     line = {
-        "metric": "RE-converged atmospheres/s, batched + surrogate vs plain", "value": round(int((st_s == 1).sum()) / t_sur, 3),
+        "metric": "RE-converged atmospheres/s, batched + surrogate vs plain", "value": round(n_conv_s / t_sur_job, 3),
         "unit": "atm/s", "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step / bf16 MLP", "data": "synthetic",
         "config": {"workload": f"learned-initialiser family: {n_te} held-out planets, 100 layers x {args.bins} bins x 20 g, "
                                f"scattering, 2-table mixtures; surrogate trained on {int(ok.sum())} converged planets",
                    "tol": prm.tol, "max_iter": prm.max_iter, "parallelism": f"replicas x{world}"},
-        "plain": {"atm_per_s": round(int((st_p == 1).sum()) / t_plain, 3), "wall_s": round(t_plain, 3),
+        "plain": {"atm_per_s": round(n_conv_p / t_plain_job, 3), "wall_s": round(t_plain, 3),
                   "converged": int((st_p == 1).sum()), "iters_median": float(np.median(it_p)),
                   "iters_mean": round(float(it_p.mean()), 1)},
-        "surrogate": {"atm_per_s": round(int((st_s == 1).sum()) / t_sur, 3), "wall_s": round(t_sur, 3),
+        "surrogate": {"atm_per_s": round(n_conv_s / t_sur_job, 3), "wall_s": round(t_sur, 3),
                       "inference_s": round(t_inf, 4), "converged": int((st_s == 1).sum()),
                       "iters_median": float(np.median(it_s)), "iters_mean": round(float(it_s.mean()), 1),
                       "used_learned_start": int(used.sum())},
@@ -470,6 +499,71 @@ def run_gpu_learned(args):
         "training": {"solve_s": round(t_tr, 2), "fit_s": round(t_fit, 2), "loss_first": float(losses[0]),
                      "loss_last": float(losses[-1]), "samples": int(ok.sum()), "epochs": args.epochs,
                      "mlp_tflops": round(3 * flop_fwd * n_fit / t_fit / 1e12, 4)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu_spectrum(args):
+    """Post-processing emission spectrum (Sect. 3): the full-size atmosphere (100 layers x 3000
+    bins x 20 g, scattering) on isothermal layers, from a cold start, with 1 + 80 scattering
+    passes (Sect. 2.2.3) and with their limit, the exact column solve.  A step is one spectrum;
+    L2 is flushed before every step; CUDA events on the launching stream."""
+    import torch
+    rank, world, local = dist_env()
+    init_replicas(world, local)
+    import synth
+    import paper_1606_05474_b300 as hp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = synth.config2()
+    T0 = synth.perturbed_profile(wl.atms[0], 21 + rank, amp=200.0)
+    ctx = hp.Context(local)
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(iso_layers=1))
+    T = torch.from_numpy(np.asarray(T0, np.float64)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, npass in (("exact", hp.DIRECT), ("passes_81", 81)):
+        for _ in range(args.warmup):
+            plan.emission_spectrum(T, n_passes=npass)
+        plan.set_timing(args.steps)
+        torch.cuda.synchronize()
+        barrier(world)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            plan.emission_spectrum(T, n_passes=npass)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        total = max_over_ranks(float(np.sum([a.elapsed_time(b) for a, b in ev])), world, dev)
+        res[name] = {"ms_per_spectrum": round(total / args.steps, 5),
+                     "sweep_ms": round(float(np.median(plan.sweep_times(args.steps))), 5)}
+    if rank != 0:
+        return
+    cells = plan.info.cells
+    P = peaks()
+    sm_max = P.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * sm_max * 1e6 / 1e12
+    # algorithmic FP32 instructions of the exact solve per cell: 2 sublayers x (24 for the
+    # coefficients + 14 for the three recurrences and G_up = rho G_dn + u)
+    fp32 = 2 * (24 + 14) * cells
+    achieved = fp32 / (res["exact"]["sweep_ms"] * 1e-3) / 1e12
+    line = {
+        "metric": "post-processing emission spectra/s (isothermal layers, exact column solve)",
+        "value": round(world * 1e3 / res["exact"]["ms_per_spectrum"], 3), "unit": "spectra/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["exact"]["ms_per_spectrum"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 sums",
+        "data": "synthetic",
+        "config": {"workload": "full-size atmosphere on 100 isothermal layers x 3000 bins x 20 g, scattering, cold start",
+                   "cells": cells, "l2": "flushed before every step", "parallelism": f"replicas x{world}"},
+        "exact": res["exact"], "passes_81": res["passes_81"],
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+                     "unit": "T FP32 inst/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                     "kernel": "sweep_kernel<7, 1, true> (exact column solve)",
+                     "peak_source": "148 SMs x 128 FP32 lanes x max SM clock"},
+        "gpu_launches": 3 * 2 * args.steps,                      # prep, sweep, finalize per spectrum
     }
     print(json.dumps(line), flush=True)
 
@@ -541,7 +635,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned", "spectrum"])
     ap.add_argument("--atmospheres", type=int, default=4096)
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -559,6 +653,8 @@ def main():
         run_gpu_batched(args)
     elif args.workload == "learned":
         run_gpu_learned(args)
+    elif args.workload == "spectrum":
+        run_gpu_spectrum(args)
     else:
         run_gpu(args)
 

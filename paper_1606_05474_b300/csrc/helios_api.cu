@@ -132,8 +132,11 @@ size_t sweep_smem(int M, int G)
 }
 
 // lane chunks up to 7 fit two 640-thread blocks per SM within the register file (48 registers)
-// (the direct column solve holds more per-lane arrays: one block per SM, 96 registers)
-template <int M, bool DIRECT> constexpr int sweep_minb() { return (M <= 7 && !DIRECT) ? 2 : 1; }
+// Two 640-thread blocks per SM (48 registers, some spilled to L1) up to lane chunk 11 for the
+// passes and 7 for the exact column solve, which holds more per-lane arrays; one block (96
+// registers) beyond.  Measured: occupancy outweighs the spills up to there (2 blocks at chunk 13
+// were slower again).
+template <int M, bool DIRECT> constexpr int sweep_minb() { return (M <= (DIRECT ? 7 : 11)) ? 2 : 1; }
 
 template <int M, bool DIRECT>
 int sweep_occupancy_MD(int threads, size_t smem)

@@ -656,9 +656,13 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 const bool last = pass == K - 1;
                 // downward sweep: G_dn[s] = Ts G_dn[s+1] + (Rs G_up[s] - Ss), from the TOA
                 {
+                    // G_up[s] enters only through Rs G_up[s] - Ss: X[k] is replaced by that term
                     float b = 0.0f;
 #pragma unroll
-                    for (int k = M - 1; k >= 0; --k) b = fmaf(Ts[k], b, fmaf(Rs[k], X[k], -Ss[k]));
+                    for (int k = M - 1; k >= 0; --k) {
+                        X[k] = fmaf(Rs[k], X[k], -Ss[k]);
+                        b = fmaf(Ts[k], b, X[k]);
+                    }
 #pragma unroll
                     for (int lv = 0; lv < 5; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv), b);
                     const float outv = fmaf(adn_fin, toa_g, b);
@@ -666,7 +670,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     if (lane == 31) inv = toa_g;
                     X[M] = inv;
 #pragma unroll
-                    for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], fmaf(Rs[k], X[k], -Ss[k]));
+                    for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], X[k]);
                     if (last) {
 #pragma unroll
                         for (int k = 0; k < M; ++k) {
@@ -677,9 +681,13 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 }
                 // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
                 {
+                    // G_dn[s+1] enters only through Rs G_dn[s+1] + Ss: X[k+1] is replaced by that term
                     float c = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < M; ++k) c = fmaf(Ts[k], c, fmaf(Rs[k], X[k + 1], Ss[k]));
+                    for (int k = 0; k < M; ++k) {
+                        X[k + 1] = fmaf(Rs[k], X[k + 1], Ss[k]);
+                        c = fmaf(Ts[k], c, X[k + 1]);
+                    }
 #pragma unroll
                     for (int lv = 0; lv < 5; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv), c);
                     const float boa = __shfl_sync(FULL, X[0], 0) + bint;
@@ -688,7 +696,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     if (lane == 0) inv = boa;
                     X[0] = inv;
 #pragma unroll
-                    for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], fmaf(Rs[k], X[k + 1], Ss[k]));
+                    for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], X[k + 1]);
                     if (last) {
                         // weighted deviations at the interfaces; the TOA keeps the unweighted value
                         // so its Gauss sum and the Planck add-back are done in double (emergent spectrum)
