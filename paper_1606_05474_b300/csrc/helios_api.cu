@@ -125,11 +125,7 @@ int upload(T* dst, const std::vector<T>& src)
     return HELIOS_OK;
 }
 
-size_t sweep_smem(int M, int G)
-{
-    const size_t W = 32 * (size_t)M, KST = W + 1;
-    return 3 * (W / 2) * sizeof(double) + (G * KST + 4 * W + 1) * sizeof(float);
-}
+size_t sweep_smem(int M, int G) { return sweep_smem_bytes(M, G); }
 
 // lane chunks up to 7 fit two 640-thread blocks per SM within the register file (48 registers)
 // Two 640-thread blocks per SM (48 registers, some spilled to L1) up to lane chunk 11 for the

@@ -437,6 +437,15 @@ __device__ __forceinline__ void direct_column(const float (&Ts)[M], const float 
     }
 }
 
+// dynamic shared memory of one sweep block (lane chunk M, G Gauss points): FP64 accumulators
+// [3][16 M], the per-warp rows of opacities / weighted downward deviations and of weighted
+// upward deviations [2][G][32 M + 1], four per-point rows [32 M], and the TOA value
+__host__ __device__ constexpr size_t sweep_smem_bytes(int M, int G)
+{
+    return 3 * (size_t)(16 * M) * sizeof(double) +
+           (2 * (size_t)G * (32 * M + 1) + 4 * (size_t)(32 * M) + 1) * sizeof(float);
+}
+
 // ---------------------------------------------------------------------------
 // one work item = (atmosphere, tile of bins); the whole block cooperates
 template <int M, bool DIRECT>
@@ -456,8 +465,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     const int l_end = min(l_begin + P.TB, ad.L);
 
     double* acc = reinterpret_cast<double*>(smem_raw);         // [3][n+1], n+1 <= W/2
-    float* kap = reinterpret_cast<float*>(acc + 3 * (W / 2));  // [G][KST]; later per-warp reduction rows
-    float* bt = kap + G * KST;                                 // [W] 2 pi eps B at points
+    float* kap = reinterpret_cast<float*>(acc + 3 * (W / 2));  // [G][KST] opacities, then w_g G_dn per point
+    float* upr = kap + G * KST;                                // [G][KST] w_g G_up per point
+    float* bt = upr + G * KST;                                 // [W] 2 pi eps B at points
     float* dbs = bt + W;                                       // [W] warm-start shift B_old - B_new
     float* dbt = dbs + W;                                      // [W] 2 pi eps (B_a - B_b) per sublayer
     float* dm = dbt + W;                                       // [W] sublayer column mass
@@ -583,15 +593,12 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             const float toa_g = bc_toa[0];
             __syncwarp();                                           // the warp's row is free now
             direct_column<M>(Ts, Rs, Es, Ss, U, Dn, toa_g, bc.bint, lane);
-            float* red_dn = kap + g * KST;
-            float* red_up = red_dn + (n + 1);
+            float* red_dn = kap + g * KST + lane * M;
+            float* red_up = upr + g * KST + lane * M;
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                const int p = lane * M + k;
-                if (p < NP && !(p & 1)) {
-                    red_dn[p >> 1] = wg * Dn[k];
-                    red_up[p >> 1] = (p == NS) ? U[k] : wg * U[k];  // TOA: unweighted (double sum)
-                }
+                red_dn[k] = wg * Dn[k];
+                red_up[k] = wg * U[k];
             }
             const long long col = (long long)(l * G + g) * W;
 #pragma unroll
@@ -649,8 +656,10 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             const float toa_g = bc_toa[0];
             const float bint = bc.bint;
             __syncwarp();
-            float* red_dn = kap + g * KST;          // this warp's row is free now
-            float* red_up = red_dn + (n + 1);
+            // weighted deviations of every point of the column (phase 3 reads the interfaces);
+            // the opacity row is free now
+            float* red_dn = kap + g * KST + lane * M;
+            float* red_up = upr + g * KST + lane * M;
             const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
             for (int pass = 0; pass < K; ++pass) {
                 const bool last = pass == K - 1;
@@ -673,10 +682,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], X[k]);
                     if (last) {
 #pragma unroll
-                        for (int k = 0; k < M; ++k) {
-                            const int p = lane * M + k;
-                            if (p < NP && !(p & 1)) red_dn[p >> 1] = wg * X[k];
-                        }
+                        for (int k = 0; k < M; ++k) red_dn[k] = wg * X[k];
                     }
                 }
                 // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
@@ -698,14 +704,8 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 #pragma unroll
                     for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], X[k + 1]);
                     if (last) {
-                        // weighted deviations at the interfaces; the TOA keeps the unweighted value
-                        // so its Gauss sum and the Planck add-back are done in double (emergent spectrum)
 #pragma unroll
-                        for (int k = 1; k <= M; ++k) {
-                            const int p = lane * M + k;
-                            if (p < NP && !(p & 1)) red_up[p >> 1] = (p == NS) ? X[k] : wg * X[k];
-                        }
-                        if (lane == 0) red_up[0] = wg * X[0];
+                        for (int k = 0; k < M; ++k) red_up[k] = wg * X[k];
                     }
                 }
             }
@@ -714,18 +714,21 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         }
         __syncthreads();
         // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators.
-        // Thread t sums column t of the per-warp rows (downward interfaces 0..n, then upward
-        // interfaces 0..n); the threads after them add the Planck fluxes at the interfaces
+        // Thread t sums interface t's column of the per-warp rows (downward interfaces 0..n, then
+        // upward interfaces 0..n; interface i is point 2i); the threads after them add the Planck
+        // fluxes at the interfaces
         const int NI = n + 1;
         for (int t = tid; t < 3 * NI; t += nthreads) {
             if (t == 2 * NI - 1) continue;                 // TOA upward: summed below
             double v;
             int a;
             if (t < 2 * NI) {
+                const bool dn = t < NI;
+                const float* row = (dn ? kap : upr) + 2 * (dn ? t : t - NI);
                 float sg = 0.0f;
-                for (int gg = 0; gg < G; ++gg) sg += kap[gg * KST + t];
+                for (int gg = 0; gg < G; ++gg) sg += row[gg * KST];
                 v = (double)sg;
-                a = t < NI ? NI + t : t - NI;
+                a = dn ? NI + t : t - NI;
             } else {
                 v = (double)bt[2 * (t - 2 * NI)];
                 a = t;
@@ -733,14 +736,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             acc[a] += v;
         }
         // the emergent bin: sum_g w_g G_up(TOA) as a float-float reduction over the lanes of the
-        // last warp (exact products, fixed butterfly), then the Planck add-back in double
+        // last warp (error-free sums in a fixed butterfly), then the Planck add-back in double
         if (tid >= nthreads - 32) {
-            float2 sv = make_float2(0.0f, 0.0f);
-            if (lane < G) {
-                const float w = P.gw[lane], x = kap[lane * KST + 2 * NI - 1];
-                const float pr = w * x;
-                sv = make_float2(pr, fmaf(w, x, -pr));
-            }
+            float2 sv = make_float2(lane < G ? upr[lane * KST + NS] : 0.0f, 0.0f);
 #pragma unroll
             for (int d = 16; d >= 1; d >>= 1) {
                 const float2 o = make_float2(__shfl_xor_sync(FULL, sv.x, d), __shfl_xor_sync(FULL, sv.y, d));

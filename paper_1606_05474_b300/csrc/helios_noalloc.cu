@@ -145,7 +145,7 @@ template <int M>
 int launch_sweep(const PlanDev& P, int dev, int count, const int* order, int n_passes, float* toa, cudaStream_t s)
 {
     constexpr int MINB = M <= 7 ? 2 : 1;
-    const size_t W = 32 * M, smem = 3 * (W / 2) * sizeof(double) + (P.G * (W + 1) + 4 * W + 1) * sizeof(float);
+    const size_t smem = sweep_smem_bytes(M, P.G);
     if (!g_smem_set[dev][M]) {
         NA_CUDA(cudaFuncSetAttribute(sweep_kernel<M, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         g_smem_set[dev][M] = true;
