@@ -109,6 +109,12 @@ def flux_sweep_noalloc(atm, table, kappa, T, out, n_passes=0, params=None, strea
     return Fu, Fd, toa
 
 
+def _cat(arrays, dtype):
+    # an empty batch passes empty arrays on, for the library to reject
+    return np.ascontiguousarray(np.concatenate([np.asarray(x, dtype) for x in arrays]) if arrays else
+                                np.zeros(1, dtype))
+
+
 def _marshal(atms, tables, kappa):
     """Host arrays of a helios_batch_t and the helios_ktable_t descriptors (kept alive by the caller)."""
     torch = _torch()
@@ -122,9 +128,9 @@ def _marshal(atms, tables, kappa):
         "T_irr": np.array([a.T_irr for a in atms], dtype=np.float64),
         "T_int": np.array([a.T_int for a in atms], dtype=np.float64),
         "T_star": np.array([a.T_star for a in atms], dtype=np.float64),
-        "nu_edges": np.ascontiguousarray(np.concatenate([np.asarray(a.nu_edges, np.float64) for a in atms])),
-        "omega0": np.ascontiguousarray(np.concatenate([np.asarray(a.omega0, np.float32) for a in atms])),
-        "g0": np.ascontiguousarray(np.concatenate([np.asarray(a.g0, np.float32) for a in atms])),
+        "nu_edges": _cat([a.nu_edges for a in atms], np.float64),
+        "omega0": _cat([a.omega0 for a in atms], np.float32),
+        "g0": _cat([a.g0 for a in atms], np.float32),
     }
     if any(getattr(a, "species", None) for a in atms):
         # eq. (34) mixing: (table, mass mixing ratio) pairs per atmosphere; plain atmospheres
