@@ -194,15 +194,15 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(warm):
-        plan.flux_sweep(T, warm=warm, want_toa=False, out=(Fu, Fd, None))
-        plan.temp_update(Fu, Fd, T, state)
+        plan.re_step(T, state, warm=warm, out=(Fu, Fd))
 
     # warm-up (the first step starts the coupled stream from zero)
     step(False)
     for _ in range(args.warmup - 1):
         step(True)
     torch.cuda.synchronize()
-    n_launch_per_step = 3 + len({(2 * a.n_layers + 1 + 31) // 32 | 1 for a in wl.atms})   # prep, sweep groups, finalize, temp
+    # prep, sweep groups, finalize (unless fused), post
+    n_launch_per_step = 2 + plan.info.sweep_launches + (0 if plan.info.fused_finalize else 1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
@@ -362,8 +362,7 @@ def run_gpu_batched(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(warm):
-        plan.flux_sweep(T, warm=warm, want_toa=False, out=(Fu, Fd, None))
-        plan.temp_update(Fu, Fd, T, state)
+        plan.re_step(T, state, warm=warm, out=(Fu, Fd))
 
     step(False)
     for _ in range(args.warmup - 1):
@@ -407,7 +406,7 @@ def run_gpu_batched(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "sweep_kernel (all lane chunks)",
                      "kernel_ms": round(sweep_ms, 3), "algorithmic_bytes": int(alg_bytes), "peak_source": "measured"},
-        "gpu_launches": (3 + groups) * args.steps,               # prep, sweep groups, finalize, temp
+        "gpu_launches": (2 + plan.info.sweep_launches + (0 if plan.info.fused_finalize else 1)) * args.steps,
         "clocks": clk,
         "setup_s": {"inputs": round(t_gen, 2), "autotune": round(t_tune, 2), "plan": round(t_plan, 2)},
         "workspace_gb": round(plan.info.workspace_bytes / 1e9, 2),

@@ -168,12 +168,17 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* batch, const helio
 int helios_plan_destroy(helios_plan* plan);
 
 /* Packed sizes of a plan: total layers, interfaces, points, bins; the number
- * of passes per temperature step (1 + n_scat if any omega0 > 0, else 1);
- * bytes of workspace held. */
+ * of passes per temperature step (1 + n_scat if any omega0 > 0, else 1;
+ * HELIOS_DIRECT with params.direct); bytes of workspace held; the sweep launches
+ * per evaluation (one per group of atmospheres with the same lane chunk); whether
+ * the bolometric sums join the temperature-step kernel (1) or run as their own
+ * launch (0: an atmosphere with many work items). */
 typedef struct {
     int64_t layers, interfaces, points, bins, cells;
     int passes;
     int64_t workspace_bytes;
+    int sweep_launches;
+    int fused_finalize;
 } helios_plan_info_t;
 int helios_plan_info(const helios_plan* plan, helios_plan_info_t* info);
 
@@ -234,6 +239,20 @@ int helios_flux_sweep(helios_plan* plan, const double* T_layer, int n_passes, in
 int helios_temp_update(helios_plan* plan, const double* Fup_bol, const double* Fdn_bol, double* T_layer,
                        double* mult, uint8_t* hist, uint8_t* nhist, int32_t* status, int32_t* iters,
                        double* metric, cudaStream_t stream);
+
+/* One radiative-equilibrium iteration of every atmosphere (Sects. 2.2.3-2.2.4):
+ * helios_flux_sweep with the plan's default passes followed by helios_temp_update,
+ * as three launches (the bolometric sums, the metric and the temperature step are
+ * one kernel per atmosphere).  Every atmosphere is evaluated whatever its status;
+ * status[a] is recomputed from this step's metric (an atmosphere whose metric
+ * meets eq. (29) keeps its temperatures) and iters[a] advances by one.
+ *   T_layer, mult, hist, nhist, status, iters, metric: as helios_temp_update
+ *   warm     as helios_flux_sweep
+ *   Fup_bol, Fdn_bol  device, double [interfaces]: this step's bolometric fluxes
+ *            (may be NULL: the plan's own buffers). */
+int helios_re_step(helios_plan* plan, double* T_layer, int warm, double* mult, uint8_t* hist, uint8_t* nhist,
+                   int32_t* status, int32_t* iters, double* metric, double* Fup_bol, double* Fdn_bol,
+                   cudaStream_t stream);
 
 /* The radiative-equilibrium iteration (Sect. 2.2.3): flux evaluation and
  * temperature step repeated, every atmosphere dropping out when it converges,

@@ -264,6 +264,19 @@ class Plan:
                                           _ptr(s.get("iters")), _ptr(s.get("metric")), _stream_ptr(stream)))
         return state
 
+    def re_step(self, T, state, warm=True, out=None, stream=None):
+        """One radiative-equilibrium iteration of every atmosphere in place (helios_re_step):
+        the flux evaluation with the plan's default passes and the temperature step.  out:
+        optional (Fup_bol, Fdn_bol) tensors for this step's bolometric fluxes."""
+        self._check_T(T)
+        s = state
+        Fu, Fd = out if out is not None else (None, None)
+        check(self.lib.helios_re_step(self.h, T.data_ptr(), 1 if warm else 0, s["mult"].data_ptr(),
+                                      s["hist"].data_ptr(), s["nhist"].data_ptr(), s["status"].data_ptr(),
+                                      _ptr(s.get("iters")), _ptr(s.get("metric")), _ptr(Fu), _ptr(Fd),
+                                      _stream_ptr(stream)))
+        return state
+
     def solve_re(self, T, stream=None, raise_on_noconv=False):
         """Iterate to radiative equilibrium in place; returns (iters, status) CUDA tensors."""
         torch = _torch()

@@ -38,12 +38,13 @@ class Params(ctypes.Structure):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("layers", c_int64), ("interfaces", c_int64), ("points", c_int64), ("bins", c_int64),
-                ("cells", c_int64), ("passes", c_int), ("workspace_bytes", c_int64)]
+                ("cells", c_int64), ("passes", c_int), ("workspace_bytes", c_int64), ("sweep_launches", c_int),
+                ("fused_finalize", c_int)]
 
 
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
-           "helios_flux_sweep", "helios_temp_update", "helios_solve_re", "helios_plan_set_timing",
+           "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_solve_re", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
            "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_forward",
            "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step"]
@@ -73,6 +74,7 @@ def load(path: str = SO_PATH):
     lib.helios_interp_opacity.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.helios_flux_sweep.argtypes = [vp, vp, c_int, c_int, vp, vp, vp, vp]
     lib.helios_temp_update.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.helios_re_step.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_solve_re.argtypes = [vp, vp, vp, vp, vp]
     lib.helios_plan_set_timing.argtypes = [vp, c_int]
     lib.helios_plan_last_sweep_ms.argtypes = [vp, P(ctypes.c_float)]

@@ -127,6 +127,10 @@ int upload(T* dst, const std::vector<T>& src)
 
 size_t sweep_smem(int M, int G) { return sweep_smem_bytes(M, G); }
 
+// atmospheres of at most this many work items have their bolometric sums done by the
+// per-atmosphere temperature-step block (post_kernel); wider ones by finalize_kernel
+constexpr int kFuseFinalizeItems = 64;
+
 // lane chunks up to 7 fit two 640-thread blocks per SM within the register file (48 registers)
 // Two 640-thread blocks per SM (48 registers, some spilled to L1) up to lane chunk 11 for the
 // passes and 7 for the exact column solve, which holds more per-lane arrays; one block (96
@@ -208,6 +212,7 @@ struct helios_plan {
     const void* graph_key[3];
     int graph_chunk;
     int graph_device_loop;
+    int max_items;      // work items of the widest atmosphere
     int threads;        // sweep block size: one warp per Gauss point
     int* chunks_left;   // device budget of WHILE-node iterations (device_loop)
     cudaEvent_t fork;
@@ -429,6 +434,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     for (int a = 0; a < A; ++a) {
         AtmDesc& d = ad[a];
         d.n_items = (d.L + TB - 1) / TB;
+        P->max_items = std::max(P->max_items, d.n_items);
         d.item_off = (int)items.size();
         for (int t = 0; t < d.n_items; ++t) items.push_back(make_int2(a, t));
         d.part_off = part;
@@ -685,6 +691,8 @@ int helios_plan_info(const helios_plan* p, helios_plan_info_t* info)
     info->layers = p->layers; info->interfaces = p->interfaces; info->points = p->points;
     info->bins = p->bins; info->cells = p->cells; info->passes = p->passes;
     info->workspace_bytes = p->ws_bytes;
+    info->sweep_launches = (int)p->groups.size();
+    info->fused_finalize = p->max_items <= kFuseFinalizeItems ? 1 : 0;
     return HELIOS_OK;
 }
 
@@ -773,12 +781,19 @@ int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid
     return HELIOS_OK;
 }
 
-int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes, int warm_valid, double* Fup,
-                double* Fdn, float* Fup_toa, cudaStream_t s)
+int launch_prep(helios_plan* p, const double* T, const int* status, int warm_valid, cudaStream_t s)
 {
     prep_kernel<<<dim3((2 * p->max_n + 1 + 63) / 64, p->A), 64, 0, s>>>(p->dev, T, status, warm_valid);
     CUDA_TRY(cudaGetLastError());
-    int rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
+    return HELIOS_OK;
+}
+
+int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes, int warm_valid, double* Fup,
+                double* Fdn, float* Fup_toa, cudaStream_t s)
+{
+    int rc = launch_prep(p, T, status, warm_valid, s);
+    if (rc) return rc;
+    rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
     if (rc) return rc;
     finalize_kernel<<<dim3((p->max_n + 1 + 7) / 8, p->A), 256, 0, s>>>(p->dev, status, Fup, Fdn);
     CUDA_TRY(cudaGetLastError());
@@ -792,6 +807,27 @@ TempArgs temp_args(const helios_plan* p)
     t.osc_down = p->prm.osc_down; t.osc_up = p->prm.osc_up; t.mult_max = p->prm.mult_max;
     t.T_floor = p->prm.T_floor; t.max_iter = p->prm.max_iter;
     return t;
+}
+
+TempArgs temp_args(const helios_plan* p);
+
+// finalize + temperature step (+ the next evaluation's point quantities) of every atmosphere.
+// The bolometric sums join the per-atmosphere block when every atmosphere has few work items;
+// an atmosphere of many items (a single wide one) keeps them in finalize_kernel, whose blocks
+// spread its interfaces over many SMs
+int launch_post(helios_plan* p, const int* status_gate, double* Fup, double* Fdn, double* T, double* mult,
+                uint8_t* hist, uint8_t* nhist, int* status, int* iters, double* metric, int* n_active, int gate,
+                int do_prep, cudaStream_t s)
+{
+    const int fuse = p->max_items <= kFuseFinalizeItems;
+    if (!fuse) {
+        finalize_kernel<<<dim3((p->max_n + 1 + 7) / 8, p->A), 256, 0, s>>>(p->dev, status_gate, Fup, Fdn);
+        CUDA_TRY(cudaGetLastError());
+    }
+    post_kernel<<<p->A, 512, 0, s>>>(p->dev, temp_args(p), Fup, Fdn, T, mult, hist, nhist, status, iters, metric,
+                                     n_active, gate, fuse, do_prep);
+    CUDA_TRY(cudaGetLastError());
+    return HELIOS_OK;
 }
 
 int launch_temp(helios_plan* p, const double* Fup, const double* Fdn, double* T, double* mult, uint8_t* hist,
@@ -848,6 +884,23 @@ int helios_temp_update(helios_plan* p, const double* Fup_bol, const double* Fdn_
     return launch_temp(p, Fup_bol, Fdn_bol, T_layer, mult, hist, nhist, status, iters, metric, nullptr, s);
 }
 
+int helios_re_step(helios_plan* p, double* T_layer, int warm, double* mult, uint8_t* hist, uint8_t* nhist,
+                   int32_t* status, int32_t* iters, double* metric, double* Fup_bol, double* Fdn_bol, cudaStream_t s)
+{
+    if (!p || !T_layer || !mult || !hist || !nhist || !status)
+        return fail(HELIOS_EINVAL, "helios_re_step: null argument");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    const int warm_valid = (warm && p->warm_ready) ? 1 : 0;
+    double* Fu = Fup_bol ? Fup_bol : p->Fup;
+    double* Fd = Fdn_bol ? Fdn_bol : p->Fdn;
+    int rc = launch_prep(p, T_layer, nullptr, warm_valid, s);
+    if (!rc) rc = launch_sweep(p, nullptr, p->passes, warm_valid, nullptr, s);
+    if (!rc) rc = launch_post(p, nullptr, Fu, Fd, T_layer, mult, hist, nhist, status, iters, metric, nullptr, 0, 0, s);
+    if (rc) return rc;
+    p->warm_ready = true;
+    return HELIOS_OK;
+}
+
 int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t s)
 {
     if (!p || !T_layer || !iters || !status) return fail(HELIOS_EINVAL, "helios_solve_re: null argument");
@@ -868,10 +921,12 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
     const int timing = p->timing;
     p->timing = 0;    // no event records inside the captured graph
     struct Restore { helios_plan* p; int t; ~Restore() { p->timing = t; } } restore{p, timing};
-    // first temperature step: the coupled stream starts from zero
-    int rc = launch_eval(p, T_layer, status, p->passes, 0, p->Fup, p->Fdn, nullptr, w);
-    if (rc) return rc;
-    rc = launch_temp(p, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr, p->n_active, w);
+    // first temperature step: the coupled stream starts from zero.  Every step ends with
+    // post_kernel, which also prepares the next evaluation at the new temperatures
+    int rc = launch_prep(p, T_layer, status, 0, w);
+    if (!rc) rc = launch_sweep(p, status, p->passes, 0, nullptr, w);
+    if (!rc) rc = launch_post(p, status, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr,
+                              p->n_active, 1, 1, w);
     if (rc) return rc;
     // later steps start from the previous step's fluxes; captured as a graph of `chunk` steps,
     // either inside a conditional WHILE node that the device keeps looping (device_loop) or
@@ -908,10 +963,10 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
             CUDA_TRY(cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal));
         }
         for (int i = 0; i < chunk && rc == HELIOS_OK; ++i) {
-            rc = launch_eval(p, T_layer, status, p->passes, 1, p->Fup, p->Fdn, nullptr, w);
+            rc = launch_sweep(p, status, p->passes, 1, nullptr, w);
             if (rc == HELIOS_OK)
-                rc = launch_temp(p, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr,
-                                 p->n_active, w);
+                rc = launch_post(p, status, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters,
+                                 nullptr, p->n_active, 1, 1, w);
         }
         if (rc == HELIOS_OK && dloop) {
             loop_cond_kernel<<<1, 1, 0, w>>>(h, p->n_active, p->chunks_left);

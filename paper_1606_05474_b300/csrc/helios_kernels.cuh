@@ -1,6 +1,8 @@
 // Device kernels of the radiative-equilibrium hot path (sm_103a).
 //
-// One flux evaluation + temperature step is four launches:
+// One flux evaluation + temperature step (helios_flux_sweep + helios_temp_update) is four
+// launches; helios_re_step fuses finalize and temp into post_kernel (three), and inside
+// helios_solve_re post_kernel also does the next step's prep (two: sweep + post):
 //   prep_kernel      one thread per point: point temperatures (Sect. 2.2.1),
 //                    temperature-table coordinates in IEEE double (Sect. 2.3), the
 //                    table row offset and the four bilinear weights of the point, and
@@ -18,6 +20,7 @@
 //                    the convergence metric of eq. (29) reduced with an exact max, the
 //                    convergence decision and the FP64 temperature step of eqs. (24)-(28)
 //                    with the oscillation rule.
+//   post_kernel      one block per atmosphere: finalize + temp (+ prep of the next step).
 //
 // Fluxes are carried in the sweep as deviations from the local two-stream Planck flux,
 // G = F - 2 pi eps B_l(T_p).  With per-sublayer transmission Ts, reflection Rs and
@@ -228,15 +231,12 @@ __device__ __forceinline__ float planck_ff(const BinConst& b, float2 it, float& 
 }
 
 // ---------------------------------------------------------------------------
-__global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const int* __restrict__ status,
-                            int warm_valid)
+// point quantities of point p of atmosphere ad at the temperatures T_layer (warm_valid: the
+// previous evaluation's point temperature is the old one of the warm-start shift)
+__device__ __forceinline__ void prep_point(const PlanDev& P, const double* __restrict__ T_layer, const AtmDesc& ad,
+                                           int p, int warm_valid)
 {
-    const int a = blockIdx.y;
-    if (status && status[a] != 0) return;
-    const AtmDesc ad = P.atms[a];
-    const int n = ad.n, np = 2 * n + 1;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
+    const int n = ad.n;
     const TabDesc td = P.tabs[ad.tab];
     const double* T = T_layer + ad.lay_off;
     const int q = ad.pt_off + p;
@@ -266,6 +266,17 @@ __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const
         P.dinv_sub[ad.sub_off + p] = (float)(Tn - Tb) / (Tnf * Tbf);
         P.dT_sub[ad.sub_off + p] = (float)(Tn - Tb);
     }
+}
+
+__global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const int* __restrict__ status,
+                            int warm_valid)
+{
+    const int a = blockIdx.y;
+    if (status && status[a] != 0) return;
+    const AtmDesc ad = P.atms[a];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 2 * ad.n + 1) return;
+    prep_point(P, T_layer, ad, p, warm_valid);
 }
 
 // Two-stream coefficients of one sublayer in deviation form (see file header).
@@ -782,16 +793,12 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
 // ---------------------------------------------------------------------------
 // bolometric fluxes, one warp per interface: F_up = sum_items (sum G_up + sum B),
 // F_dn likewise; lane-strided FP64 sums and a fixed xor-shuffle tree (deterministic)
-__global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, double* __restrict__ Fup,
-                                double* __restrict__ Fdn)
+// interface i's bolometric fluxes by one warp: lane-strided fixed-order FP64 sums over the
+// atmosphere's work items and a fixed xor tree (deterministic)
+__device__ __forceinline__ void finalize_sums(const PlanDev& P, const AtmDesc& ad, int i, int lane, double& up,
+                                              double& dn)
 {
-    const int a = blockIdx.y;
-    if (status && status[a] != 0) return;
-    const AtmDesc ad = P.atms[a];
     const int n = ad.n, stride = 3 * (n + 1);
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i > n) return;
     const double* part = P.part + ad.part_off;
     double su = 0.0, sd = 0.0, sb = 0.0;
 #pragma unroll 4
@@ -806,9 +813,24 @@ __global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, doubl
         sd += __shfl_xor_sync(FULL, sd, o);
         sb += __shfl_xor_sync(FULL, sb, o);
     }
+    up = su + sb;
+    dn = sd + sb;
+}
+
+__global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, double* __restrict__ Fup,
+                                double* __restrict__ Fdn)
+{
+    const int a = blockIdx.y;
+    if (status && status[a] != 0) return;
+    const AtmDesc ad = P.atms[a];
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i > ad.n) return;
+    double up, dn;
+    finalize_sums(P, ad, i, lane, up, dn);
     if (lane == 0) {
-        Fup[ad.if_off + i] = su + sb;
-        Fdn[ad.if_off + i] = sd + sb;
+        Fup[ad.if_off + i] = up;
+        Fdn[ad.if_off + i] = dn;
     }
 }
 
@@ -824,25 +846,24 @@ __device__ __forceinline__ double layer_divergence(const double* fu, const doubl
     return (fu[i + 1] - fd[i + 1]) - (fu[i] - fd[i]);
 }
 
-// metric (eq. 29) and temperature step (eqs. 23-28, Sect. 2.2.4) of one atmosphere per block
-// (blockDim >= n, a multiple of 32): the block reduces the metric itself, so no separate
-// reduction launch and no atomics are needed
-__global__ void temp_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
-                            double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
-                            uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
-                            double* __restrict__ metric_out, int* __restrict__ n_active)
+// metric (eq. 29) and temperature step (eqs. 23-28, Sect. 2.2.4) of atmosphere a by one block
+// (blockDim >= n, a multiple of 32; every thread of the block calls it): the block reduces the
+// metric itself, so no separate reduction launch and no atomics are needed.  Fu, Fd: the
+// atmosphere's bolometric fluxes at its n+1 interfaces (global or shared memory).
+__device__ __forceinline__ void temp_block(const PlanDev& P, const TempArgs& targ, const AtmDesc& ad, int a,
+                                           const double* Fu, const double* Fd, double* __restrict__ T_layer,
+                                           double* __restrict__ mult, uint8_t* __restrict__ hist,
+                                           uint8_t* __restrict__ nhist, int* __restrict__ status,
+                                           int* __restrict__ iters, double* __restrict__ metric_out,
+                                           int* __restrict__ n_active, unsigned long long* s_max)
 {
-    __shared__ unsigned long long s_max[32];
-    const int a = blockIdx.x;
-    if (status[a] != 0) return;
-    const AtmDesc ad = P.atms[a];
     const int i = threadIdx.x, lane = i & 31, w = i >> 5;
     const bool mine = i < ad.n;
     const int li = ad.lay_off + i;
     double dF = 0.0, Ti = 1.0;
     unsigned long long bits = 0ull;
     if (mine) {
-        dF = layer_divergence(Fup + ad.if_off, Fdn + ad.if_off, i);
+        dF = layer_divergence(Fu, Fd, i);
         Ti = T_layer[li];
         double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
         if (!(m == m) || !isfinite(Ti) || isinf(m)) m = __longlong_as_double(0x7ff8000000000000ll);
@@ -881,26 +902,88 @@ __global__ void temp_kernel(PlanDev P, TempArgs targ, const double* __restrict__
             if (n_active) atomicSub(n_active, 1);
         }
     }
-    if (!mine || bad || worst < targ.tol) return;
-    double step = 0.0;
-    if (dF != 0.0) {
-        const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) / (targ.sigma * Ti * Ti * Ti * P.lnr[li]);
-        step = -mult[li] * (dF > 0.0 ? mag : -mag);
+    if (mine && !bad && !(worst < targ.tol)) {
+        double step = 0.0;
+        if (dF != 0.0) {
+            const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) /
+                               (targ.sigma * Ti * Ti * Ti * P.lnr[li]);
+            step = -mult[li] * (dF > 0.0 ? mag : -mag);
+        }
+        double Tn = Ti + step;
+        if (Tn < targ.T_floor) Tn = targ.T_floor;
+        T_layer[li] = Tn;
+        const unsigned h = ((unsigned)hist[li] << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
+        hist[li] = (uint8_t)h;
+        unsigned c = nhist[li];
+        if (c < 6) c += 1;
+        nhist[li] = (uint8_t)c;
+        if (c >= 6) {
+            double m = mult[li];
+            if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
+            else m = m * targ.osc_down;
+            mult[li] = m;
+        }
     }
-    double Tn = Ti + step;
-    if (Tn < targ.T_floor) Tn = targ.T_floor;
-    T_layer[li] = Tn;
-    const unsigned h = ((unsigned)hist[li] << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
-    hist[li] = (uint8_t)h;
-    unsigned c = nhist[li];
-    if (c < 6) c += 1;
-    nhist[li] = (uint8_t)c;
-    if (c >= 6) {
-        double m = mult[li];
-        if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
-        else m = m * targ.osc_down;
-        mult[li] = m;
+}
+
+__global__ void temp_kernel(PlanDev P, TempArgs targ, const double* __restrict__ Fup, const double* __restrict__ Fdn,
+                            double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
+                            uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
+                            double* __restrict__ metric_out, int* __restrict__ n_active)
+{
+    __shared__ unsigned long long s_max[32];
+    const int a = blockIdx.x;
+    if (status[a] != 0) return;
+    const AtmDesc ad = P.atms[a];
+    temp_block(P, targ, ad, a, Fup + ad.if_off, Fdn + ad.if_off, T_layer, mult, hist, nhist, status, iters,
+               metric_out, n_active, s_max);
+}
+
+constexpr int kPostMaxIf = 256;     // interfaces of the deepest supported atmosphere (239 layers)
+
+// Everything after the sweep of one RE step, one block per atmosphere: the bolometric fluxes
+// (finalize_sums), the metric and temperature step (temp_block), and, with do_prep, the point
+// quantities of the next evaluation at the new temperatures (prep_point with the warm-start
+// shift) -- so an iteration inside helios_solve_re is two launches: sweep and this.
+// gate: atmospheres whose status is not ACTIVE are skipped (inside helios_solve_re); without it
+// every atmosphere is stepped and its status recomputed (helios_re_step).  do_finalize: the
+// bolometric sums are done here (few work items per atmosphere); otherwise finalize_kernel,
+// spread over many blocks, has written Fup/Fdn already.
+__global__ void post_kernel(PlanDev P, TempArgs targ, double* __restrict__ Fup, double* __restrict__ Fdn,
+                            double* __restrict__ T_layer, double* __restrict__ mult, uint8_t* __restrict__ hist,
+                            uint8_t* __restrict__ nhist, int* __restrict__ status, int* __restrict__ iters,
+                            double* __restrict__ metric_out, int* __restrict__ n_active, int gate, int do_finalize,
+                            int do_prep)
+{
+    __shared__ double sF[2][kPostMaxIf];
+    __shared__ unsigned long long s_max[32];
+    const int a = blockIdx.x;
+    if (gate && status[a] != 0) return;
+    if (!gate && threadIdx.x == 0) status[a] = 0;   // re-decided by this step's metric
+    const AtmDesc ad = P.atms[a];
+    const double* Fu = Fup + ad.if_off;
+    const double* Fd = Fdn + ad.if_off;
+    if (do_finalize) {
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = threadIdx.x >> 5; i <= ad.n; i += nw) {
+            double up, dn;
+            finalize_sums(P, ad, i, lane, up, dn);
+            if (lane == 0) {
+                Fup[ad.if_off + i] = up;
+                Fdn[ad.if_off + i] = dn;
+                sF[0][i] = up;
+                sF[1][i] = dn;
+            }
+        }
+        Fu = sF[0];
+        Fd = sF[1];
     }
+    __syncthreads();
+    temp_block(P, targ, ad, a, Fu, Fd, T_layer, mult, hist, nhist, status, iters, metric_out, n_active, s_max);
+    if (!do_prep) return;
+    __syncthreads();                        // the new temperatures and the status are visible
+    if (status[a] != 0) return;             // converged or failed in this step: no next evaluation
+    for (int p = threadIdx.x; p < 2 * ad.n + 1; p += blockDim.x) prep_point(P, T_layer, ad, p, 1);
 }
 
 // ---------------------------------------------------------------------------

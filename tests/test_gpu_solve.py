@@ -196,3 +196,41 @@ def test_direct_column_solve_reaches_the_same_equilibrium():
     iters, status = plan.solve_re(T)
     assert status.item() == 1
     assert np.abs(T.cpu().numpy() - Tref).max() < 0.1
+
+
+def test_re_step_equals_sweep_plus_temperature_update_bitwise():
+    import torch
+    wl = _small_ragged([3, 20, 41], max_bins=16)
+    T0 = [synth.perturbed_profile(a, i) for i, a in enumerate(wl.atms)]
+    pa, pb = make_plan(wl), make_plan(wl)
+    Ta, Tb = pack(T0), pack(T0)
+    sa, sb = pa.new_state(), pb.new_state()
+    Fub = torch.empty(pb.info.interfaces, dtype=torch.float64, device="cuda"); Fdb = torch.empty_like(Fub)
+    for k in range(4):
+        Fua, Fda, _ = pa.flux_sweep(Ta, warm=k > 0, want_toa=False)
+        pa.temp_update(Fua, Fda, Ta, sa)
+        pb.re_step(Tb, sb, warm=k > 0, out=(Fub, Fdb))
+        assert bool((Fua == Fub).all()) and bool((Fda == Fdb).all())
+        assert bool((Ta == Tb).all())
+        for key in ("mult", "hist", "nhist", "status", "iters", "metric"):
+            assert bool((sa[key] == sb[key]).all()), key
+
+
+def test_solve_equals_a_loop_of_re_steps():
+    # helios_solve_re (graph loop; the next step's point quantities prepared by the post kernel)
+    # and a host loop of helios_re_step reach the same temperatures in the same number of steps
+    wl = synth.small_scattering(L=12, n=30)
+    p1 = make_plan(wl, max_iter=20000)
+    T1 = pack([wl.atms[0].T_init])
+    iters, status = p1.solve_re(T1)
+    assert status.item() == 1
+    p2 = make_plan(wl)
+    T2 = pack([wl.atms[0].T_init])
+    s2 = p2.new_state()
+    for k in range(20000):
+        p2.re_step(T2, s2, warm=k > 0)
+        if s2["status"].item() == 1:          # stop at the first converged step, as the solve does
+            break
+    assert s2["status"].item() == 1
+    assert int(s2["iters"].item()) == int(iters.item())
+    assert bool((T1 == T2).all())
