@@ -134,7 +134,7 @@ typedef struct {
     int check_every;     /* helios_solve_re: iterations per CUDA-graph launch between checks (0: auto) */
     int persistent;      /* 1: a resident grid pulls work items from a counter; 0: one block per item */
     int iso_layers;      /* 0: non-isothermal layers, two linear-B sublayers each (Sect. 2.2.1, Fig. 2);
-                            1: isothermal layers (Sect. 2.2.1, eqs. 9-10): layer i at its centre
+                            1: isothermal layers (Sect. 2.2.1, eqs. 9, 11): layer i at its centre
                             temperature and pressure, opacity at the centre, optical thickness over
                             the whole layer -- the grid of the emission spectra computed as a
                             post-processing step (Sect. 3; with n_passes = 81, Sect. 2.2.3) */

@@ -501,7 +501,7 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
 
 /* ------------------------------------------------------------------------ */
 /* Two-stream fluxes across one isothermal layer of Planck intensity B,
- * Sect. 2.1.3: eq. (9) without scattering (omega0 = 0), eq. (10) with the
+ * Sect. 2.1.3: eq. (9) without scattering (omega0 = 0), eq. (11) with the
  * coefficients of eq. (12) and the coupling coefficients of eq. (13) otherwise,
  * and the pure-scattering form eq. (14) when 1 - omega0 < w0_pure.  Inputs and
  * outputs as ref_layer_twostream. */
@@ -528,7 +528,7 @@ static void iso_layer(double F1up, double F2dn, double B, double dtau, double w0
     double beta = zp * zm * (1.0 - trans * trans);
     double xi = (zm * zm - zp * zp) * trans;
     double ups = (zm * zm * trans + zp * zp) * (1.0 - trans);
-    *F2up = (xi * F1up - beta * F2dn + 2.0 * PI * eps * B * (beta - ups)) / alpha;   /* eq. (10) */
+    *F2up = (xi * F1up - beta * F2dn + 2.0 * PI * eps * B * (beta - ups)) / alpha;   /* eq. (11) */
     *F1dn = (xi * F2dn - beta * F1up + 2.0 * PI * eps * B * (beta - ups)) / alpha;
 }
 
@@ -538,7 +538,7 @@ static void iso_layer(double F1up, double F2dn, double B, double dtau, double w0
  * of its centre (the same centres as the non-isothermal grid), its opacity is
  * interpolated there (Sect. 2.3), and its optical thickness is kappa_i dm_i with
  * dm_i = (P_i - P_{i+1})/g between its interfaces (eq. 18).  Layer fluxes from
- * eqs. (9), (10) or (14) with B_i = B(T_i).  Passes, boundary conditions (eqs.
+ * eqs. (9), (11) or (14) with B_i = B(T_i).  Passes, boundary conditions (eqs.
  * 20, 22) and the Gauss-point and bin sums as ref_flux_sweep, each pass from
  * the previous pass's upward fluxes, the first from zero.  Fup_bol, Fdn_bol:
  * [n+1] at the interfaces; Fup_toa: [L] (optional).  Returns 0, or -1 on a
@@ -629,7 +629,7 @@ int ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, i
  * ref_layer_affine returns the six coefficients of ref_layer_twostream's layer
  * (eq. 14 for pure scattering, eq. 11 below dtau_iso, else eq. 15, with the same
  * readings); iso_affine those of an isothermal layer of Planck intensity B
- * (eq. 9 without scattering, eq. 10 with it, eq. 14 for pure scattering). */
+ * (eq. 9 without scattering, eq. 11 with it, eq. 14 for pure scattering). */
 void ref_layer_affine(double B1, double B2, double dtau, double w0, double g0, const ref_params* p, double* c)
 {
     const double D = p->D, eps = 1.0 / D;
@@ -683,7 +683,7 @@ static void iso_affine(double B, double dtau, double w0, double g0, const ref_pa
     double beta = zp * zm * (1.0 - trans * trans);
     double xi = (zm * zm - zp * zp) * trans;
     double ups = (zm * zm * trans + zp * zp) * (1.0 - trans);
-    c[0] = c[3] = xi / alpha;                                                   /* eq. (10) */
+    c[0] = c[3] = xi / alpha;                                                   /* eq. (11) */
     c[1] = c[4] = -beta / alpha;
     c[2] = c[5] = 2.0 * PI * eps * B * (beta - ups) / alpha;
 }

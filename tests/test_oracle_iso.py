@@ -1,4 +1,4 @@
-"""Pins of the oracle's isothermal-layer grid (Sect. 2.2.1, eqs. 9-10 and 14): the grid on
+"""Pins of the oracle's isothermal-layer grid (Sect. 2.2.1, eqs. 9, 11 and 14): the grid on
 which the emission spectra are computed after convergence (Sect. 3, post-processing).
 
 - an isothermal cavity carries pi B at every interface, with and without scattering;
