@@ -537,7 +537,7 @@ static void iso_layer(double F1up, double F2dn, double B, double dtau, double w0
  * a post-processing step).  Layer i has the temperature T[i] and the pressure
  * of its centre (the same centres as the non-isothermal grid), its opacity is
  * interpolated there (Sect. 2.3), and its optical thickness is kappa_i dm_i with
- * dm_i = (P_i - P_{i+1})/g between its interfaces (eq. 18).  Layer fluxes from
+ * dm_i = (P_i - P_{i+1})/g between its interfaces (eq. 19).  Layer fluxes from
  * eqs. (9), (11) or (14) with B_i = B(T_i).  Passes, boundary conditions (eqs.
  * 20, 22) and the Gauss-point and bin sums as ref_flux_sweep, each pass from
  * the previous pass's upward fluxes, the first from zero.  Fup_bol, Fdn_bol:

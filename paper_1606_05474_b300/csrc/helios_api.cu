@@ -475,7 +475,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
             host_table_coord(lq, k.log10P0, k.dlog10P, k.nP, iP[d.pt_off + p], wP[d.pt_off + p]);
         }
         for (int s = 0; s < 2 * n; ++s) {
-            // isothermal layers: sublayer 2i is layer i between its interfaces (eq. 18), sublayer
+            // isothermal layers: sublayer 2i is layer i between its interfaces (eq. 19), sublayer
             // 2i+1 the zero-thickness step to layer i+1
             const double dP = prm->iso_layers ? ((s & 1) ? 0.0 : Pp[s] - Pp[s + 2]) : Pp[s] - Pp[s + 1];
             dm[d.sub_off + s] = (float)(dP / b->grav[a]);
