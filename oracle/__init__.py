@@ -55,7 +55,7 @@ class RefAtm(ctypes.Structure):
                 ("nP", ctypes.c_int), ("nT", ctypes.c_int), ("L_table", ctypes.c_int),
                 ("log10P0", ctypes.c_double), ("dlog10P", ctypes.c_double),
                 ("T0", ctypes.c_double), ("dT", ctypes.c_double),
-                ("kappa", ctypes.c_void_p), ("grey", ctypes.c_int)]
+                ("kappa", ctypes.c_void_p), ("grey", ctypes.c_int), ("rayleigh", ctypes.c_int)]
 
 
 class RefParams(ctypes.Structure):
@@ -93,6 +93,8 @@ def _load():
     lib.ref_flux_direct.argtypes = [P(RefAtm), P(RefParams), vp, i, vp, vp, vp]
     lib.ref_layer_affine.restype = None
     lib.ref_layer_affine.argtypes = [d, d, d, d, d, P(RefParams), vp]
+    lib.ref_rayleigh_kappa.restype = d
+    lib.ref_rayleigh_kappa.argtypes = [d, d, d]
     lib.ref_flux_sweep_iso.restype = i
     lib.ref_flux_sweep_iso.argtypes = [P(RefAtm), P(RefParams), vp, i, vp, vp, vp]
     lib.ref_temp_update.restype = i
@@ -120,7 +122,7 @@ def params(**overrides) -> RefParams:
 class Atm:
     """An oracle view of one synthetic atmosphere (keeps its arrays alive)."""
 
-    def __init__(self, atm, table, grey: bool = False, kappa64=None):
+    def __init__(self, atm, table, grey: bool = False, kappa64=None, rayleigh: bool = False):
         self.src = atm
         self.nu = np.ascontiguousarray(atm.nu_edges, dtype=np.float64)
         self.w0 = np.ascontiguousarray(atm.omega0, dtype=np.float64)
@@ -136,6 +138,7 @@ class Atm:
         s.log10P0, s.dlog10P, s.T0, s.dT = table.log10P0, table.dlog10P, table.T0, table.dT
         s.kappa = self.kappa.ctypes.data
         s.grey = 1 if grey else 0
+        s.rayleigh = 1 if rayleigh else 0
         self.s = s
         self.n, self.L, self.G = atm.n_layers, atm.n_bins, table.G
 
@@ -268,6 +271,11 @@ def flux_direct(atm: Atm, T: np.ndarray, iso: bool = False, p: RefParams = None)
     rc = _load().ref_flux_direct(ctypes.byref(atm.s), ctypes.byref(p), T.ctypes.data, 1 if iso else 0,
                                  Fu.ctypes.data, Fd.ctypes.data, toa.ctypes.data)
     return {"Fup": Fu, "Fdn": Fd, "toa": toa, "rc": rc}
+
+
+def rayleigh_kappa(nu_lo, nu_hi, mbar_mp=2.4):
+    """H2 Rayleigh opacity (cm^2/g) of the bin [nu_lo, nu_hi] cm^-1 (eqs. 16-17)."""
+    return _load().ref_rayleigh_kappa(nu_lo, nu_hi, mbar_mp)
 
 
 def layer_affine(B1, B2, dtau, w0, g0, p: RefParams = None):

@@ -158,6 +158,21 @@ double ref_planck_bin(double nu_lo, double nu_hi, double T)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Opacity of Rayleigh scattering by H2 in a bin (Sect. 2.1.4): the cross section
+ * sigma = 24 pi^3 / (n_ref^2 lambda^4) ((n^2 - 1)/(n^2 + 2))^2 K (eq. 16) with
+ * n_ref = 2.68678e19 cm^-3, K = 1 and the refractive index
+ * n = 13.58e-5 (1 + 7.52e-11 cm^2 / lambda^2) + 1 (eq. 17), at the bin's centre
+ * wavelength lambda = 1/nu_c, divided by the mean molecular mass (cm^2/g). */
+double ref_rayleigh_kappa(double nu_lo, double nu_hi, double mbar_mp)
+{
+    const double lam = 1.0 / (0.5 * (nu_lo + nu_hi));                      /* cm */
+    const double n = 13.58e-5 * (1.0 + 7.52e-11 / (lam * lam)) + 1.0;
+    const double f = (n * n - 1.0) / (n * n + 2.0);
+    const double nref = 2.68678e19;
+    const double sigma = 24.0 * PI * PI * PI / (nref * nref * pow(lam, 4)) * f * f;
+    return sigma / (mbar_mp * M_PROTON);
+}
+
 /* Model grid, Sect. 2.2.1 and Fig. 2.  Layer centres are evenly spaced in
  * log10 P from P_bot (layer 0) to P_top (layer n-1); interfaces sit midway in
  * log P (the geometric mean of adjacent centres) and the outermost interfaces
@@ -375,6 +390,7 @@ void ref_layer_exact(double F1up, double F2dn, double B1, double B2, double dtau
  * omega0 = 0 the up and down streams decouple and one pass is exact). */
 int ref_passes(const ref_atm* a, const ref_params* p)
 {
+    if (a->rayleigh) return 1 + p->n_scat;
     for (int l = 0; l < a->L; ++l)
         if (a->omega0[l] != 0.0) return 1 + p->n_scat;
     return 1;
@@ -438,7 +454,9 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
         double* dtau = (double*)malloc(sizeof(double) * (np - 1));
         double* Fup = (double*)malloc(sizeof(double) * np);
         double* Fdn = (double*)malloc(sizeof(double) * np);
-        const double w0 = a->omega0[l], g0 = a->g0[l];
+        const double g0 = a->g0[l];
+        const double kR = a->rayleigh ? ref_rayleigh_kappa(a->nu_edges[l], a->nu_edges[l + 1], p->mbar_mp) : 0.0;
+        double* w0s = (double*)malloc(sizeof(double) * (np - 1));
         for (int q = 0; q < np; ++q) B[q] = bin_planck(a, l, Tp[q]);
         if (Fup_spec) memset(Fup_spec + (size_t)l * np, 0, sizeof(double) * np);
         if (Fdn_spec) memset(Fdn_spec + (size_t)l * np, 0, sizeof(double) * np);
@@ -452,7 +470,13 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
                 kap[q] = (1.0 - wT[q]) * ((1.0 - wP[q]) * k00 + wP[q] * k10)
                        + wT[q] * ((1.0 - wP[q]) * k01 + wP[q] * k11);
             }
-            for (int s = 0; s < np - 1; ++s) dtau[s] = 0.5 * (kap[s] + kap[s + 1]) * dm[s];
+            /* sublayer opacity: the mean of its end points (Sect. 2.3), plus the Rayleigh
+             * opacity, whose share of it is the sublayer's omega0 (Sect. 2.1.4) */
+            for (int s = 0; s < np - 1; ++s) {
+                const double kabs = 0.5 * (kap[s] + kap[s + 1]);
+                dtau[s] = (kabs + kR) * dm[s];
+                w0s[s] = a->rayleigh ? kR / (kabs + kR) : a->omega0[l];
+            }
             double* wcol = warm ? warm + ((size_t)l * G + g) * np : NULL;
             for (int q = 0; q < np; ++q) Fup[q] = (wcol && warm_valid) ? wcol[q] : 0.0;
             for (int pass = 0; pass < n_passes; ++pass) {
@@ -462,14 +486,16 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
                     if (exact)
                         ref_layer_exact(Fup[s], Fdn[s + 1], B[s], B[s + 1], dtau[s], p->dtau_iso, &up_dummy, &Fdn[s]);
                     else
-                        ref_layer_twostream(Fup[s], Fdn[s + 1], B[s], B[s + 1], dtau[s], w0, g0, p, &up_dummy, &Fdn[s]);
+                        ref_layer_twostream(Fup[s], Fdn[s + 1], B[s], B[s + 1], dtau[s], w0s[s], g0, p, &up_dummy,
+                                            &Fdn[s]);
                 }
                 Fup[0] = Fdn[0] + bint[l];
                 for (int s = 0; s < np - 1; ++s) {
                     if (exact)
                         ref_layer_exact(Fup[s], Fdn[s + 1], B[s], B[s + 1], dtau[s], p->dtau_iso, &Fup[s + 1], &dn_dummy);
                     else
-                        ref_layer_twostream(Fup[s], Fdn[s + 1], B[s], B[s + 1], dtau[s], w0, g0, p, &Fup[s + 1], &dn_dummy);
+                        ref_layer_twostream(Fup[s], Fdn[s + 1], B[s], B[s + 1], dtau[s], w0s[s], g0, p, &Fup[s + 1],
+                                            &dn_dummy);
                 }
             }
             if (wcol) memcpy(wcol, Fup, sizeof(double) * np);
@@ -483,7 +509,7 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
             for (int q = 0; q < np; ++q)
                 if (!isfinite(Fup[q]) || !isfinite(Fdn[q])) bad = 1;
         }
-        free(B); free(kap); free(dtau); free(Fup); free(Fdn);
+        free(B); free(kap); free(dtau); free(Fup); free(Fdn); free(w0s);
     }
     for (int i = 0; i <= n; ++i) {
         double su = 0.0, sd = 0.0;
@@ -577,7 +603,9 @@ int ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, i
         double* dtau = (double*)malloc(sizeof(double) * n);
         double* Fup = (double*)malloc(sizeof(double) * (n + 1));
         double* Fdn = (double*)malloc(sizeof(double) * (n + 1));
-        const double w0 = a->omega0[l], g0 = a->g0[l];
+        const double g0 = a->g0[l];
+        const double kR = a->rayleigh ? ref_rayleigh_kappa(a->nu_edges[l], a->nu_edges[l + 1], p->mbar_mp) : 0.0;
+        double* w0s = (double*)malloc(sizeof(double) * n);
         for (int i = 0; i < n; ++i) B[i] = bin_planck(a, l, T[i]);
         if (Fup_toa) Fup_toa[l] = 0.0;
         for (int g = 0; g < G; ++g) {
@@ -588,17 +616,18 @@ int ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, i
                 double k01 = table_value(a, iP[i], j1, l, g), k11 = table_value(a, i1, j1, l, g);
                 double kap = (1.0 - wT[i]) * ((1.0 - wP[i]) * k00 + wP[i] * k10)
                            + wT[i] * ((1.0 - wP[i]) * k01 + wP[i] * k11);
-                dtau[i] = kap * dm[i];
+                dtau[i] = (kap + kR) * dm[i];                      /* Rayleigh opacity, Sect. 2.1.4 */
+                w0s[i] = a->rayleigh ? kR / (kap + kR) : a->omega0[l];
             }
             for (int i = 0; i <= n; ++i) Fup[i] = 0.0;
             for (int pass = 0; pass < n_passes; ++pass) {
                 double dummy;
                 Fdn[n] = toa[l];
                 for (int i = n - 1; i >= 0; --i)
-                    iso_layer(Fup[i], Fdn[i + 1], B[i], dtau[i], w0, g0, p, &dummy, &Fdn[i]);
+                    iso_layer(Fup[i], Fdn[i + 1], B[i], dtau[i], w0s[i], g0, p, &dummy, &Fdn[i]);
                 Fup[0] = Fdn[0] + bint[l];
                 for (int i = 0; i < n; ++i)
-                    iso_layer(Fup[i], Fdn[i + 1], B[i], dtau[i], w0, g0, p, &Fup[i + 1], &dummy);
+                    iso_layer(Fup[i], Fdn[i + 1], B[i], dtau[i], w0s[i], g0, p, &Fup[i + 1], &dummy);
             }
             for (int i = 0; i <= n; ++i) {
                 up_bin[(size_t)l * (n + 1) + i] += wg * Fup[i];
@@ -607,7 +636,7 @@ int ref_flux_sweep_iso(const ref_atm* a, const ref_params* p, const double* T, i
             }
             if (Fup_toa) Fup_toa[l] += wg * Fup[n];
         }
-        free(B); free(dtau); free(Fup); free(Fdn);
+        free(B); free(dtau); free(Fup); free(Fdn); free(w0s);
     }
     for (int i = 0; i <= n; ++i) {
         double su = 0.0, sd = 0.0;
@@ -781,7 +810,8 @@ int ref_flux_direct(const ref_atm* a, const ref_params* p, const double* T, int 
         double* kap = (double*)malloc(sizeof(double) * nq);
         double* A = (double*)malloc(sizeof(double) * (size_t)M2 * M2);
         double* x = (double*)malloc(sizeof(double) * M2);
-        const double w0 = a->omega0[l], g0 = a->g0[l];
+        const double g0 = a->g0[l];
+        const double kR = a->rayleigh ? ref_rayleigh_kappa(a->nu_edges[l], a->nu_edges[l + 1], p->mbar_mp) : 0.0;
         for (int q = 0; q < nq; ++q) B[q] = bin_planck(a, l, Tq[q]);
         if (Fup_toa) Fup_toa[l] = 0.0;
         for (int g = 0; g < G; ++g) {
@@ -797,8 +827,10 @@ int ref_flux_direct(const ref_atm* a, const ref_params* p, const double* T, int 
             A[0] = 1.0; A[1] = -1.0; x[0] = bint[l];                    /* eq. (22) */
             for (int s = 0; s < N - 1; ++s) {
                 double c[6];
-                if (iso) iso_affine(B[s], kap[s] * dml[s], w0, g0, p, c);
-                else ref_layer_affine(B[s], B[s + 1], 0.5 * (kap[s] + kap[s + 1]) * dm[s], w0, g0, p, c);
+                const double kabs = iso ? kap[s] : 0.5 * (kap[s] + kap[s + 1]);
+                const double w0 = a->rayleigh ? kR / (kabs + kR) : a->omega0[l];       /* Sect. 2.1.4 */
+                if (iso) iso_affine(B[s], (kabs + kR) * dml[s], w0, g0, p, c);
+                else ref_layer_affine(B[s], B[s + 1], (kabs + kR) * dm[s], w0, g0, p, c);
                 double* ru = A + (size_t)(2 * s + 1) * M2;              /* F_up,s+1 equation */
                 ru[2 * s + 2] = 1.0; ru[2 * s] = -c[0]; ru[2 * s + 3] = -c[1]; x[2 * s + 1] = c[2];
                 double* rd = A + (size_t)(2 * s + 2) * M2;              /* F_dn,s equation */

@@ -44,6 +44,8 @@ typedef struct {
     double T0, dT;            /* temperature nodes T0 + k*dT (K) */
     const double* kappa;
     int grey;                 /* 1: two-band grey test mode (bin 0 visible, bin 1 thermal) */
+    int rayleigh;             /* 1: H2 Rayleigh scattering (eqs. 16-17) added to every (sub)layer's
+                                 opacity; omega0 per (sub)layer, point and g (the per-bin omega0 unused) */
 } ref_atm;
 
 typedef struct {
@@ -74,6 +76,7 @@ double ref_trans_exact(double dtau);            /* 2 E_3(dtau), eq. (6) */
 double ref_diffusivity_exact(double dtau);      /* eq. (7) */
 void   ref_gauss_legendre(int G, double* x, double* w);
 double ref_planck_bin(double nu_lo, double nu_hi, double T);
+double ref_rayleigh_kappa(double nu_lo, double nu_hi, double mbar_mp);
 
 /* grid, temperatures at points, table lookup */
 void   ref_grid(const ref_atm* a, double* log10P_pts, double* P_pts, double* dm_sub, double* P_lay);
