@@ -145,6 +145,10 @@ typedef struct {
     int direct;          /* 1: evaluations with the plan's default passes (n_passes = 0, and every step
                             of helios_solve_re) solve each column's coupled equations exactly instead of
                             making 1 + n_scat passes (HELIOS_DIRECT below) */
+    int rayleigh;        /* 1: Rayleigh scattering by H2 (Sect. 2.1.4, eqs. 16-17): its opacity, per
+                            bin at the bin's centre wavelength over mbar = 2.4 m_p, joins every
+                            sublayer's opacity, and omega0 = kappa_R / (kappa + kappa_R) per sublayer,
+                            bin and g (the batch's omega0 is then not used; g0 is) */
 } helios_params_t;
 
 void helios_default_params(helios_params_t* p);

@@ -22,6 +22,8 @@ constexpr double hP = 6.62607015e-27;
 constexpr double cL = 2.99792458e10;
 constexpr double sigmaSB = 5.670374419e-5;
 constexpr double kPi = 3.14159265358979323846;
+constexpr double mProton = 1.67262192369e-24;
+constexpr double mbarMp = 2.4;        // mean molecular mass in proton masses (Sect. 2.2.1)
 
 thread_local std::string g_err;
 
@@ -251,6 +253,7 @@ void helios_default_params(helios_params_t* p)
     p->iso_layers = 0;
     p->device_loop = 1;
     p->direct = 0;
+    p->rayleigh = 0;
 }
 
 int helios_version(void) { return HELIOS_VERSION; }
@@ -320,7 +323,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         prm->n_scat < 0 || prm->max_iter < 1 || !(prm->osc_down > 0.0) || !(prm->osc_up > 0.0) ||
         !(prm->mult_max > 0.0) || !(prm->T_floor > 0.0) || prm->bins_per_item < 0 || prm->check_every < 0 ||
         prm->persistent < 0 || prm->persistent > 1 || prm->iso_layers < 0 || prm->iso_layers > 1 ||
-        prm->device_loop < 0 || prm->device_loop > 1 || prm->direct < 0 || prm->direct > 1)
+        prm->device_loop < 0 || prm->device_loop > 1 || prm->direct < 0 || prm->direct > 1 ||
+        prm->rayleigh < 0 || prm->rayleigh > 1 || (prm->rayleigh && prm->grey_mode))
         return fail(HELIOS_EINVAL, "invalid parameter set");
     const int G = tabs[0].G;
     if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
@@ -516,6 +520,21 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
             }
             c.toa = (float)toa;
             c.bint = (float)bint;
+            if (prm->rayleigh) {
+                // Sect. 2.1.4, eqs. (16)-(17): H2 cross section at the bin centre over mbar; the
+                // sublayer constants follow from it in the sweep (rayleigh_const)
+                const double lam_cm = 1.0 / nu;
+                const double nr = 13.58e-5 * (1.0 + 7.52e-11 / (lam_cm * lam_cm)) + 1.0;
+                const double f = (nr * nr - 1.0) / (nr * nr + 2.0), nref = 2.68678e19;
+                const double sig = 24.0 * kPi * kPi * kPi / (nref * nref * lam_cm * lam_cm * lam_cm * lam_cm) * f * f;
+                const double g0 = b->g0[d.bin_off + l];
+                c.flags |= BIN_RAYLEIGH;
+                c.lam = (float)(sig / (mbarMp * mProton));
+                c.q = (float)g0;
+                c.gam = (float)(D * (1.0 - g0) / 2.0);
+                any_scat = true;
+                continue;
+            }
             const double w0 = b->omega0[d.bin_off + l], g0 = b->g0[d.bin_off + l];
             if (w0 != 0.0) any_scat = true;
             if (1.0 - w0 < prm->w0_pure) c.flags |= BIN_PURE_SCAT;
@@ -634,6 +653,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
     dv.spec_tab = d_spec_tab; dv.spec_w = d_spec_w;
     dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso; dv.iso_layers = prm->iso_layers;
+    dv.D = (float)prm->D; dv.eps = (float)(1.0 / prm->D); dv.w0_pure = (float)prm->w0_pure;
+    dv.printed_gradient = prm->printed_gradient;
     P->atms_h = ad;
     P->ws_bytes = (int64_t)tot;
     *out = P;

@@ -45,6 +45,8 @@ constexpr int BIN_PURE_SCAT = 1;    // 1 - omega0 < w0_pure: eq. (14), no therma
 constexpr int BIN_NO_SCAT = 2;      // omega0 == 0: streams decouple, one pass is exact
 constexpr int BIN_GREY_DARK = 4;    // grey mode visible band: no emission
 constexpr int BIN_GREY_THERM = 8;   // grey mode thermal band: pi B = sigma T^4
+constexpr int BIN_RAYLEIGH = 16;    // H2 Rayleigh opacity kappa_R (in `lam`) added to every sublayer;
+                                    // omega0 per sublayer and g (g0 in `q`), constants per sublayer
 
 struct BinConst {
     float xs;      // h c nu_c / k_B  (x = xs / T), high part
@@ -110,6 +112,8 @@ struct PlanDev {
     double* part;               // per-item partial sums [3][n+1]
     int G, TB, A;
     float dtau_iso;
+    float D, eps, w0_pure;      // per-sublayer two-stream constants (Rayleigh scattering)
+    int printed_gradient;
     int iso_layers;             // 1: isothermal-layer grid (both points of layer i at T_i)
 };
 
@@ -279,6 +283,36 @@ __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const
     prep_point(P, T_layer, ad, p, warm_valid);
 }
 
+// Two-stream constants of one sublayer of a Rayleigh bin (Sect. 2.1.4): the H2 opacity kappa_R
+// joins the sublayer's absorption opacity kabs, and omega0 = kappa_R / (kabs + kappa_R).
+// 1 - omega0 = kabs/kt and 1 - omega0 g0 = (kabs + kappa_R (1 - g0))/kt are formed from the
+// opacities (no cancellation), as is 1 - r = kappa_R (1 - g0)/(kt (1 - omega0 g0)(1 + r)), so
+// q = zeta_-/zeta_+ = (1 - r)/(1 + r) keeps relative accuracy when scattering is weak.
+// Returns the constants in a BinConst (flags: pure scattering or not) and the total opacity kt.
+__device__ __forceinline__ BinConst rayleigh_const(const BinConst& b, const PlanDev& P, float kabs, float& kt)
+{
+    BinConst c = b;
+    const float kR = b.lam, g0 = b.q;
+    kt = kabs + kR;
+    const float inv = __frcp_rn(kt);
+    const float omw = kabs * inv;                               // 1 - omega0
+    const float omwg = fmaf(kR, 1.0f - g0, kabs) * inv;         // 1 - omega0 g0
+    c.flags = b.flags & ~BIN_RAYLEIGH;
+    if (omw < P.w0_pure) {
+        c.flags |= BIN_PURE_SCAT;
+        return c;
+    }
+    const float r = sqrtf(__fdiv_rn(omw, omwg));
+    const float omr = __fdiv_rn(kR * (1.0f - g0) * inv, omwg * (1.0f + r));
+    const float q = __fdiv_rn(omr, 1.0f + r);
+    c.lam = P.D * sqrtf(omwg * omw);                           // eq. (8)
+    c.q = q;
+    c.q2 = q * q;
+    c.omq2 = __fdiv_rn(4.0f * r, (1.0f + r) * (1.0f + r));     // 1 - q^2
+    c.cl = c.lam * __fdiv_rn(P.eps, P.printed_gradient ? fmaf(kR * inv, g0, 1.0f) : omwg);
+    return c;
+}
+
 // Two-stream coefficients of one sublayer in deviation form (see file header).
 // dB = 2 pi eps (B_bottom - B_top).
 // With WANT_E the absorption Es = 1 - Ts - Rs of the sublayer is returned too, formed without
@@ -288,12 +322,15 @@ template <bool WANT_E = false>
 __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
                                            float& Ts, float& Rs, float& Ss, float* Es = nullptr, float omq = 0.0f)
 {
-    if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source, G = F
+    if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source
         const float a = b.gam * dtau;
         const float t = __frcp_rn(1.0f + a);
         Ts = t;
         Rs = a * t;
-        Ss = 0.0f;
+        // eq. (14) has no source, and Ts + Rs = 1: in deviation form G = F - 2 pi eps B the upward
+        // stream gains Ts dB across the sublayer and the downward one loses it (zero in a
+        // pure-scattering bin, where B = 0; not in a pure-scattering sublayer of a Rayleigh bin)
+        Ss = t * dB;
         if constexpr (WANT_E) *Es = 0.0f;
         return;
     }
@@ -593,8 +630,15 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 const int s = lane * M + k;
                 float t = 1.0f, r = 0.0f, src = 0.0f, e = 0.0f;
                 if (s < NS) {
-                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                    layer_coef<true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, &e, omq);
+                    const float kabs = 0.5f * (krow[s] + krow[s + 1]);          // Sect. 2.3
+                    if (bc.flags & BIN_RAYLEIGH) {
+                        float kt;
+                        const BinConst c = rayleigh_const(bc, P, kabs, kt);
+                        layer_coef<true>(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src, &e,
+                                         __fdiv_rn(c.omq2, 1.0f + c.q));
+                    } else {
+                        layer_coef<true>(bc, kabs * dm[s], dbt[s], P.dtau_iso, t, r, src, &e, omq);   // eq. (19)
+                    }
                 }
                 Ts[k] = t;
                 Rs[k] = r;
@@ -618,18 +662,35 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             float Ts[M], Rs[M], Ss[M], X[M + 1];
             float Ap = 1.0f;
             const float* krow = kap + g * KST;
+            if (bc.flags & BIN_RAYLEIGH) {                                      // uniform per bin
 #pragma unroll
-            for (int k = 0; k < M; ++k) {
-                const int s = lane * M + k;
-                float t = 1.0f, r = 0.0f, src = 0.0f;
-                if (s < NS) {
-                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                    layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
+                for (int k = 0; k < M; ++k) {
+                    const int s = lane * M + k;
+                    float t = 1.0f, r = 0.0f, src = 0.0f;
+                    if (s < NS) {
+                        float kt;
+                        const BinConst c = rayleigh_const(bc, P, 0.5f * (krow[s] + krow[s + 1]), kt);
+                        layer_coef(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src);
+                    }
+                    Ts[k] = t;
+                    Rs[k] = r;
+                    Ss[k] = src;
+                    Ap *= t;
                 }
-                Ts[k] = t;
-                Rs[k] = r;
-                Ss[k] = src;
-                Ap *= t;
+            } else {
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int s = lane * M + k;
+                    float t = 1.0f, r = 0.0f, src = 0.0f;
+                    if (s < NS) {
+                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                        layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
+                    }
+                    Ts[k] = t;
+                    Rs[k] = r;
+                    Ss[k] = src;
+                    Ap *= t;
+                }
             }
             // scan multipliers (depend on the transmissions only)
             float adn[5], aup[5], adn_fin, aup_fin;

@@ -225,3 +225,38 @@ def test_direct_column_solve_conservative_scattering():
     r = oracle.flux_direct(atm, T)
     _check_fluxes(Fu, Fd, r)
     _check_toa(toa, r, atm)
+
+
+@pytest.mark.parametrize("n,L,direct", [(40, 12, 0), (111, 7, 0), (40, 9, 1)])
+def test_rayleigh_scattering_matches_oracle(n, L, direct):
+    # H2 Rayleigh opacity joins every sublayer (Sect. 2.1.4): omega0 and the two-stream constants
+    # per sublayer and g, formed in the sweep
+    import paper_1606_05474_b300 as hp
+    wl = synth.small_scattering(L=L, n=n)
+    atm = oracle.Atm.from_workload(wl, rayleigh=True)
+    T = synth.perturbed_profile(wl.atms[0], 12)
+    plan = make_plan(wl, rayleigh=1)
+    if direct:
+        Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=hp.DIRECT)
+        r = oracle.flux_direct(atm, T)
+    else:
+        Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=5)
+        r = oracle.flux_sweep(atm, T, n_passes=5)
+    assert r["rc"] == 0
+    _check_fluxes(Fu, Fd, r)
+    _check_toa(toa, r, atm)
+
+
+def test_rayleigh_scattering_only_conserves_net_flux():
+    # no absorption: every sublayer is pure scattering (per sublayer, in emitting bins)
+    import paper_1606_05474_b300 as hp
+    wl = synth.small_scattering(L=6, n=40)
+    wl.tables[0].kappa32[...] = 1e-30
+    atm = oracle.Atm.from_workload(wl, rayleigh=True)
+    T = synth.perturbed_profile(wl.atms[0], 13)
+    plan = make_plan(wl, rayleigh=1)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=hp.DIRECT)
+    r = oracle.flux_direct(atm, T)
+    _check_fluxes(Fu, Fd, r)
+    net = (Fu - Fd).cpu().numpy()
+    assert np.max(np.abs(net - net[0])) < 1e-5 * np.max(r["Fup"])

@@ -234,3 +234,16 @@ def test_solve_equals_a_loop_of_re_steps():
     assert s2["status"].item() == 1
     assert int(s2["iters"].item()) == int(iters.item())
     assert bool((T1 == T2).all())
+
+
+def test_rayleigh_atmosphere_converges_to_the_oracle_profile():
+    wl = synth.small_scattering(L=16, n=30)
+    atm = oracle.Atm.from_workload(wl, rayleigh=True)
+    st = oracle.State(atm, wl.atms[0].T_init)
+    rc, it, m = oracle.solve_re(atm, st, oracle.params(tol=1e-10, max_iter=200000))
+    assert rc == oracle.CONVERGED
+    plan = make_plan(wl, max_iter=100000, rayleigh=1)
+    T = pack([wl.atms[0].T_init])
+    iters, status = plan.solve_re(T)
+    assert status.item() == 1
+    assert np.abs(T.cpu().numpy() - st.T).max() < 0.1
