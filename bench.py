@@ -299,8 +299,9 @@ def run_gpu(args):
     table_bytes = touched_table_bytes(plan, wl, T)
     alg_bytes = warm_bytes + table_bytes + 16 * plan.info.interfaces
     achieved = alg_bytes / (sweep_avg * 1e-3) / 1e9
-    sm_max = P.get("sm_max_mhz", 2032.0)
-    fp32_peak = 148 * 128 * sm_max * 1e6 / 1e12       # T FP32 instructions/s (FMA = 1) at max clock
+    # FP32 and MUFU peaks measured on this device (helios_measure_peaks): T instructions/s
+    fp32_tflops, sfu_tops = hp.measure_peaks(ctx)
+    fp32_peak = fp32_tflops / 2.0                        # an FMA counts once as an instruction
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
@@ -315,7 +316,8 @@ def run_gpu(args):
                      "kernel": "sweep_kernel<7>", "kernel_ms": round(sweep_avg, 5),
                      "algorithmic_bytes": int(alg_bytes), "peak_source": "measured",
                      "fp32_frac": round(fp32 / (sweep_avg * 1e-3) / 1e12 / fp32_peak, 4),
-                     "sfu_frac": round(sfu / (sweep_avg * 1e-3) / 1e12 / (148 * 16 * sm_max * 1e6 / 1e12), 4)},
+                     "sfu_frac": round(sfu / (sweep_avg * 1e-3) / 1e12 / sfu_tops, 4),
+                     "fp32_peak_measured_tinst_s": round(fp32_peak, 2), "sfu_peak_measured_tops": round(sfu_tops, 3)},
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(8 * plan.info.layers),
                 "d2h_bytes_per_step": int(8 * plan.info.layers + 4 * plan.A)},
         "gpu_launches": n_launch_per_step * args.steps,
@@ -543,8 +545,7 @@ def run_gpu_spectrum(args):
         return
     cells = plan.info.cells
     P = peaks()
-    sm_max = P.get("sm_max_mhz", 2032.0)
-    fp32_peak = 148 * 128 * sm_max * 1e6 / 1e12
+    fp32_peak = hp.measure_peaks(ctx)[0] / 2.0           # measured, T FP32 instructions/s
     # algorithmic FP32 instructions of the exact solve per cell: 2 sublayers x (24 for the
     # coefficients + 14 for the three recurrences and G_up = rho G_dn + u)
     fp32 = 2 * (24 + 14) * cells
@@ -560,8 +561,8 @@ def run_gpu_spectrum(args):
         "exact": res["exact"], "passes_81": res["passes_81"],
         "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
                      "unit": "T FP32 inst/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                     "kernel": "sweep_kernel<7, 1, true> (exact column solve)",
-                     "peak_source": "148 SMs x 128 FP32 lanes x max SM clock"},
+                     "kernel": "sweep_kernel<7, 2, true> (exact column solve)",
+                     "peak_source": "measured (helios_measure_peaks: independent FMA chains on every SM)"},
         "gpu_launches": 3 * 2 * args.steps,                      # prep, sweep, finalize per spectrum
     }
     print(json.dumps(line), flush=True)

@@ -304,6 +304,12 @@ int helios_mlp_train_step(helios_mlp* mlp, const float* x, const float* target, 
 int helios_autotune(helios_ctx* ctx, const helios_batch_t* batch, const helios_ktable_t* tables, int ntab,
                     const helios_params_t* base, const char* cache_path, helios_params_t* tuned);
 
+/* Measured FP32-FMA throughput (TFLOP/s, an FMA counted as 2) and MUFU ex2
+ * throughput (T op/s) of the context's device, from independent dependency chains
+ * filling every SM (the paper has no counterpart): the denominators of the sweep's
+ * FP32-issue and SFU roofline terms.  Synchronous; allocates and frees a small buffer. */
+int helios_measure_peaks(helios_ctx* ctx, double* fp32_tflops, double* sfu_tops);
+
 /* Allocation-free flux evaluation (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory -- code running under a framework
  * that owns the device's memory pool, or in a region where cudaMalloc is not

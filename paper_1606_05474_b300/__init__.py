@@ -154,6 +154,13 @@ def _marshal(atms, tables, kappa):
     return b, tabs, host
 
 
+def measure_peaks(ctx):
+    """(FP32 TFLOP/s, MUFU ex2 T op/s) measured on the context's device (helios_measure_peaks)."""
+    f, u = ctypes.c_double(), ctypes.c_double()
+    check(ctx.lib.helios_measure_peaks(ctx.h, ctypes.byref(f), ctypes.byref(u)))
+    return f.value, u.value
+
+
 def autotune(ctx, atms, tables, kappa, params=None, cache_path=None):
     """Pick bins_per_item and the launch mode for this batch (helios_autotune); returns tuned params."""
     base = params if params is not None else default_params()

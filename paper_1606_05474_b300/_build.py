@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libhelios.so")
 SOURCES = [os.path.join(HERE, "csrc", "helios_api.cu"), os.path.join(HERE, "csrc", "helios_noalloc.cu"),
-           os.path.join(HERE, "csrc", "helios_mlp.cu")]
+           os.path.join(HERE, "csrc", "helios_mlp.cu"), os.path.join(HERE, "csrc", "helios_peaks.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "helios_mlp.cu"), os.path.join(HERE, "csrc", "helios_kernels.cuh"), os.path.join(ROOT, "include", "helios.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

@@ -247,3 +247,13 @@ def test_rayleigh_atmosphere_converges_to_the_oracle_profile():
     iters, status = plan.solve_re(T)
     assert status.item() == 1
     assert np.abs(T.cpu().numpy() - st.T).max() < 0.1
+
+
+def test_measured_peaks_are_plausible():
+    # FP32 FMA and MUFU ex2 rates of the device: B300 has 148 SMs of 128 FP32 lanes and 16 MUFU
+    # lanes at up to ~2 GHz (nominal 77 TFLOP/s and 4.8 T op/s)
+    import paper_1606_05474_b300 as hp
+    from helpers import ctx
+    f, u = hp.measure_peaks(ctx())
+    assert 20.0 < f < 100.0, f
+    assert 1.0 < u < 12.0, u
