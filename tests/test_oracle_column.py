@@ -187,3 +187,26 @@ def test_grey_two_band_matches_analytic_profile():
     e25, e50 = _grey_error(25), _grey_error(50)
     assert e50 < 1e-3           # 0.1% in T at 50 layers
     assert e25 > 3.0 * e50      # second-order convergence under refinement
+
+
+def test_grey_profile_against_the_eddington_closure():
+    # the method's closure (D = 2, eps = 1/2) against the Eddington-closure grey profile of
+    # Guillot (2010, A&A 520, A27): T^4 = 3/4 T_int^4 (2/3 + tau)
+    #   + 3/4 T_irr^4 [2/3 + 1/(g sqrt3) + (g/sqrt3 - 1/(g sqrt3)) exp(-g tau sqrt3)],
+    # with the incident flux sigma T_irr^4 already averaged (our T_irr).  The two closures differ
+    # by several per cent in T (the deep slope T^4 ~ tau vs 3/4 tau); the converged profile sits
+    # on the D = 2 solution (previous test) and within 10 % of the Eddington one everywhere
+    g = synth.grey_two_band(n=50)
+    atm = oracle.Atm.from_workload(g)
+    st = oracle.State(atm, g.atms[0].T_init)
+    rc, it, m = oracle.solve_re(atm, st, oracle.params(tol=1e-10, max_iter=200000))
+    assert rc == oracle.CONVERGED
+    _, P, _, Pl = oracle.grid(atm)
+    gam, kth = g.meta["gamma"], g.meta["kappa_th"]
+    tau = kth * (Pl - P[-1]) / g.atms[0].grav
+    s3 = math.sqrt(3.0)
+    T4e = 0.75 * 100.0 ** 4 * (2.0 / 3.0 + tau) + 0.75 * 1200.0 ** 4 * (
+        2.0 / 3.0 + 1.0 / (gam * s3) + (gam / s3 - 1.0 / (gam * s3)) * np.exp(-gam * tau * s3))
+    dev = st.T / T4e ** 0.25 - 1.0
+    assert np.abs(dev).max() < 0.10
+    assert np.abs(dev).max() > 0.01          # the closures do differ

@@ -84,3 +84,19 @@ def test_direct_solve_isothermal_cavity_with_scattering():
         r = oracle.flux_direct(atm, np.full(20, 900.0), iso=iso)
         assert np.allclose(r["Fup"], tot, rtol=1e-11) and np.allclose(r["Fdn"], tot, rtol=1e-11)
         assert np.allclose(r["toa"], math.pi * B, rtol=1e-11)
+
+
+def test_pass_truncation_error_against_the_exact_solution():
+    # reading of the scattering passes (Sect. 2.2.3): from a cold start the error of K passes
+    # against the exact column solution falls geometrically with K; a temperature step's
+    # 1 + 4 passes start warm, from the previous step's field
+    wl = synth.small_scattering(L=8, n=20)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 3)
+    d = oracle.flux_direct(atm, T)
+    err = []
+    for K in (1, 2, 5, 10, 20):
+        r = oracle.flux_sweep(atm, T, n_passes=K)
+        err.append(max(np.max(np.abs(r["Fup"] / d["Fup"] - 1)), np.max(np.abs(r["toa"] / d["toa"] - 1))))
+    assert all(a > b for a, b in zip(err, err[1:]))
+    assert err[-1] < 1e-3 * err[0]
