@@ -326,7 +326,7 @@ def run_gpu(args):
         "exact_column_solve": direct,
         "wall_s": round(wall, 3),
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:            # rank 0 at N = 1 only
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     print(json.dumps(line), flush=True)
 
