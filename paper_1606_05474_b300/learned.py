@@ -6,8 +6,8 @@ parameters (T_irr, T_int, log10 g, [M/H], C/O, log10 of the mean opacity) to a 1
 temperature profile (bottom to top, evenly spaced in log P over the model's range) with the
 library's MLP (BF16 tensor-core products, FP32 accumulation, trained with Adam on the solver's
 own converged solutions), interpolates it to each atmosphere's layers and validates it; an
-invalid prediction falls back to the isothermal start, and the plain iteration remains the
-judge of every result (the solver still iterates to eq. 29 from the predicted start).
+invalid prediction falls back to the isothermal start, and the plain iteration still decides
+every result (the solver iterates to eq. 29 from the predicted start).
 """
 from __future__ import annotations
 
