@@ -182,8 +182,9 @@ def run_gpu(args):
     wl.atms[0].T_init = synth.perturbed_profile(wl.atms[0], 11 + rank, amp=200.0)
     ctx = hp.Context(local)
     kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
-    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params())
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(col_lanes=args.col_lanes))
     n_passes = plan.info.passes
+    lanes = 32 if args.col_lanes == 32 else 16       # automatic: 16 lanes for 24..119 layers
     plan.set_timing(args.steps)
     T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).to(dev)
     T0 = T.clone()
@@ -308,12 +309,13 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step", "data": "synthetic",
         "config": {"workload": WORKLOAD, "atmospheres_per_gpu": 1, "layers": 100, "bins": 3000, "g": 20,
                    "passes_per_step": n_passes, "cells_per_step_per_gpu": cells, "l2": "flushed before every step",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "lanes_per_column": lanes},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4),
                      "traffic": (SWEEP_TRAFFIC["bytes_per_launch"]
                                  if kernel_source_hash() == SWEEP_TRAFFIC["kernels_sha256"] else None),
-                     "kernel": "sweep_kernel<7>", "kernel_ms": round(sweep_avg, 5),
+                     "kernel": "sweep_kernel<7> (32 lanes)" if lanes == 32 else "sweep_kernel<13> (16 lanes)",
+                     "kernel_ms": round(sweep_avg, 5),
                      "algorithmic_bytes": int(alg_bytes), "peak_source": "measured",
                      "fp32_frac": round(fp32 / (sweep_avg * 1e-3) / 1e12 / fp32_peak, 4),
                      "sfu_frac": round(sfu / (sweep_avg * 1e-3) / 1e12 / sfu_tops, 4),
@@ -395,7 +397,6 @@ def run_gpu_batched(args):
     table_bytes = touched_table_bytes(plan, wl, T)
     alg_bytes = warm_bytes + table_bytes + 16 * plan.info.interfaces
     achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    groups = len({(2 * a.n_layers + 1 + 31) // 32 | 1 for a in wl.atms})
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -404,7 +405,7 @@ def run_gpu_batched(args):
                                "bins U{300..3000} x 20 g, scattering, 64-table pool",
                    "cells_per_step_per_gpu": cells, "l2": "working set far larger than L2 (no flush)",
                    "tuned": {"bins_per_item": tuned.bins_per_item, "persistent": tuned.persistent},
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "lanes_per_column": "16 for 24..119 layers, else 32"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "sweep_kernel (all lane chunks)",
                      "kernel_ms": round(sweep_ms, 3), "algorithmic_bytes": int(alg_bytes), "peak_source": "measured"},
@@ -638,6 +639,8 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batched", "learned", "spectrum"])
     ap.add_argument("--atmospheres", type=int, default=4096)
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--col-lanes", type=int, default=0, choices=[0, 16, 32],
+                    help="lanes per column of the iterated sweep (16: two Gauss points per warp; 0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--train", type=int, default=2048, help="learned workload: training planets")

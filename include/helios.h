@@ -149,6 +149,12 @@ typedef struct {
                             bin at the bin's centre wavelength over mbar = 2.4 m_p, joins every
                             sublayer's opacity, and omega0 = kappa_R / (kappa + kappa_R) per sublayer,
                             bin and g (the batch's omega0 is then not used; g0 is) */
+    int col_lanes;       /* lanes per column of the iterated sweep: 32 (one warp per Gauss point), 16
+                            (two Gauss points per warp: fewer scan steps and padded sublayer slots
+                            per column, twice the registers per lane; atmospheres of 24 to 119
+                            layers, others are rejected), or 0: 16 where an atmosphere has 24 to 119
+                            layers, else 32.  Results agree to rounding; the exact column solve
+                            always runs 32 lanes per column */
 } helios_params_t;
 
 void helios_default_params(helios_params_t* p);

@@ -144,8 +144,22 @@ class Atm:
 
     @classmethod
     def from_workload(cls, wl, a: int = 0, **kw):
+        """Atmosphere a of a workload; a species mixture (eq. 34) gets its mixed table."""
         atm = wl.atms[a]
+        species = getattr(atm, "species", None)
+        if species and "kappa64" not in kw:
+            kw["kappa64"] = mixed_kappa(wl.tables, species)
         return cls(atm, wl.tables[atm.table_id], grey=wl.grey, **kw)
+
+
+def mixed_kappa(tables, species) -> np.ndarray:
+    """Eq. (34): the opacity of a mixture is sum_j X_j kappa_j over its species.  The species'
+    tables share one (P, T) grid and bilinear interpolation is linear, so the oracle mixes the
+    tables element-wise (float32 values widened to float64) and interpolates the result."""
+    k = np.zeros(tables[0].kappa32.shape)
+    for t, w in species:
+        k += float(w) * tables[t].kappa32.astype(np.float64)
+    return k
 
 
 # ---------------------------------------------------------------------------

@@ -226,7 +226,7 @@ class Plan:
     def interp_opacity(self, T, want_kappa=True, stream=None):
         torch = _torch()
         self._check_T(T)
-        nk = int(sum((2 * n + 1) * L for n, L in zip(self.n, self.L)) * self.G)
+        nk = sum((2 * int(n) + 1) * int(L) for n, L in zip(self.n, self.L)) * int(self.G)
         kap = self._empty(nk, torch.float32) if want_kappa else None
         idx = self._empty(2 * self.info.points, torch.int32)
         w = self._empty(2 * self.info.points, torch.float64)

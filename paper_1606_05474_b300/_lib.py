@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
                 ("fpre_num", c_double), ("fpre_exp", c_double), ("osc_down", c_double), ("osc_up", c_double),
                 ("mult_max", c_double), ("T_floor", c_double), ("n_scat", c_int), ("max_iter", c_int),
                 ("grey_mode", c_int), ("printed_gradient", c_int), ("bins_per_item", c_int),
-                ("check_every", c_int), ("persistent", c_int), ("iso_layers", c_int), ("device_loop", c_int), ("direct", c_int), ("rayleigh", c_int)]
+                ("check_every", c_int), ("persistent", c_int), ("iso_layers", c_int), ("device_loop", c_int), ("direct", c_int), ("rayleigh", c_int),
+                ("col_lanes", c_int)]
 
 
 class PlanInfo(ctypes.Structure):

@@ -64,10 +64,10 @@ struct BinConst {
 };
 
 struct AtmDesc {
-    int n, L, M, tab;
+    int n, L, M, tab;       // M: lane chunk of the iterated sweep's layout (cl lanes per column)
     int lay_off, if_off, pt_off, sub_off;
     int bin_off, item_off, n_items, n_spec;   // n_spec > 1: opacity mixed from several tables
-    int spec_off, pad0, pad1, pad2;
+    int spec_off, cl, pad1, pad2;             // cl: lanes per column of the iterated sweep (16, 32)
     long long warm_off;     // float offset of this atmosphere's warm-start block
     long long part_off;     // double offset of this atmosphere's partial sums
 };
@@ -485,25 +485,34 @@ __device__ __forceinline__ void direct_column(const float (&Ts)[M], const float 
     }
 }
 
-// dynamic shared memory of one sweep block (lane chunk M, G Gauss points): FP64 accumulators
-// [3][16 M], the per-warp rows of opacities / weighted downward deviations and of weighted
-// upward deviations [2][G][32 M + 1], four per-point rows [32 M], and the TOA value
-__host__ __device__ constexpr size_t sweep_smem_bytes(int M, int G)
+// dynamic shared memory of one sweep block (CL lanes per column, lane chunk M, W = CL M point
+// slots, G Gauss points): FP64 accumulators [3][W/2], the per-column rows of opacities / weighted
+// downward deviations and of weighted upward deviations [2][G][W + 1], four per-point rows [W],
+// and the TOA value
+__host__ __device__ constexpr size_t sweep_smem_bytes(int M, int G, int CL = 32)
 {
-    return 3 * (size_t)(16 * M) * sizeof(double) +
-           (2 * (size_t)G * (32 * M + 1) + 4 * (size_t)(32 * M) + 1) * sizeof(float);
+    return 3 * (size_t)(CL * M / 2) * sizeof(double) +
+           (2 * (size_t)G * (CL * M + 1) + 4 * (size_t)(CL * M) + 1) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
 // one work item = (atmosphere, tile of bins); the whole block cooperates
-template <int M, bool DIRECT>
+// CL = 32: one warp per Gauss point; CL = 16: two Gauss points per warp (lanes 0-15 and 16-31),
+// half the scan levels and fewer padded slots per column, at twice the registers per lane
+template <int M, bool DIRECT, int CL = 32>
 __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int* __restrict__ status, int n_passes,
                                            int warm_valid, float* __restrict__ Fup_toa, unsigned char* smem_raw)
 {
-    constexpr int W = 32 * M;               // point slots per column
+    static_assert(CL == 32 || (CL == 16 && !DIRECT), "16-lane columns: iterated passes only");
+    constexpr int W = CL * M;               // point slots per column
     constexpr int KST = W + 1;              // row stride of the per-column smem rows
+    constexpr int LV = CL == 32 ? 5 : 4;    // scan levels
     const int G = P.G;
-    const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g_raw = CL == 32 ? tid >> 5 : 2 * (tid >> 5) + (lane >> 4);
+    const int sub = lane & (CL - 1);        // the lane's place in its column
+    const bool g_ok = g_raw < G;            // odd G, CL = 16: the last warp's upper half is idle
+    const int g = g_ok ? g_raw : G - 1;
     const int2 it = P.items[item];
     if (status && status[it.x] != 0) return;
     const AtmDesc ad = P.atms[it.x];
@@ -524,7 +533,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     const int nthreads = blockDim.x;
     for (int t = tid; t < W; t += nthreads) dm[t] = t < NS ? P.dm[ad.sub_off + t] : 0.0f;
     for (int t = tid; t < 3 * (n + 1); t += nthreads) acc[t] = 0.0;
-    const float wg = P.gw[g];
+    const float wg = g_ok ? P.gw[g] : 0.0f;
     const int p_first = tid / G, g_of = tid - p_first * G;     // gather mapping: consecutive g
     const int p_stride = nthreads / G;
     // float4 gather over four consecutive g when rows stay 16-byte aligned
@@ -619,7 +628,8 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         }
         __syncthreads();
 
-        // ---- phase 2: one warp per Gauss point; lane holds sublayers lane*M .. lane*M+M-1
+        // ---- phase 2: CL lanes per Gauss point; lane `sub` of a column holds its sublayers
+        // sub*M .. sub*M+M-1 (the exact solve: CL = 32)
         if constexpr (DIRECT) {
             // the exact column solution (no passes, no warm start needed)
             float Ts[M], Rs[M], Ss[M], Es[M], U[M], Dn[M];
@@ -655,9 +665,21 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 red_dn[k] = wg * Dn[k];
                 red_up[k] = wg * U[k];
             }
-            const long long col = (long long)(l * G + g) * W;
+            // the warm start of later iterated passes, in their layout: point p at slot
+            // (p mod M') CL' + p / M' of the column's CL' M' slots
+            if (ad.cl == 32) {
+                const long long col = (long long)(l * G + g) * W;
 #pragma unroll
-            for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = U[k];
+                for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = U[k];
+            } else {
+                const int wm = ad.M, wl = ad.cl;
+                const long long col = (long long)(l * G + g) * (wl * wm);
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int p = lane * M + k;
+                    if (p < wl * wm) wbase[col + (p % wm) * wl + p / wm] = U[k];
+                }
+            }
         } else {
             float Ts[M], Rs[M], Ss[M], X[M + 1];
             float Ap = 1.0f;
@@ -665,7 +687,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             if (bc.flags & BIN_RAYLEIGH) {                                      // uniform per bin
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
-                    const int s = lane * M + k;
+                    const int s = sub * M + k;
                     float t = 1.0f, r = 0.0f, src = 0.0f;
                     if (s < NS) {
                         float kt;
@@ -680,7 +702,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             } else {
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
-                    const int s = lane * M + k;
+                    const int s = sub * M + k;
                     float t = 1.0f, r = 0.0f, src = 0.0f;
                     if (s < NS) {
                         const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
@@ -693,24 +715,24 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 }
             }
             // scan multipliers (depend on the transmissions only)
-            float adn[5], aup[5], adn_fin, aup_fin;
+            float adn[LV], aup[LV], adn_fin, aup_fin;
             {
                 float a = Ap;
 #pragma unroll
-                for (int lv = 0; lv < 5; ++lv) {
+                for (int lv = 0; lv < LV; ++lv) {
                     const int d = 1 << lv;
-                    const float ao = __shfl_down_sync(FULL, a, d);
-                    const bool ok = lane + d < 32;
+                    const float ao = __shfl_down_sync(FULL, a, d, CL);
+                    const bool ok = sub + d < CL;
                     adn[lv] = ok ? a : 0.0f;
                     a = ok ? a * ao : a;
                 }
                 adn_fin = a;
                 a = Ap;
 #pragma unroll
-                for (int lv = 0; lv < 5; ++lv) {
+                for (int lv = 0; lv < LV; ++lv) {
                     const int d = 1 << lv;
-                    const float ao = __shfl_up_sync(FULL, a, d);
-                    const bool ok = lane >= d;
+                    const float ao = __shfl_up_sync(FULL, a, d, CL);
+                    const bool ok = sub >= d;
                     aup[lv] = ok ? a : 0.0f;
                     a = ok ? a * ao : a;
                 }
@@ -721,8 +743,8 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             const long long col = (long long)(l * G + g) * W;
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                const int p = lane * M + k;
-                X[k] = warm_valid ? wbase[col + k * 32 + lane] + dbs[p] : -bt[p];
+                const int p = sub * M + k;
+                X[k] = warm_valid ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
             }
             X[M] = 0.0f;
             const float toa_g = bc_toa[0];
@@ -730,8 +752,8 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             __syncwarp();
             // weighted deviations of every point of the column (phase 3 reads the interfaces);
             // the opacity row is free now
-            float* red_dn = kap + g * KST + lane * M;
-            float* red_up = upr + g * KST + lane * M;
+            float* red_dn = kap + g * KST + sub * M;
+            float* red_up = upr + g * KST + sub * M;
             const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
             for (int pass = 0; pass < K; ++pass) {
                 const bool last = pass == K - 1;
@@ -745,14 +767,14 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                         b = fmaf(Ts[k], b, X[k]);
                     }
 #pragma unroll
-                    for (int lv = 0; lv < 5; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv), b);
+                    for (int lv = 0; lv < LV; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv, CL), b);
                     const float outv = fmaf(adn_fin, toa_g, b);
-                    float inv = __shfl_down_sync(FULL, outv, 1);
-                    if (lane == 31) inv = toa_g;
+                    float inv = __shfl_down_sync(FULL, outv, 1, CL);
+                    if (sub == CL - 1) inv = toa_g;
                     X[M] = inv;
 #pragma unroll
                     for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], X[k]);
-                    if (last) {
+                    if (last && g_ok) {
 #pragma unroll
                         for (int k = 0; k < M; ++k) red_dn[k] = wg * X[k];
                     }
@@ -767,22 +789,24 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                         c = fmaf(Ts[k], c, X[k + 1]);
                     }
 #pragma unroll
-                    for (int lv = 0; lv < 5; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv), c);
-                    const float boa = __shfl_sync(FULL, X[0], 0) + bint;
+                    for (int lv = 0; lv < LV; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv, CL), c);
+                    const float boa = __shfl_sync(FULL, X[0], 0, CL) + bint;
                     const float outv = fmaf(aup_fin, boa, c);
-                    float inv = __shfl_up_sync(FULL, outv, 1);
-                    if (lane == 0) inv = boa;
+                    float inv = __shfl_up_sync(FULL, outv, 1, CL);
+                    if (sub == 0) inv = boa;
                     X[0] = inv;
 #pragma unroll
                     for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], X[k + 1]);
-                    if (last) {
+                    if (last && g_ok) {
 #pragma unroll
                         for (int k = 0; k < M; ++k) red_up[k] = wg * X[k];
                     }
                 }
             }
+            if (g_ok) {
 #pragma unroll
-            for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = X[k];
+                for (int k = 0; k < M; ++k) wbase[col + k * CL + sub] = X[k];
+            }
         }
         __syncthreads();
         // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators.
@@ -830,14 +854,14 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 
 // counter == nullptr: block b takes item order[b].  Otherwise persistent: the resident
 // blocks pull items (in cost order) from the counter until the group is exhausted.
-template <int M, int MINB, bool DIRECT = false>
-__global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
-                                                         int* __restrict__ counter, const int* __restrict__ status,
-                                                         int n_passes, int warm_valid, float* __restrict__ Fup_toa)
+template <int M, int MINB, bool DIRECT = false, int CL = 32>
+__global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
+                                                             int* __restrict__ counter, const int* __restrict__ status,
+                                                             int n_passes, int warm_valid, float* __restrict__ Fup_toa)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!counter) {
-        sweep_item<M, DIRECT>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        sweep_item<M, DIRECT, CL>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
         return;
     }
     __shared__ int s_next;
@@ -846,7 +870,7 @@ __global__ void __launch_bounds__(640, MINB) sweep_kernel(PlanDev P, const int* 
         __syncthreads();
         const int k = s_next;
         if (k >= count) break;
-        sweep_item<M, DIRECT>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        sweep_item<M, DIRECT, CL>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
         __syncthreads();                    // shared memory is reused by the next item
     }
 }

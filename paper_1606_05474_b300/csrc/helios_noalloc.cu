@@ -286,7 +286,7 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     for (int t = 0; t < items; ++t) { h_items[t] = make_int2(0, t); h_order[t] = t; }
     gauss_weights(G, h_gw);
     std::memset(&h_atm, 0, sizeof h_atm);
-    h_atm.n = n; h_atm.L = L; h_atm.M = M; h_atm.tab = 0; h_atm.n_items = items;
+    h_atm.n = n; h_atm.L = L; h_atm.M = M; h_atm.cl = 32; h_atm.tab = 0; h_atm.n_items = items;
     std::memset(&h_tab, 0, sizeof h_tab);
     h_tab.kappa = tab->kappa; h_tab.nP = tab->nP; h_tab.nT = tab->nT; h_tab.L = tab->L; h_tab.G = G;
     h_tab.log10P0 = tab->log10P0; h_tab.dlog10P = tab->dlog10P; h_tab.T0 = tab->T0; h_tab.dT = tab->dT;

@@ -347,10 +347,3 @@ def learned_dataset(n_samples: int, L: int = 300, n: int = 100, first: int = 0) 
                                        "log10_mean_kappa": float(np.log10(cA * meanA + cB * meanB))}))
     return Workload(name=f"learned-{n_samples}x{n}x{L}x{G}", atms=atms, tables=[tabA, tabB], n_scat=4)
 
-
-def mixed_table64(wl: Workload, atm: Atmosphere) -> np.ndarray:
-    """The element-wise mixed table of a species-mixing atmosphere, float64 (for the oracle)."""
-    k = np.zeros(wl.tables[0].kappa32.shape)
-    for t, w in atm.species:
-        k += w * wl.tables[t].kappa32.astype(np.float64)
-    return k

@@ -8,6 +8,7 @@ than in the FP64 oracle; per tensor the relative L2 error is bounded by 2e-3 (on
 import numpy as np
 import pytest
 
+import oracle
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
@@ -116,11 +117,22 @@ def test_learned_initializer_saves_iterations_and_reaches_the_same_equilibrium()
     # eq. (29) bounds the flux divergence, not the distance to the fixed point: Sect. 2.2.4 states
     # it leaves temperature changes of up to 4 K, and layers whose flux divergence responds weakly
     # to T (deep, or of small column mass) may stop that far apart
-    dT = np.abs(T2c - Tc[te])[ok]
+    dT = np.abs(T2c - Tc[te])
     per_atm = dT.max(axis=1)
-    assert np.median(per_atm) < 0.1, np.sort(per_atm)[-8:]
-    assert np.quantile(dT, 0.95) < 0.1, np.sort(per_atm)[-8:]
-    assert dT.max() < 4.0, np.sort(per_atm)[-8:]
+    assert np.median(per_atm[ok]) < 0.1, np.sort(per_atm[ok])[-8:]
+    assert np.quantile(dT[ok], 0.95) < 0.1, np.sort(per_atm[ok])[-8:]
+    # radiative equilibrium need not be unique: an opacity bilinear in T can hold two equilibria
+    # of one atmosphere (in this family one held-out planet has two, 82 K apart in a deep layer).
+    # A start that reaches another one is allowed where the oracle confirms both profiles as
+    # equilibria: the exact column solution's flux divergence stays at the eq. (29) level
+    far = np.where(ok & (per_atm >= 4.0))[0]
+    assert len(far) <= 2, np.sort(per_atm[ok])[-8:]
+    for i in far:
+        atm = oracle.Atm.from_workload(test_wl, int(i))
+        for prof in (T2c[i], Tc[te][i]):
+            d = oracle.flux_direct(atm, prof)
+            div = np.abs(np.diff(d["Fup"] - d["Fdn"])) / (oracle.SIGMA_SB * prof ** 4)
+            assert div.max() < 1e-6, (i, div.max())
     # fewer iterations on average; the step law of eqs. (24)-(28) makes a step's size depend on
     # the flux imbalance only as its 0.1 power, so a closer start saves a modest fraction
     assert it2.cpu().numpy()[ok].mean() < it_plain[te][ok].mean()

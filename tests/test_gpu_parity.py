@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+import paper_1606_05474_b300 as hp
 from helpers import make_plan, pack, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -157,7 +158,7 @@ def test_species_mixing_matches_mixed_table():
     Fu, Fd, toa = plan.flux_sweep(pack(Ts), n_passes=5)
     Fus, Fds = plan.split_interfaces(Fu.cpu().numpy()), plan.split_interfaces(Fd.cpu().numpy())
     for i, a in enumerate(wl.atms):
-        atm = oracle.Atm(a, wl.tables[0], kappa64=synth.mixed_table64(wl, a))
+        atm = oracle.Atm.from_workload(wl, i)
         r = oracle.flux_sweep(atm, Ts[i], n_passes=5)
         assert rel_err(Fus[i], r["Fup"]) < FLUX_TOL and rel_err(Fds[i], r["Fdn"]) < FLUX_TOL
 
@@ -260,3 +261,58 @@ def test_rayleigh_scattering_only_conserves_net_flux():
     _check_fluxes(Fu, Fd, r)
     net = (Fu - Fd).cpu().numpy()
     assert np.max(np.abs(net - net[0])) < 1e-5 * np.max(r["Fup"])
+
+
+@pytest.mark.parametrize("n,L,G", [(36, 9, 20), (40, 12, 7), (111, 7, 20), (119, 4, 3)])
+def test_sixteen_lane_columns_match_oracle(n, L, G):
+    # two Gauss points per warp (16 lanes per column; odd G leaves half a warp idle), cold
+    # then warm-started passes
+    wl = synth.small_scattering(L=L, n=n, G=G)
+    atm = oracle.Atm.from_workload(wl)
+    T1 = synth.perturbed_profile(wl.atms[0], 8)
+    T2 = T1 + 5.0 * np.cos(np.arange(n))
+    plan = make_plan(wl, col_lanes=16)
+    Fu, Fd, toa = plan.flux_sweep(pack([T1]), n_passes=5)
+    warm = np.zeros(atm.L * atm.G * (2 * n + 1))
+    r1 = oracle.flux_sweep(atm, T1, n_passes=5, warm=warm, warm_valid=False)
+    _check_fluxes(Fu, Fd, r1)
+    _check_toa(toa, r1, atm)
+    Fu2, Fd2, toa2 = plan.flux_sweep(pack([T2]), n_passes=5, warm=True)
+    r2 = oracle.flux_sweep(atm, T2, n_passes=5, warm=warm, warm_valid=True)
+    _check_fluxes(Fu2, Fd2, r2)
+    _check_toa(toa2, r2, atm)
+
+
+def test_sixteen_lane_columns_full_size():
+    wl = synth.config2()
+    T = synth.perturbed_profile(wl.atms[0], 6)
+    Fu, Fd, toa = make_plan(wl, col_lanes=16).flux_sweep(pack([T]))
+    r = _oracle_sweep(wl, 0, T)
+    _check_fluxes(Fu, Fd, r)
+    _check_toa(toa, r, oracle.Atm.from_workload(wl))
+
+
+def test_sixteen_lane_columns_reject_what_they_do_not_cover():
+    for n in (23, 120):
+        with pytest.raises(hp.HeliosError, match="16-lane"):
+            make_plan(synth.small_scattering(L=3, n=n), col_lanes=16)
+    with pytest.raises(hp.HeliosError):
+        make_plan(synth.small_scattering(L=3, n=40), col_lanes=8)
+
+
+@pytest.mark.parametrize("n,lanes", [(40, 16), (40, 32), (111, 0), (119, 0)])
+def test_exact_solve_leaves_the_warm_start_of_the_passes(n, lanes):
+    # the exact solve stores its upward deviations in the iterated sweep's layout (16 or 32
+    # lanes per column): passes warm-started from it at the same temperatures stay at the limit,
+    # while passes from a misplaced start would be visibly short of it
+    wl = synth.small_scattering(L=6, n=n)
+    atm = oracle.Atm.from_workload(wl)
+    T = synth.perturbed_profile(wl.atms[0], 9)
+    plan = make_plan(wl, col_lanes=lanes)
+    plan.flux_sweep(pack([T]), n_passes=hp.DIRECT)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=5, warm=True)
+    d = oracle.flux_direct(atm, T)
+    _check_fluxes(Fu, Fd, d)
+    _check_toa(toa, d, atm)
+    cold = oracle.flux_sweep(atm, T, n_passes=5)
+    assert np.max(np.abs(cold["toa"] / d["toa"] - 1)) > 1e-4
