@@ -316,6 +316,13 @@ int helios_autotune(helios_ctx* ctx, const helios_batch_t* batch, const helios_k
  * FP32-issue and SFU roofline terms.  Synchronous; allocates and frees a small buffer. */
 int helios_measure_peaks(helios_ctx* ctx, double* fp32_tflops, double* sfu_tops);
 
+/* y[i] = 1/x[i], i < n, by the device reciprocal of the two-stream coefficients (the
+ * hardware's approximate reciprocal refined by one Newton-Raphson step): a check of that
+ * routine against correctly rounded quotients (no counterpart in the paper).  x, y: device
+ * float arrays of n >= 0 elements (x normal and positive for the stated accuracy); async on
+ * `stream`.  HELIOS_EINVAL for a null array with n > 0 or n < 0. */
+int helios_device_recip(const float* x, float* y, int n, cudaStream_t stream);
+
 /* Allocation-free flux evaluation (the paper has no counterpart; it exists for
  * callers that cannot allocate device memory -- code running under a framework
  * that owns the device's memory pool, or in a region where cudaMalloc is not

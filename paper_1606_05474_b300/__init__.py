@@ -161,6 +161,17 @@ def measure_peaks(ctx):
     return f.value, u.value
 
 
+def device_recip(x, stream=None):
+    """1/x by the device reciprocal of the two-stream coefficients (helios_device_recip); x: a
+    float32 CUDA tensor.  Returns a new tensor."""
+    torch = _torch()
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    y = torch.empty_like(x)
+    check(_lib.load().helios_device_recip(x.data_ptr(), y.data_ptr(), x.numel(), _stream_ptr(stream)))
+    return y
+
+
 def autotune(ctx, atms, tables, kappa, params=None, cache_path=None):
     """Pick bins_per_item and the launch mode for this batch (helios_autotune); returns tuned params."""
     base = params if params is not None else default_params()

@@ -45,7 +45,7 @@ class PlanInfo(ctypes.Structure):
 
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
-           "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_solve_re", "helios_measure_peaks", "helios_plan_set_timing",
+           "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_solve_re", "helios_measure_peaks", "helios_device_recip", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
            "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_forward",
            "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step"]
@@ -77,6 +77,7 @@ def load(path: str = SO_PATH):
     lib.helios_temp_update.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_re_step.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_measure_peaks.argtypes = [vp, P(c_double), P(c_double)]
+    lib.helios_device_recip.argtypes = [vp, vp, c_int, vp]
     lib.helios_solve_re.argtypes = [vp, vp, vp, vp, vp]
     lib.helios_plan_set_timing.argtypes = [vp, c_int]
     lib.helios_plan_last_sweep_ms.argtypes = [vp, P(ctypes.c_float)]

@@ -750,6 +750,15 @@ int helios_plan_sweep_times(helios_plan* p, float* ms, int max_n, int* n_out)
     return HELIOS_OK;
 }
 
+int helios_device_recip(const float* x, float* y, int n, cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(HELIOS_EINVAL, "helios_device_recip: invalid arguments");
+    if (n == 0) return HELIOS_OK;
+    recip_kernel<<<(n + 255) / 256, 256, 0, stream>>>(x, y, n);
+    CUDA_TRY(cudaGetLastError());
+    return HELIOS_OK;
+}
+
 int helios_plan_last_sweep_ms(helios_plan* p, float* ms)
 {
     int n = 0;

@@ -59,3 +59,21 @@ def test_precision_stress_error_tables():
     for r in rows:
         assert r["Fup_rel_max"] < 1e-5 and r["Fdn_rel_max"] < 1e-5 and r["net_rel_max"] < 1e-5, r
         assert r["spectrum_rel_max"] < 1e-5, r
+
+
+def test_device_reciprocal_is_within_an_ulp_and_unbiased():
+    # the layer coefficients' reciprocal (one Newton-Raphson step on the hardware's approximate
+    # reciprocal) against correctly rounded float32 quotients: over the coefficients' range
+    # (1/(1 - q^2 trans^2) of denominators in (1e-7, 1]) and a wide one, every result within one
+    # unit in the last place, nearly all correctly rounded, and errors of either sign alike
+    import torch
+    import paper_1606_05474_b300 as hp
+    rng = np.random.default_rng(17)
+    for lo, hi in ((-7.0, 0.0), (-30.0, 30.0)):
+        x = (10.0 ** rng.uniform(lo, hi, 1 << 20)).astype(np.float32)
+        y = hp.device_recip(torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = np.float32(1.0) / x                          # IEEE float32 division, rounded to nearest
+        ulp = (y.view(np.int32).astype(np.int64) - ref.view(np.int32).astype(np.int64))
+        assert np.abs(ulp).max() <= 1
+        assert np.mean(ulp == 0) > 0.95
+        assert abs(np.mean(ulp)) < 0.01
