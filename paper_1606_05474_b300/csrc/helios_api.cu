@@ -141,15 +141,17 @@ constexpr int kFuseFinalizeItems = 64;
 // were slower again).
 template <int M, bool DIRECT> constexpr int sweep_minb() { return (M <= (DIRECT ? 7 : 11)) ? 2 : 1; }
 
-// 16-lane columns (two per warp): 320-thread blocks, two per SM within 102 registers
-constexpr int kMinB16 = 2;
+// 16-lane columns (two per warp), 320-thread blocks: three per SM (64 registers, a few spilled)
+// up to lane chunk 11, two (96 registers) beyond.  Measured on the full-size bins: three blocks
+// are 5-14 % faster than two up to chunk 11; four at chunks 5-7 were slower again
+template <int M> constexpr int minb16() { return M <= 11 ? 3 : 2; }
 
 template <int M, bool DIRECT, int CL = 32>
 int sweep_occupancy_MD(int threads, size_t smem)
 {
     int nb = 0;
     auto k = [] {
-        if constexpr (CL == 16) return sweep_kernel<M, kMinB16, false, 16>;
+        if constexpr (CL == 16) return sweep_kernel<M, minb16<M>(), false, 16>;
         else return sweep_kernel<M, sweep_minb<M, DIRECT>(), DIRECT>;
     }();
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess ||
@@ -164,8 +166,8 @@ int sweep_occupancy_M(int threads, size_t smem, bool direct)
     return direct ? sweep_occupancy_MD<M, true>(threads, smem) : sweep_occupancy_MD<M, false>(threads, smem);
 }
 
-// lane chunks of 16-lane columns: 24 to 119 layers (chunk 15 is the most that two 320-thread
-// blocks per SM hold in registers without spilling)
+// lane chunks of 16-lane columns: 24 to 119 layers (chunk 15 is the largest that two 320-thread
+// blocks per SM hold in registers with little spilling)
 constexpr bool cl16_chunk(int M) { return M >= 5 && M <= 15; }
 
 // lanes per column of an atmosphere of n layers for the request 0 (automatic), 16 or 32; 0 if
@@ -800,7 +802,7 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
 {
     const size_t smem = sweep_smem(M, p->G, CL);
     const int threads = DIRECT ? 32 * p->G : gr.threads;
-    static thread_local int configured_dev[kMaxM + 1][3][2][2] = {};
+    static thread_local int configured_dev[kMaxM + 1][4][2][2] = {};      // [M][MINB][DIRECT][16 lanes]
     int& conf = configured_dev[M][MINB][DIRECT][CL == 16];
     if (conf != p->ctx->device + 1) {
         CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB, DIRECT, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -824,7 +826,7 @@ int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_pa
 {
     if constexpr (cl16_chunk(M)) {
         if (gr.cl == 16 && n_passes != HELIOS_DIRECT)
-            return launch_sweep_MB<M, kMinB16, false, 16>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+            return launch_sweep_MB<M, minb16<M>(), false, 16>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
     }
     if (n_passes == HELIOS_DIRECT)
         return launch_sweep_MB<M, sweep_minb<M, true>(), true>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
