@@ -130,13 +130,17 @@ class ClockSampler:
 # DRAM traffic (read + write) of one sweep-kernel launch on the full-size single atmosphere, from
 # the ncu capture summarised in profiles/sweep_kernel_full_single_atmosphere.md, valid only for the
 # kernel source it was taken on (sha256 prefix of csrc/helios_kernels.cuh); null otherwise.
-SWEEP_TRAFFIC = {"kernels_sha256": "f868734dac66f515", "bytes_per_launch": 73464832}
+SWEEP_TRAFFIC = {"kernels_sha256": "fbfc5cc9d4ad2ee7", "bytes_per_launch": 62572288}
 
 
 def kernel_source_hash():
+    """Hash of the sweep kernel's source and its launch configuration (the recorded DRAM traffic
+    holds only while both are unchanged)."""
     import hashlib
-    p = os.path.join(ROOT, "paper_1606_05474_b300", "csrc", "helios_kernels.cuh")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("helios_kernels.cuh", "helios_api.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1606_05474_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def algorithmic_counts(wl, n_passes):

@@ -229,7 +229,7 @@ struct MGroup {
     int M_direct;     // lane chunk of the exact column solve (32 lanes per column)
     int count;
     int* order;       // device
-    int* counter;     // device work counter (persistent launches)
+    int* counter;     // device work counters of persistent launches: [items pulled, blocks done]
     int grid;         // persistent grid: resident blocks on all SMs
     int grid_direct;  // the same for the direct column solve
     cudaStream_t stream;   // the group's own stream (several groups overlap)
@@ -659,7 +659,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     ALLOC(dv.part, part); ALLOC(dv.warm, warm);
     ALLOC(P->Fup, ifc); ALLOC(P->Fdn, ifc); ALLOC(P->mult, lay); ALLOC(P->hist, lay); ALLOC(P->nhist, lay);
     ALLOC(P->n_active, 1); ALLOC(P->chunks_left, 1);
-    ALLOC(P->counters, kGroups);
+    ALLOC(P->counters, 2 * kGroups);
 #undef ALLOC
     std::vector<int> order;
     int nsm_all = 148;
@@ -675,7 +675,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         gr.M_direct = gr.cl == 32 ? gr.M : lane_chunk((gr.cl * gr.M - 1) / 2, 32);
         gr.count = (int)byM[key].size();
         gr.order = d_order + order.size();
-        gr.counter = P->counters + key;
+        gr.counter = P->counters + 2 * key;     // [work items pulled, blocks finished]
         gr.grid = std::min(gr.count, nsm_all * std::max(1, sweep_occupancy(gr.M, gr.threads,
                                                                           sweep_smem(gr.M, G, gr.cl), false, gr.cl)));
         gr.grid_direct = std::min(gr.count, nsm_all * std::max(1, sweep_occupancy(gr.M_direct, 32 * G,
@@ -704,6 +704,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         return rc;
     }
     cudaError_t ce = cudaMemset(dv.warm, 0, std::max<int64_t>(warm, 1) * sizeof(float));
+    if (ce == cudaSuccess) ce = cudaMemset(P->counters, 0, sizeof(int) * 2 * kGroups);   // the sweeps keep them at 0
     if (ce != cudaSuccess) { helios_plan_destroy(P); return fail(HELIOS_ECUDA, "cudaMemset: %s", cudaGetErrorString(ce)); }
     dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.gw = d_gw;
     dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
@@ -842,7 +843,6 @@ int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid
         ++p->n_timed;
         CUDA_TRY(cudaEventRecord(p->ev_sweep0, s));
     }
-    if (p->prm.persistent) CUDA_TRY(cudaMemsetAsync(p->counters, 0, sizeof(int) * kGroups, s));
     const bool fork = p->groups.size() > 1;
     if (fork) CUDA_TRY(cudaEventRecord(p->fork, s));
     for (const MGroup& gr0 : p->groups) {
@@ -887,7 +887,7 @@ int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes
     if (rc) return rc;
     rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
     if (rc) return rc;
-    finalize_kernel<<<dim3((p->max_n + 1 + 7) / 8, p->A), 256, 0, s>>>(p->dev, status, Fup, Fdn);
+    finalize_kernel<<<dim3(p->max_n + 1, p->A), 32, 0, s>>>(p->dev, status, Fup, Fdn);
     CUDA_TRY(cudaGetLastError());
     return HELIOS_OK;
 }
@@ -905,15 +905,16 @@ TempArgs temp_args(const helios_plan* p);
 
 // finalize + temperature step (+ the next evaluation's point quantities) of every atmosphere.
 // The bolometric sums join the per-atmosphere block when every atmosphere has few work items;
-// an atmosphere of many items (a single wide one) keeps them in finalize_kernel, whose blocks
-// spread its interfaces over many SMs
+// an atmosphere of many items (a single wide one) keeps them in finalize_kernel: one warp per
+// block and interface, so its FP64 sums spread over as many SMs as there are interfaces (the
+// FP64 pipe of an SM is narrow)
 int launch_post(helios_plan* p, const int* status_gate, double* Fup, double* Fdn, double* T, double* mult,
                 uint8_t* hist, uint8_t* nhist, int* status, int* iters, double* metric, int* n_active, int gate,
                 int do_prep, cudaStream_t s)
 {
     const int fuse = p->max_items <= kFuseFinalizeItems;
     if (!fuse) {
-        finalize_kernel<<<dim3((p->max_n + 1 + 7) / 8, p->A), 256, 0, s>>>(p->dev, status_gate, Fup, Fdn);
+        finalize_kernel<<<dim3(p->max_n + 1, p->A), 32, 0, s>>>(p->dev, status_gate, Fup, Fdn);
         CUDA_TRY(cudaGetLastError());
     }
     post_kernel<<<p->A, 512, 0, s>>>(p->dev, temp_args(p), Fup, Fdn, T, mult, hist, nhist, status, iters, metric,

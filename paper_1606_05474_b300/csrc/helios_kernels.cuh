@@ -872,7 +872,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 }
 
 // counter == nullptr: block b takes item order[b].  Otherwise persistent: the resident
-// blocks pull items (in cost order) from the counter until the group is exhausted.
+// blocks pull items (in cost order) from counter[0] until the group is exhausted; counter[1]
+// counts the blocks that have left, and the last one to leave returns both to zero for the
+// next launch (every block has then stopped pulling), so no reset is needed between launches.
 template <int M, int MINB, bool DIRECT = false, int CL = 32>
 __global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
                                                              int* __restrict__ counter, const int* __restrict__ status,
@@ -891,6 +893,10 @@ __global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const i
         if (k >= count) break;
         sweep_item<M, DIRECT, CL>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
         __syncthreads();                    // shared memory is reused by the next item
+    }
+    if (threadIdx.x == 0 && atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {
+        atomicExch(counter, 0);
+        atomicExch(counter + 1, 0);
     }
 }
 
@@ -964,14 +970,26 @@ __device__ __forceinline__ void temp_block(const PlanDev& P, const TempArgs& tar
     const int i = threadIdx.x, lane = i & 31, w = i >> 5;
     const bool mine = i < ad.n;
     const int li = ad.lay_off + i;
-    double dF = 0.0, Ti = 1.0;
+    double dF = 0.0, Ti = 1.0, m_old = 1.0, step = 0.0;
+    unsigned h_old = 0u, c_old = 0u;
     unsigned long long bits = 0ull;
     if (mine) {
+        // the layer's state and its candidate step are read and formed before the block-wide
+        // reduction (no barrier in between, so the loads and the FP64 pow overlap it); they are
+        // applied below only while the atmosphere is not converged
+        m_old = mult[li];
+        h_old = hist[li];
+        c_old = nhist[li];
+        const double lnr = P.lnr[li];
         dF = layer_divergence(Fu, Fd, i);
         Ti = T_layer[li];
         double m = fabs(dF) / (targ.sigma * Ti * Ti * Ti * Ti);
         if (!(m == m) || !isfinite(Ti) || isinf(m)) m = __longlong_as_double(0x7ff8000000000000ll);
         bits = (unsigned long long)__double_as_longlong(m);
+        if (dF != 0.0) {
+            const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) / (targ.sigma * Ti * Ti * Ti * lnr);
+            step = -m_old * (dF > 0.0 ? mag : -mag);
+        }
     }
     // non-negative doubles order like their bit patterns (NaN above +inf): an exact max
 #pragma unroll
@@ -1007,22 +1025,16 @@ __device__ __forceinline__ void temp_block(const PlanDev& P, const TempArgs& tar
         }
     }
     if (mine && !bad && !(worst < targ.tol)) {
-        double step = 0.0;
-        if (dF != 0.0) {
-            const double mag = targ.fpre_num * pow(fabs(dF), 1.0 - targ.fpre_exp) /
-                               (targ.sigma * Ti * Ti * Ti * P.lnr[li]);
-            step = -mult[li] * (dF > 0.0 ? mag : -mag);
-        }
         double Tn = Ti + step;
         if (Tn < targ.T_floor) Tn = targ.T_floor;
         T_layer[li] = Tn;
-        const unsigned h = ((unsigned)hist[li] << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
+        const unsigned h = (h_old << 1 | (step > 0.0 ? 1u : 0u)) & 0x3Fu;
         hist[li] = (uint8_t)h;
-        unsigned c = nhist[li];
+        unsigned c = c_old;
         if (c < 6) c += 1;
         nhist[li] = (uint8_t)c;
         if (c >= 6) {
-            double m = mult[li];
+            double m = m_old;
             if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
             else m = m * targ.osc_down;
             mult[li] = m;
