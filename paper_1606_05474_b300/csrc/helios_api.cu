@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 using namespace helios_dev;
@@ -797,6 +798,38 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, const int* n_acti
     cudaGraphSetConditional(h, (*n_active > 0 && left > 0) ? 1u : 0u);
 }
 
+// Programmatic dependent launch of the kernels of one evaluation (prep, sweep, finalize, post;
+// each waits for its predecessor's completion before touching memory, see pdl_enter): only on
+// an ordinary stream -- not while it is being captured into a graph, not between the sweep
+// timing events -- and for the sweep only when a single launch group runs on the caller's stream
+bool use_pdl(const helios_plan* p, cudaStream_t s)
+{
+    if (p->timing) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusNone;
+}
+
+template <typename... KArgs, typename... Args>
+int launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    return HELIOS_OK;
+}
+
 template <int M, int MINB, bool DIRECT, int CL = 32>
 int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
                     float* Fup_toa, cudaStream_t s)
@@ -810,15 +843,13 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
                                       200 * 1024));
         conf = p->ctx->device + 1;
     }
-    if (p->prm.persistent) {
-        sweep_kernel<M, MINB, DIRECT, CL><<<DIRECT ? gr.grid_direct : gr.grid, threads, smem, s>>>(
-            p->dev, gr.order, gr.count, gr.counter, status, n_passes, warm_valid, Fup_toa);
-    } else {
-        sweep_kernel<M, MINB, DIRECT, CL><<<gr.count, threads, smem, s>>>(p->dev, gr.order, gr.count, nullptr,
-                                                                           status, n_passes, warm_valid, Fup_toa);
-    }
-    CUDA_TRY(cudaGetLastError());
-    return HELIOS_OK;
+    const bool pdl = p->groups.size() == 1 && use_pdl(p, s);
+    if (p->prm.persistent)
+        return launch_k(pdl, sweep_kernel<M, MINB, DIRECT, CL>, dim3(DIRECT ? gr.grid_direct : gr.grid), dim3(threads),
+                        smem, s, p->dev, (const int*)gr.order, gr.count, gr.counter, status, n_passes, warm_valid,
+                        Fup_toa);
+    return launch_k(pdl, sweep_kernel<M, MINB, DIRECT, CL>, dim3(gr.count), dim3(threads), smem, s, p->dev,
+                    (const int*)gr.order, gr.count, (int*)nullptr, status, n_passes, warm_valid, Fup_toa);
 }
 
 template <int M>
@@ -875,9 +906,8 @@ int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid
 
 int launch_prep(helios_plan* p, const double* T, const int* status, int warm_valid, cudaStream_t s)
 {
-    prep_kernel<<<dim3((2 * p->max_n + 1 + 63) / 64, p->A), 64, 0, s>>>(p->dev, T, status, warm_valid);
-    CUDA_TRY(cudaGetLastError());
-    return HELIOS_OK;
+    return launch_k(use_pdl(p, s), prep_kernel, dim3((2 * p->max_n + 1 + 63) / 64, p->A), dim3(64), 0, s, p->dev, T,
+                    status, warm_valid);
 }
 
 int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes, int warm_valid, double* Fup,
@@ -887,9 +917,7 @@ int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes
     if (rc) return rc;
     rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
     if (rc) return rc;
-    finalize_kernel<<<dim3(p->max_n + 1, p->A), 32, 0, s>>>(p->dev, status, Fup, Fdn);
-    CUDA_TRY(cudaGetLastError());
-    return HELIOS_OK;
+    return launch_k(use_pdl(p, s), finalize_kernel, dim3(p->max_n + 1, p->A), dim3(32), 0, s, p->dev, status, Fup, Fdn);
 }
 
 TempArgs temp_args(const helios_plan* p)
@@ -913,14 +941,14 @@ int launch_post(helios_plan* p, const int* status_gate, double* Fup, double* Fdn
                 int do_prep, cudaStream_t s)
 {
     const int fuse = p->max_items <= kFuseFinalizeItems;
+    const bool pdl = use_pdl(p, s);
     if (!fuse) {
-        finalize_kernel<<<dim3(p->max_n + 1, p->A), 32, 0, s>>>(p->dev, status_gate, Fup, Fdn);
-        CUDA_TRY(cudaGetLastError());
+        const int rc = launch_k(pdl, finalize_kernel, dim3(p->max_n + 1, p->A), dim3(32), 0, s, p->dev, status_gate,
+                                Fup, Fdn);
+        if (rc) return rc;
     }
-    post_kernel<<<p->A, 512, 0, s>>>(p->dev, temp_args(p), Fup, Fdn, T, mult, hist, nhist, status, iters, metric,
-                                     n_active, gate, fuse, do_prep);
-    CUDA_TRY(cudaGetLastError());
-    return HELIOS_OK;
+    return launch_k(pdl, post_kernel, dim3(p->A), dim3(512), 0, s, p->dev, temp_args(p), Fup, Fdn, T, mult, hist,
+                    nhist, status, iters, metric, n_active, gate, fuse, do_prep);
 }
 
 int launch_temp(helios_plan* p, const double* Fup, const double* Fdn, double* T, double* mult, uint8_t* hist,

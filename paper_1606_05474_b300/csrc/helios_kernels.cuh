@@ -253,6 +253,18 @@ __device__ __forceinline__ float planck_ff(const BinConst& b, float2 it, float& 
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  The kernels of one evaluation (prep, sweep, finalize, post)
+// may be launched to start while their predecessor in the stream is still running: each one
+// first lets its own successor launch, then waits until its predecessor has completed and its
+// memory is visible, before it reads or writes anything.  Launched the ordinary way, both are
+// no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // point quantities of point p of atmosphere ad at the temperatures T_layer (warm_valid: the
 // previous evaluation's point temperature is the old one of the warm-start shift)
 __device__ __forceinline__ void prep_point(const PlanDev& P, const double* __restrict__ T_layer, const AtmDesc& ad,
@@ -293,6 +305,7 @@ __device__ __forceinline__ void prep_point(const PlanDev& P, const double* __res
 __global__ void prep_kernel(PlanDev P, const double* __restrict__ T_layer, const int* __restrict__ status,
                             int warm_valid)
 {
+    pdl_enter();
     const int a = blockIdx.y;
     if (status && status[a] != 0) return;
     const AtmDesc ad = P.atms[a];
@@ -880,6 +893,7 @@ __global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const i
                                                              int* __restrict__ counter, const int* __restrict__ status,
                                                              int n_passes, int warm_valid, float* __restrict__ Fup_toa)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!counter) {
         sweep_item<M, DIRECT, CL>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
@@ -930,6 +944,7 @@ __device__ __forceinline__ void finalize_sums(const PlanDev& P, const AtmDesc& a
 __global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, double* __restrict__ Fup,
                                 double* __restrict__ Fdn)
 {
+    pdl_enter();
     const int a = blockIdx.y;
     if (status && status[a] != 0) return;
     const AtmDesc ad = P.atms[a];
@@ -1071,6 +1086,7 @@ __global__ void post_kernel(PlanDev P, TempArgs targ, double* __restrict__ Fup, 
                             double* __restrict__ metric_out, int* __restrict__ n_active, int gate, int do_finalize,
                             int do_prep)
 {
+    pdl_enter();
     __shared__ double sF[2][kPostMaxIf];
     __shared__ unsigned long long s_max[32];
     const int a = blockIdx.x;
