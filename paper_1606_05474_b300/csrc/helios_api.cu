@@ -801,10 +801,12 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, const int* n_acti
 // Programmatic dependent launch of the kernels of one evaluation (prep, sweep, finalize, post;
 // each waits for its predecessor's completion before touching memory, see pdl_enter): only on
 // an ordinary stream -- not while it is being captured into a graph, not between the sweep
-// timing events -- and for the sweep only when a single launch group runs on the caller's stream
+// timing events -- and only for plans of a single launch group, whose kernels follow one
+// another directly on the caller's stream (with several groups the sweeps run on forked
+// streams and rejoin through event waits, so a kernel's predecessor is not always a kernel)
 bool use_pdl(const helios_plan* p, cudaStream_t s)
 {
-    if (p->timing) return false;
+    if (p->timing || p->groups.size() != 1) return false;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -843,7 +845,7 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
                                       200 * 1024));
         conf = p->ctx->device + 1;
     }
-    const bool pdl = p->groups.size() == 1 && use_pdl(p, s);
+    const bool pdl = use_pdl(p, s);
     if (p->prm.persistent)
         return launch_k(pdl, sweep_kernel<M, MINB, DIRECT, CL>, dim3(DIRECT ? gr.grid_direct : gr.grid), dim3(threads),
                         smem, s, p->dev, (const int*)gr.order, gr.count, gr.counter, status, n_passes, warm_valid,
