@@ -579,47 +579,49 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     for (int l = l_begin; l < l_end; ++l) {
         const BinConst bc = P.bins[ad.bin_off + l];
         const bool emits = !(bc.flags & (BIN_GREY_DARK | BIN_PURE_SCAT | BIN_GREY_THERM));
-        // ---- phase 1: per-point Planck values, per-sublayer Planck differences (each thread
-        // evaluates its point and the point above, so no barrier is needed in between) ...
-        for (int p = tid; p < W; p += nthreads) {
-            float B = 0.0f, sh = 0.0f, d = 0.0f;
-            if (p < NP) {
-                const int q = ad.pt_off + p;
-                if (bc.flags & BIN_GREY_THERM) {
-                    const float T = P.Tf[q], c = 2.0f * bc.E;       // 2 eps sigma T^4
-                    const float T2 = T * T;
-                    B = c * T2 * T2;
-                    if (warm_valid) {
-                        const float dT = P.dT_step[q], To = T + dT;
-                        sh = c * dT * (To + T) * (To * To + T2);
-                    }
-                    if (p < NS) {
-                        const float Tb = P.Tf[q + 1];
-                        d = c * P.dT_sub[ad.sub_off + p] * (T + Tb) * (T2 + Tb * Tb);
-                    }
-                } else if (emits) {
-                    float x;
-                    B = planck_ff(bc, P.invT[q], x);
-                    if (warm_valid) {
-                        // B_old - B_new = B_new (e^y - 1) / (1 - e^{-x_old}), y = x_new - x_old
-                        const float y = bc.xs * P.dinv_step[q];
-                        float xo;
-                        const float Bo = planck_ff(bc, P.invT_old[q], xo);
-                        sh = fabsf(y) < 1.0f ? B * __fdividef(em1(y), -em1(-xo)) : Bo - B;
-                    }
-                    if (p < NS) {
-                        // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
-                        float xb;
-                        const float Bb = planck_ff(bc, P.invT[q + 1], xb);
-                        const float y = bc.xs * P.dinv_sub[ad.sub_off + p];
-                        d = fabsf(y) < 1.0f ? Bb * __fdividef(em1(y), -em1(-x)) : B - Bb;
-                    }
+        // ---- phase 1: per-point Planck values, per-sublayer Planck differences.  Each warp
+        // takes 31 consecutive points plus, in lane 31, the first point of the next group, so a
+        // lane reads the Planck value of the point above from its neighbour (no barrier and no
+        // second evaluation; lane 31's value serves only that read) ...
+        for (int p0 = (tid >> 5) * 31; p0 < W; p0 += (nthreads >> 5) * 31) {
+            const int p = p0 + lane;
+            const bool pt = p < NP;
+            const int q = ad.pt_off + p;
+            float B = 0.0f, sh = 0.0f, d = 0.0f, x = 0.0f;
+            if (pt && (bc.flags & BIN_GREY_THERM)) {
+                const float T = P.Tf[q], c = 2.0f * bc.E;           // 2 eps sigma T^4
+                const float T2 = T * T;
+                B = c * T2 * T2;
+                if (warm_valid) {
+                    const float dT = P.dT_step[q], To = T + dT;
+                    sh = c * dT * (To + T) * (To * To + T2);
+                }
+                if (p < NS) {
+                    const float Tb = P.Tf[q + 1];
+                    d = c * P.dT_sub[ad.sub_off + p] * (T + Tb) * (T2 + Tb * Tb);
+                }
+            } else if (pt && emits) {
+                B = planck_ff(bc, P.invT[q], x);
+                if (warm_valid) {
+                    // B_old - B_new = B_new (e^y - 1) / (1 - e^{-x_old}), y = x_new - x_old
+                    const float y = bc.xs * P.dinv_step[q];
+                    float xo;
+                    const float Bo = planck_ff(bc, P.invT_old[q], xo);
+                    sh = fabsf(y) < 1.0f ? B * __fdividef(em1(y), -em1(-xo)) : Bo - B;
+                }
+            }
+            const float Bb = __shfl_down_sync(FULL, B, 1);          // B of point p + 1
+            if (lane < 31 && p < W) {
+                if (pt && emits && p < NS) {
+                    // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
+                    const float y = bc.xs * P.dinv_sub[ad.sub_off + p];
+                    d = fabsf(y) < 1.0f ? Bb * __fdividef(em1(y), -em1(-x)) : B - Bb;
                 }
                 if (p == NP - 1) bc_toa[0] = bc.toa - B;
+                bt[p] = B;
+                dbs[p] = sh;
+                dbt[p] = d;
             }
-            bt[p] = B;
-            dbs[p] = sh;
-            dbt[p] = d;
         }
         // ... and the opacity gather, consecutive threads on consecutive g
         if (ad.n_spec > 1) {
