@@ -130,7 +130,7 @@ class ClockSampler:
 # DRAM traffic (read + write) of one sweep-kernel launch on the full-size single atmosphere, from
 # the ncu capture summarised in profiles/sweep_kernel_full_single_atmosphere.md, valid only for the
 # kernel source it was taken on (sha256 prefix of csrc/helios_kernels.cuh); null otherwise.
-SWEEP_TRAFFIC = {"kernels_sha256": "fbfc5cc9d4ad2ee7", "bytes_per_launch": 62572288}
+SWEEP_TRAFFIC = {"kernels_sha256": "97a21530e2888626", "bytes_per_launch": 62859520}
 
 
 def kernel_source_hash():
