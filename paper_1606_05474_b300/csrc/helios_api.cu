@@ -467,10 +467,9 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     P->cells = cells;
 
     // ---- work items: tiles of TB bins
-    // bins per work item: one resident wave of blocks (one block per SM at this register
-    // budget) for a single atmosphere, capped for long batches so the tail stays short
-    // block: one warp per Gauss point
-    // (one warp per Gauss point, or per two with 16-lane columns)
+    // bins per work item: one resident wave of blocks (at the sweep occupancy of the widest
+    // atmosphere) for a single atmosphere, capped for long batches so the tail stays short.
+    // Block: one warp per Gauss point, or per two with 16-lane columns
     auto block_threads = [G](int cl) { return cl == 16 ? 32 * ((G + 1) / 2) : 32 * G; };
     int amax = 0;
     for (int a = 0; a < A; ++a)
