@@ -252,6 +252,12 @@ __device__ __forceinline__ float planck_ff(const BinConst& b, float2 it, float& 
     return __fdividef(b.E, em);
 }
 
+// a hint to bring the line holding p into L2 (generic address; no effect on results)
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.L2 [%0];" ::"l"(p));
+}
+
 // ---------------------------------------------------------------------------
 // Programmatic dependent launch.  The kernels of one evaluation (prep, sweep, finalize, post)
 // may be launched to start while their predecessor in the stream is still running: each one
@@ -577,6 +583,28 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     float* wbase = P.warm + ad.warm_off;
 
     for (int l = l_begin; l < l_end; ++l) {
+        // the next bin's inputs move into L2 while this bin is processed: its constants, the
+        // table rows at every point's four corners (first and last element of each) and, with a
+        // warm start, its columns' upward deviations (one contiguous block of G W floats)
+        if (l + 1 < l_end) {
+            if (tid == 0) prefetch_l2(P.bins + ad.bin_off + l + 1);
+            if (ad.n_spec <= 1) {
+                const int lg1 = (l + 1) * G;
+                for (int p = tid; p < NP; p += nthreads) {
+                    const float* r = tab + P.row[ad.pt_off + p] + lg1;
+                    const float* c[4] = {r, r + td.offP, r + td.offT, r + td.offP + td.offT};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        prefetch_l2(c[j]);
+                        prefetch_l2(c[j] + G - 1);
+                    }
+                }
+            }
+            if (!DIRECT && warm_valid) {
+                const float* wn = wbase + (long long)(l + 1) * G * W;
+                for (int i = tid * 32; i < G * W; i += nthreads * 32) prefetch_l2(wn + i);
+            }
+        }
         const BinConst bc = P.bins[ad.bin_off + l];
         const bool emits = !(bc.flags & (BIN_GREY_DARK | BIN_PURE_SCAT | BIN_GREY_THERM));
         // ---- phase 1: per-point Planck values, per-sublayer Planck differences.  Each warp
