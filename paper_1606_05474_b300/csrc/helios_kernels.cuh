@@ -722,25 +722,28 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             direct_column<M>(Ts, Rs, Es, Ss, U, Dn, toa_g, bc.bint, lane);
             float* red_dn = kap + g * KST + lane * M;
             float* red_up = upr + g * KST + lane * M;
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-                red_dn[k] = wg * Dn[k];
-                red_up[k] = wg * U[k];
-            }
-            // the warm start of later iterated passes, in their layout: point p at slot
-            // (p mod M') CL' + p / M' of the column's CL' M' slots
+            // the warm start of later iterated passes, in their layout (CL' lanes per column, lane
+            // chunk M'; point p at slot (p mod M') CL' + p / M').  At 32 lanes that is this warp's
+            // own layout.  At 16 the column goes through the warp's shared-memory row first, so
+            // that consecutive lanes write consecutive slots
             if (ad.cl == 32) {
                 const long long col = (long long)(l * G + g) * W;
 #pragma unroll
                 for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = U[k];
             } else {
-                const int wm = ad.M, wl = ad.cl;
-                const long long col = (long long)(l * G + g) * (wl * wm);
+                const int wm = ad.M;
+                const long long col = (long long)(l * G + g) * (16 * wm);
 #pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const int p = lane * M + k;
-                    if (p < wl * wm) wbase[col + (p % wm) * wl + p / wm] = U[k];
-                }
+                for (int k = 0; k < M; ++k) red_up[k] = U[k];
+                __syncwarp();
+                const float* row = upr + g * KST;
+                for (int i = lane; i < 16 * wm; i += 32) wbase[col + i] = row[(i & 15) * wm + (i >> 4)];
+                __syncwarp();
+            }
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                red_dn[k] = wg * Dn[k];
+                red_up[k] = wg * U[k];
             }
         } else {
             float Ts[M], Rs[M], Ss[M], X[M + 1];
