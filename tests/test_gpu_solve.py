@@ -257,3 +257,25 @@ def test_measured_peaks_are_plausible():
     f, u = hp.measure_peaks(ctx())
     assert 20.0 < f < 100.0, f
     assert 1.0 < u < 12.0, u
+
+
+def test_dependent_launches_give_the_same_step_bitwise():
+    # the kernels of an evaluation launch as programmatic dependents of one another unless the
+    # sweep-timing events are on; both ways the step must be the same, bit for bit
+    import torch
+    wl = synth.small_scattering(L=24, n=60)
+    T0 = synth.perturbed_profile(wl.atms[0], 4)
+    res = []
+    for timing in (0, 4):
+        plan = make_plan(wl)
+        plan.set_timing(timing)
+        T = pack([T0])
+        st = plan.new_state()
+        Fu = torch.empty(plan.info.interfaces, dtype=torch.float64, device="cuda"); Fd = torch.empty_like(Fu)
+        for k in range(3):
+            plan.re_step(T, st, warm=k > 0, out=(Fu, Fd))
+        Fs, Gs, toa = plan.flux_sweep(T, warm=True)
+        torch.cuda.synchronize()
+        res.append([x.cpu().numpy().copy() for x in (T, Fu, Fd, Fs, Gs, toa, st["mult"], st["metric"])])
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
