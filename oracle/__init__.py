@@ -63,7 +63,8 @@ class RefParams(ctypes.Structure):
                 ("tol", ctypes.c_double), ("fpre_num", ctypes.c_double), ("fpre_exp", ctypes.c_double),
                 ("osc_down", ctypes.c_double), ("osc_up", ctypes.c_double), ("mult_max", ctypes.c_double),
                 ("T_floor", ctypes.c_double), ("mbar_mp", ctypes.c_double), ("n_dof", ctypes.c_double),
-                ("n_scat", ctypes.c_int), ("max_iter", ctypes.c_int), ("printed_gradient", ctypes.c_int)]
+                ("n_scat", ctypes.c_int), ("max_iter", ctypes.c_int), ("printed_gradient", ctypes.c_int),
+                ("tabulate", ctypes.c_int)]
 
 
 def _load():
@@ -77,6 +78,8 @@ def _load():
     lib.ref_default_params.argtypes = [P(RefParams)]
     lib.ref_E1.restype = d; lib.ref_E1.argtypes = [d]
     lib.ref_trans_exact.restype = d; lib.ref_trans_exact.argtypes = [d]
+    lib.ref_tab_one_minus_trans.restype = d; lib.ref_tab_one_minus_trans.argtypes = [d]
+    lib.ref_tab_planck_bin.restype = d; lib.ref_tab_planck_bin.argtypes = [d, d, d]
     lib.ref_diffusivity_exact.restype = d; lib.ref_diffusivity_exact.argtypes = [d]
     lib.ref_gauss_legendre.argtypes = [i, vp, vp]
     lib.ref_planck_bin.restype = d; lib.ref_planck_bin.argtypes = [d, d, d]
@@ -171,6 +174,20 @@ def E1(x: float) -> float:
 
 def trans_exact(x: float) -> float:
     return _load().ref_trans_exact(x)
+
+
+# the tables of Sect. 2.6 (ref_params.tabulate): nodes of 1 - e^-x and of the Planck function
+TAB_X0, TAB_NX, TAB_DT, TAB_NT = -8.05, 102, 10.0, 601
+
+
+def tab_one_minus_trans(x: float) -> float:
+    """1 - e^-x from the table of Sect. 2.6 (linear in x between 0.1-dex nodes)."""
+    return _load().ref_tab_one_minus_trans(x)
+
+
+def tab_planck_bin(nu_lo: float, nu_hi: float, T: float) -> float:
+    """The Planck intensity of a bin from the table of Sect. 2.6 (linear in T between 10 K nodes)."""
+    return _load().ref_tab_planck_bin(nu_lo, nu_hi, T)
 
 
 def diffusivity_exact(x: float) -> float:

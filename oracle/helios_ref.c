@@ -53,6 +53,7 @@ void ref_default_params(ref_params* p)
     p->n_scat = 4;
     p->max_iter = 20000;
     p->printed_gradient = 0;
+    p->tabulate = 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -309,6 +310,37 @@ static double bin_planck(const ref_atm* a, int l, double T)
     return ref_planck_bin(a->nu_edges[l], a->nu_edges[l + 1], T);
 }
 
+/* Sect. 2.6: "tabulate the Planck and the transmission functions" on a grid in T (10 K) and in
+ * opacity (0.1 in log10).  Reading: the transmission of a layer is e^-x with x = lambda dtau
+ * proportional to the layer's opacity, so a 0.1-dex grid in opacity is a 0.1-dex grid in x and
+ * one table of x serves every layer and bin.  The table holds 1 - e^-x (exact where the layer
+ * is thin) at the nodes x_i; between nodes it is linear in x. */
+static double tab_node_x(int i) { return pow(10.0, REF_TAB_X0 + 0.1 * i); }
+
+double ref_tab_one_minus_trans(double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    const int i = (int)floor((log10(x) - REF_TAB_X0) * 10.0);
+    if (i < 0) return x;                       /* 1 - e^-x = x (1 + O(x)), x < 1e-8 */
+    if (i >= REF_TAB_NX - 1) return 1.0;       /* e^-x < 1e-48 */
+    const double x0 = tab_node_x(i), x1 = tab_node_x(i + 1);
+    const double u0 = -expm1(-x0), u1 = -expm1(-x1);
+    return u0 + (x - x0) / (x1 - x0) * (u1 - u0);
+}
+
+/* the Planck intensity of a bin, linear in T between the 10 K nodes (end nodes beyond) */
+double ref_tab_planck_bin(double nu_lo, double nu_hi, double T)
+{
+    int j = (int)floor(T / REF_TAB_DT);
+    if (j < 0) j = 0;
+    if (j > REF_TAB_NT - 2) j = REF_TAB_NT - 2;
+    double w = T / REF_TAB_DT - j;
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    const double b0 = ref_planck_bin(nu_lo, nu_hi, j * REF_TAB_DT);
+    const double b1 = ref_planck_bin(nu_lo, nu_hi, (j + 1) * REF_TAB_DT);
+    return b0 + w * (b1 - b0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Two-stream fluxes across one (sub)layer, Sect. 2.1.3, with eps = 1/D.
  * Inputs: upward flux entering from below (F1up), downward flux entering from
@@ -342,7 +374,8 @@ void ref_layer_twostream(double F1up, double F2dn, double B1, double B2, double 
         *F1dn = F2dn + x;
         return;
     }
-    double trans = exp(-D * sqrt((1.0 - w0 * g0) * (1.0 - w0)) * dtau);        /* eq. (8) */
+    const double x = D * sqrt((1.0 - w0 * g0) * (1.0 - w0)) * dtau;
+    double trans = p->tabulate ? 1.0 - ref_tab_one_minus_trans(x) : exp(-x);    /* eq. (8) */
     double r = sqrt((1.0 - w0) / (1.0 - w0 * g0));
     double zp = 0.5 * (1.0 + r), zm = 0.5 * (1.0 - r);                          /* eq. (13) */
     double alpha = zm * zm * trans * trans - zp * zp;                           /* eq. (12) */
@@ -457,7 +490,9 @@ int ref_flux_sweep(const ref_atm* a, const ref_params* p, const double* T, int n
         const double g0 = a->g0[l];
         const double kR = a->rayleigh ? ref_rayleigh_kappa(a->nu_edges[l], a->nu_edges[l + 1], p->mbar_mp) : 0.0;
         double* w0s = (double*)malloc(sizeof(double) * (np - 1));
-        for (int q = 0; q < np; ++q) B[q] = bin_planck(a, l, Tp[q]);
+        for (int q = 0; q < np; ++q)
+            B[q] = (p->tabulate && !a->grey) ? ref_tab_planck_bin(a->nu_edges[l], a->nu_edges[l + 1], Tp[q])
+                                             : bin_planck(a, l, Tp[q]);
         if (Fup_spec) memset(Fup_spec + (size_t)l * np, 0, sizeof(double) * np);
         if (Fdn_spec) memset(Fdn_spec + (size_t)l * np, 0, sizeof(double) * np);
         if (Fup_toa) Fup_toa[l] = 0.0;

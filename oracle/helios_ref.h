@@ -64,11 +64,23 @@ typedef struct {
     int n_scat;               /* additional scattering passes per temperature step (4) */
     int max_iter;             /* radiative-equilibrium iteration cap */
     int printed_gradient;     /* 1: use the gradient prefactor eps/(1+w0 g0) as printed */
+    int tabulate;             /* 1: Planck and transmission functions from tables (Sect. 2.6) */
 } ref_params;
 
 enum { REF_CONVERGED = 0, REF_UPDATED = 1, REF_NOT_CONVERGED = 2, REF_NONFINITE = 3 };
 
 void   ref_default_params(ref_params* p);
+
+/* Tabulated functions of Sect. 2.6 (used by ref_flux_sweep when p->tabulate):
+ * 1 - trans(x) on the nodes x_i = 10^(REF_TAB_X0 + 0.1 i), i < REF_TAB_NX, linear in x between
+ * nodes (x below the first node: x itself; above the last: 1); the Planck intensity of bin l on
+ * the nodes T_j = j REF_TAB_DT, j < REF_TAB_NT, linear in T (clamped to the end nodes). */
+#define REF_TAB_X0 (-8.05)
+#define REF_TAB_NX 102
+#define REF_TAB_DT 10.0
+#define REF_TAB_NT 601
+double ref_tab_one_minus_trans(double x);
+double ref_tab_planck_bin(double nu_lo, double nu_hi, double T);
 
 /* special functions and quadrature */
 double ref_E1(double x);
