@@ -296,7 +296,12 @@ def run_gpu(args):
         torch.cuda.synchronize()
         dt_d = time.time() - t0
         pp = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(iso_layers=1))
+        # Sect. 2.6: the same 1 + 4 passes with the tabulated Planck and transmission functions
+        pt = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(tabulate=1))
+        ms_tab = time_sweeps(pt, Tc, n_passes)
+        del pt
         direct = {"sweep_ms_exact": ms_dir, "sweep_ms_passes": ms_pass, "passes": n_passes,
+                  "sweep_ms_passes_tabulated_functions": ms_tab,
                   "re_solve_exact": {"wall_s": round(dt_d, 4), "iters": int(it_d.item()), "status": int(st_d.item()),
                                      "max_dT_vs_passes_K": round(float((Td - Ts).abs().max()), 4)},
                   "post_processing_spectrum_ms": {"isothermal_layers_81_passes": time_sweeps(pp, Tc, 81),

@@ -155,6 +155,12 @@ typedef struct {
                             layers, others are rejected), or 0: 16 where an atmosphere has 24 to 119
                             layers, else 32.  Results agree to rounding; the exact column solve
                             always runs 32 lanes per column */
+    int tabulate;        /* 1: the Planck and transmission functions come from tables (Sect. 2.6):
+                            each bin's Planck flux at 10 K nodes, linear in T between them, and
+                            1 - e^-x of the layer exponent x = lambda dtau at nodes 0.1 apart in
+                            log10 x, linear in x between them (x below 10^-8.05, 1 above 10^2.05).
+                            Not with iso_layers, direct, rayleigh or grey_mode, nor with
+                            n_passes = HELIOS_DIRECT; holds bins x 601 floats of device memory */
 } helios_params_t;
 
 void helios_default_params(helios_params_t* p);

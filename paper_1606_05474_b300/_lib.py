@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
                 ("mult_max", c_double), ("T_floor", c_double), ("n_scat", c_int), ("max_iter", c_int),
                 ("grey_mode", c_int), ("printed_gradient", c_int), ("bins_per_item", c_int),
                 ("check_every", c_int), ("persistent", c_int), ("iso_layers", c_int), ("device_loop", c_int), ("direct", c_int), ("rayleigh", c_int),
-                ("col_lanes", c_int)]
+                ("col_lanes", c_int), ("tabulate", c_int)]
 
 
 class PlanInfo(ctypes.Structure):

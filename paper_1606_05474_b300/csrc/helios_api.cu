@@ -296,6 +296,7 @@ void helios_default_params(helios_params_t* p)
     p->direct = 0;
     p->rayleigh = 0;
     p->col_lanes = 0;
+    p->tabulate = 0;
 }
 
 int helios_version(void) { return HELIOS_VERSION; }
@@ -367,8 +368,11 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         prm->persistent < 0 || prm->persistent > 1 || prm->iso_layers < 0 || prm->iso_layers > 1 ||
         prm->device_loop < 0 || prm->device_loop > 1 || prm->direct < 0 || prm->direct > 1 ||
         prm->rayleigh < 0 || prm->rayleigh > 1 || (prm->rayleigh && prm->grey_mode) ||
-        (prm->col_lanes != 0 && prm->col_lanes != 16 && prm->col_lanes != 32))
+        (prm->col_lanes != 0 && prm->col_lanes != 16 && prm->col_lanes != 32) || prm->tabulate < 0 ||
+        prm->tabulate > 1)
         return fail(HELIOS_EINVAL, "invalid parameter set");
+    if (prm->tabulate && (prm->iso_layers || prm->direct || prm->rayleigh || prm->grey_mode))
+        return fail(HELIOS_EINVAL, "tabulated functions: not with iso_layers, direct, rayleigh or grey_mode");
     const int G = tabs[0].G;
     if (G < 1 || G > kMaxG) return fail(HELIOS_EINVAL, "G = %d outside [1, %d]", G, kMaxG);
     for (int t = 0; t < ntab; ++t) {
@@ -543,6 +547,22 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     // ---- per-bin constants (eqs. 8, 12-14, 20-22), double precision then rounded
     const double D = prm->D, eps = 1.0 / D;
     std::vector<BinConst> bc(bins);
+    // Sect. 2.6 tables: 2 pi eps B of every bin at the 10 K nodes (the same quantity the sweep
+    // otherwise forms as E / (e^x - 1)), and 1 - e^-x at the 0.1-dex nodes of x
+    std::vector<float> btab, utab;
+    if (prm->tabulate) {
+        if (bins * (int64_t)kTabNT > ((int64_t)1 << 30)) {
+            delete P;
+            return fail(HELIOS_EINVAL, "tabulated Planck functions: %lld bins are too many", (long long)bins);
+        }
+        btab.resize((size_t)bins * kTabNT);
+        utab.resize(2 * kTabNX);
+        for (int i = 0; i < kTabNX; ++i) {
+            const double x = std::pow(10.0, (double)kTabX0 + 0.1 * i);
+            utab[i] = (float)x;
+            utab[kTabNX + i] = (float)(-std::expm1(-x));
+        }
+    }
     bool any_scat = false;
     nu_off = 0;
     for (int a = 0; a < A; ++a) {
@@ -562,6 +582,9 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
             c.xs = (float)xs;
             c.xs_lo = (float)(xs - (double)c.xs);
             c.E = (float)(2.0 * kPi * eps * 2.0 * hP * cL * cL * nu * nu * nu * dnu);
+            if (prm->tabulate)
+                for (int j = 0; j < kTabNT; ++j)
+                    btab[(size_t)(d.bin_off + l) * kTabNT + j] = (float)(2.0 * kPi * eps * planck_bin(e[l], e[l + 1], j * (double)kTabDT));
             double toa = (s_star > 0.0 && Firr > 0.0) ? Firr * planck_bin(e[l], e[l + 1], b->T_star[a]) / s_star : 0.0;
             double bint = (s_int > 0.0 && Fint > 0.0) ? Fint * planck_bin(e[l], e[l + 1], b->T_int[a]) / s_int : 0.0;
             if (prm->grey_mode) {
@@ -660,6 +683,11 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     ALLOC(P->Fup, ifc); ALLOC(P->Fdn, ifc); ALLOC(P->mult, lay); ALLOC(P->hist, lay); ALLOC(P->nhist, lay);
     ALLOC(P->n_active, 1); ALLOC(P->chunks_left, 1);
     ALLOC(P->counters, 2 * kGroups);
+    float *d_btab = nullptr, *d_utab = nullptr;
+    if (prm->tabulate) {
+        ALLOC(d_btab, btab.size());
+        ALLOC(d_utab, utab.size());
+    }
 #undef ALLOC
     std::vector<int> order;
     int nsm_all = 148;
@@ -699,7 +727,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     if ((rc = upload(d_atm, ad)) || (rc = upload(d_tab, td)) || (rc = upload(d_bc, bc)) ||
         (rc = upload(d_items, items)) || (rc = upload(d_order, order)) || (rc = upload(d_gw, gw)) ||
         (rc = upload(d_iP, iP)) || (rc = upload(d_wP, wP)) || (rc = upload(d_dm, dm)) || (rc = upload(d_lnr, lnr)) ||
-        (rc = upload(d_lay_atm, lay_atm)) || (rc = upload(d_spec_tab, spec_tab)) || (rc = upload(d_spec_w, spec_w))) {
+        (rc = upload(d_lay_atm, lay_atm)) || (rc = upload(d_spec_tab, spec_tab)) || (rc = upload(d_spec_w, spec_w)) ||
+        (prm->tabulate && ((rc = upload(d_btab, btab)) || (rc = upload(d_utab, utab))))) {
         helios_plan_destroy(P);
         return rc;
     }
@@ -709,6 +738,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     dv.atms = d_atm; dv.tabs = d_tab; dv.bins = d_bc; dv.items = d_items; dv.gw = d_gw;
     dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
     dv.spec_tab = d_spec_tab; dv.spec_w = d_spec_w;
+    dv.btab = d_btab; dv.utab = d_utab;
     dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso; dv.iso_layers = prm->iso_layers;
     dv.D = (float)prm->D; dv.eps = (float)(1.0 / prm->D); dv.w0_pure = (float)prm->w0_pure;
     dv.printed_gradient = prm->printed_gradient;
@@ -988,6 +1018,8 @@ int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int w
 {
     if (!p || !T_layer || !Fup_bol || !Fdn_bol) return fail(HELIOS_EINVAL, "helios_flux_sweep: null argument");
     if (n_passes < HELIOS_DIRECT) return fail(HELIOS_EINVAL, "helios_flux_sweep: n_passes = %d", n_passes);
+    if (n_passes == HELIOS_DIRECT && p->prm.tabulate)
+        return fail(HELIOS_EINVAL, "helios_flux_sweep: the exact column solve has no tabulated form");
     if (n_passes == 0) n_passes = p->passes;
     CUDA_TRY(cudaSetDevice(p->ctx->device));
     const int warm_valid = (warm && p->warm_ready) ? 1 : 0;

@@ -115,7 +115,17 @@ struct PlanDev {
     float D, eps, w0_pure;      // per-sublayer two-stream constants (Rayleigh scattering)
     int printed_gradient;
     int iso_layers;             // 1: isothermal-layer grid (both points of layer i at T_i)
+    // tables of Sect. 2.6 (null: the functions themselves): 1 - e^-x at the nodes
+    // x_i = 10^(kTabX0 + 0.1 i) ([0, kTabNX): x_i, [kTabNX, 2 kTabNX): 1 - e^-x_i), and each bin's
+    // 2 pi eps B_l at the nodes T_j = j kTabDT ([bins][kTabNT])
+    const float* utab;
+    const float* btab;
 };
+
+constexpr float kTabX0 = -8.05f;
+constexpr int kTabNX = 102;
+constexpr float kTabDT = 10.0f;
+constexpr int kTabNT = 601;
 
 // ---------------------------------------------------------------------------
 // Table coordinate in IEEE double without contraction (Sect. 2.3 and footnote):
@@ -220,6 +230,35 @@ __global__ void recip_kernel(const float* __restrict__ x, float* __restrict__ y,
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = recip_nr(x[i]);
+}
+
+// phi, u = 1 - e^{-x} and t = e^{-x} with u from the table of Sect. 2.6: linear in x between the
+// 0.1-dex nodes, x itself below the first node, 1 above the last; phi = u / x
+__device__ __forceinline__ void phi_u_t_tab(float x, const float* __restrict__ utab, float& phi, float& u, float& t)
+{
+    const float f = (__log10f(fmaxf(x, 1e-30f)) - kTabX0) * 10.0f;
+    const int i = (int)floorf(f);
+    if (i < 0) {
+        u = x;
+    } else if (i >= kTabNX - 1) {
+        u = 1.0f;
+    } else {
+        const float x0 = __ldg(utab + i), x1 = __ldg(utab + i + 1);
+        const float u0 = __ldg(utab + kTabNX + i), u1 = __ldg(utab + kTabNX + i + 1);
+        u = fmaf(__fdividef(x - x0, x1 - x0), u1 - u0, u0);
+    }
+    t = 1.0f - u;
+    phi = x > 0.0f ? __fdividef(u, x) : 1.0f;
+}
+
+// 2 pi eps B of a bin at temperature T from its 10 K table (linear in T, end nodes beyond)
+__device__ __forceinline__ float planck_tab(const float* __restrict__ row, float T)
+{
+    const float f = T * (1.0f / kTabDT);
+    const int j = min(max((int)floorf(f), 0), kTabNT - 2);
+    const float w = fminf(fmaxf(f - (float)j, 0.0f), 1.0f);
+    const float b0 = __ldg(row + j), b1 = __ldg(row + j + 1);
+    return fmaf(w, b1 - b0, b0);
 }
 
 // a + b for float-float values (hi, lo): Knuth's error-free two-sum of the high parts plus the
@@ -355,9 +394,10 @@ __device__ __forceinline__ BinConst rayleigh_const(const BinConst& b, const Plan
 // With WANT_E the absorption Es = 1 - Ts - Rs of the sublayer is returned too, formed without
 // cancellation: expanding eqs. (12)-(13), 1 - Ts - Rs = (1 - q)(1 - trans)(1 - q trans) d
 // (zero for pure scattering); omq = 1 - q of the bin.
-template <bool WANT_E = false>
+template <bool WANT_E = false, bool TAB = false>
 __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
-                                           float& Ts, float& Rs, float& Ss, float* Es = nullptr, float omq = 0.0f)
+                                           float& Ts, float& Rs, float& Ss, float* Es = nullptr, float omq = 0.0f,
+                                           const float* utab = nullptr)
 {
     if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source
         const float a = b.gam * dtau;
@@ -372,7 +412,8 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
         return;
     }
     float phi, u, tr;
-    phi_u_t(b.lam * dtau, phi, u, tr);      // eq. (8): tr = exp(-lam dtau), u = 1 - tr
+    if constexpr (TAB) phi_u_t_tab(b.lam * dtau, utab, phi, u, tr);     // Sect. 2.6 table
+    else phi_u_t(b.lam * dtau, phi, u, tr); // eq. (8): tr = exp(-lam dtau), u = 1 - tr
     const bool iso = dtau < dtau_iso;       // Sect. 2.2.1: thin sublayers use eq. (11)
     if (b.flags & BIN_NO_SCAT) {            // zeta_- = 0: Ts = trans, Rs = 0
         Ts = tr;
@@ -628,6 +669,11 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     const float Tb = P.Tf[q + 1];
                     d = c * P.dT_sub[ad.sub_off + p] * (T + Tb) * (T2 + Tb * Tb);
                 }
+            } else if (pt && emits && P.btab) {
+                const float* row = P.btab + (long long)(ad.bin_off + l) * kTabNT;
+                const float T = P.Tf[q];
+                B = planck_tab(row, T);
+                if (warm_valid) sh = planck_tab(row, T + P.dT_step[q]) - B;
             } else if (pt && emits) {
                 B = planck_ff(bc, P.invT[q], x);
                 if (warm_valid) {
@@ -641,9 +687,13 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             const float Bb = __shfl_down_sync(FULL, B, 1);          // B of point p + 1
             if (lane < 31 && p < W) {
                 if (pt && emits && p < NS) {
-                    // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
-                    const float y = bc.xs * P.dinv_sub[ad.sub_off + p];
-                    d = fabsf(y) < 1.0f ? Bb * __fdividef(em1(y), -em1(-x)) : B - Bb;
+                    if (P.btab) {
+                        d = B - Bb;                                 // tabulated values
+                    } else {
+                        // B_a - B_b = B_b (e^y - 1) / (1 - e^{-x_a}), y = x_b - x_a
+                        const float y = bc.xs * P.dinv_sub[ad.sub_off + p];
+                        d = fabsf(y) < 1.0f ? Bb * __fdividef(em1(y), -em1(-x)) : B - Bb;
+                    }
                 }
                 if (p == NP - 1) bc_toa[0] = bc.toa - B;
                 bt[p] = B;
@@ -758,6 +808,20 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                         float kt;
                         const BinConst c = rayleigh_const(bc, P, 0.5f * (krow[s] + krow[s + 1]), kt);
                         layer_coef(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src);
+                    }
+                    Ts[k] = t;
+                    Rs[k] = r;
+                    Ss[k] = src;
+                    Ap *= t;
+                }
+            } else if (P.utab) {                                                // uniform per launch
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int s = sub * M + k;
+                    float t = 1.0f, r = 0.0f, src = 0.0f;
+                    if (s < NS) {
+                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                        layer_coef<false, true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, nullptr, 0.0f, P.utab);
                     }
                     Ts[k] = t;
                     Rs[k] = r;

@@ -282,6 +282,7 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     if (n_passes < 0) return err(HELIOS_EINVAL, "n_passes = %d (the direct column solve needs a plan)", n_passes);
     if (prm->direct) return err(HELIOS_EINVAL, "the direct column solve needs a plan");
     if (prm->rayleigh) return err(HELIOS_EINVAL, "Rayleigh scattering needs a plan");
+    if (prm->tabulate) return err(HELIOS_EINVAL, "tabulated functions need a plan");
     if (n_passes == 0) n_passes = any_scat ? 1 + prm->n_scat : 1;
     for (int t = 0; t < items; ++t) { h_items[t] = make_int2(0, t); h_order[t] = t; }
     gauss_weights(G, h_gw);
