@@ -130,7 +130,7 @@ class ClockSampler:
 # DRAM traffic (read + write) of one sweep-kernel launch on the full-size single atmosphere, from
 # the ncu capture summarised in profiles/sweep_kernel_full_single_atmosphere.md, valid only for the
 # kernel source it was taken on (sha256 prefix of csrc/helios_kernels.cuh); null otherwise.
-SWEEP_TRAFFIC = {"kernels_sha256": "390349afbdbeda4d", "bytes_per_launch": 62976512}
+SWEEP_TRAFFIC = {"kernels_sha256": "abf436c89c4d6f59", "bytes_per_launch": 63123200}
 
 
 def kernel_source_hash():
