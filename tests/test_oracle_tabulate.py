@@ -9,7 +9,8 @@ proportional to the opacity).
   two neighbouring nodes halfway between them;
 - an isothermal cavity at a node temperature stays at pi B with the tabulated transmission
   (Kirchhoff's law holds for any transmission value);
-- tabulated fluxes stay within 1% of the exact ones on a scattering column, and differ from them.
+- tabulated fluxes stay within 1% of the exact ones on a scattering column, and differ from them;
+- the tabulated radiative equilibrium lies within 0.2 K of the exact one.
 """
 import math
 
@@ -66,3 +67,18 @@ def test_tabulated_fluxes_close_to_exact():
     for k in ("Fup", "Fdn"):
         d = np.max(np.abs(tb[k] / ex[k] - 1))
         assert 1e-6 < d < 1e-2, (k, d)
+
+
+def test_tabulated_equilibrium_close_to_the_exact_one():
+    # Sect. 2.6: the grid resolutions suffice for a converged model; here the tabulated
+    # equilibrium of a 40-layer scattering column lies within 0.2 K of the exact one (0.06 K seen)
+    wl = synth.small_scattering(L=30, n=40)
+    atm = oracle.Atm.from_workload(wl)
+    Ts = []
+    for tab in (0, 1):
+        st = oracle.State(atm, wl.atms[0].T_init)
+        rc, _, _ = oracle.solve_re(atm, st, oracle.params(tabulate=tab, tol=1e-10, max_iter=200000))
+        assert rc == oracle.CONVERGED
+        Ts.append(st.T.copy())
+    d = np.abs(Ts[1] - Ts[0])
+    assert 1e-4 < d.max() < 0.2, d.max()
