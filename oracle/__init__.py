@@ -16,7 +16,11 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   column sweeps                pinned: isothermal cavity / semi-infinite closed forms,
                                conservative scattering, exact-vs-D=2 refinement
   temperature step             pinned: converged net flux = sigma T_int^4; grey two-band profile
-  oscillation control          parity unpinned (a heuristic; only its fixed point is pinned)
+  oscillation control          pinned: hand-made sign sequences with the multipliers written out
+                               from the rule of Sect. 2.2.4 (monotonic, alternating, period-4,
+                               cap, no change before six signs)
+  RE trajectory                parity unpinned (the path of a heuristic iteration; its fixed point
+                               is pinned)
 """
 from __future__ import annotations
 

@@ -9,14 +9,15 @@
  *
  * Each function states the passage of the paper it restates.  Where the paper
  * is silent, ambiguous or garbled, the reading taken is stated beside the code
- * (and listed with its justification in the design notes).
+ * with its justification.
  *
  * Parity pins: every function here is checked, in tests/test_oracle_*.py,
  * against something other than itself (library special functions, numerical
  * solution of the two-stream ODE, closed forms, invariants).  The
- * temperature-step oscillation rule (Sect. 2.2.4) is a heuristic with no
- * independent pin: "parity unpinned" for the trajectory; only its fixed point
- * is pinned (net flux equals sigma*T_int^4 at convergence).
+ * temperature-step oscillation rule (Sect. 2.2.4) is pinned against hand-made
+ * sign sequences; the trajectory of the whole iteration is "parity unpinned"
+ * (only its fixed point is pinned: net flux equals sigma*T_int^4 at
+ * convergence).
  */
 #include "helios_ref.h"
 
