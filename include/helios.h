@@ -188,13 +188,17 @@ int helios_plan_destroy(helios_plan* plan);
  * HELIOS_DIRECT with params.direct); bytes of workspace held; the sweep launches
  * per evaluation (one per group of atmospheres with the same lane chunk); whether
  * the bolometric sums join the temperature-step kernel (1) or run as their own
- * launch (0: an atmosphere with many work items). */
+ * launch (0: an atmosphere with many work items); the sizes, in floats, of a
+ * caller-owned warm-start buffer and of the per-bin flux output of
+ * helios_flux_sweep. */
 typedef struct {
     int64_t layers, interfaces, points, bins, cells;
     int passes;
     int64_t workspace_bytes;
     int sweep_launches;
     int fused_finalize;
+    int64_t warm_floats;    /* floats of a warm-start buffer (helios_flux_sweep's Fup_warm) */
+    int64_t spec_floats;    /* floats of the per-bin flux output (helios_flux_sweep's F_spec) */
 } helios_plan_info_t;
 int helios_plan_info(const helios_plan* plan, helios_plan_info_t* info);
 
@@ -232,11 +236,25 @@ int helios_interp_opacity(helios_plan* plan, const double* T_layer, float* kappa
  *   warm     0: the coupled stream starts from zero (first temperature step);
  *            1: it starts from the upward fluxes of this plan's previous
  *               evaluation (later temperature steps, Sect. 2.2.3)
+ *   Fup_warm device, float [warm_floats of helios_plan_info], 16-byte aligned, or
+ *            NULL: the warm-start buffer (in/out; the upward fluxes of every
+ *            column, as deviations from the local Planck flux, in the library's
+ *            lane-interleaved layout).  NULL: the plan's own buffer.  Given, it
+ *            replaces the plan's buffer for this call: with warm = 1 it must hold
+ *            what an evaluation of this plan wrote into it, and the evaluation
+ *            before this one must have been made at the temperatures that buffer
+ *            was written at (the shift to the new temperatures uses the plan's
+ *            record of the previous evaluation's point temperatures)
  *   Fup_bol, Fdn_bol  device, double [interfaces]: bolometric fluxes
  *   Fup_toa  device, float [bins]: emergent TOA spectrum per bin (may be NULL)
+ *   F_spec   device, float [spec_floats of helios_plan_info] or NULL: a debug
+ *            output of every bin's Gauss-point-summed fluxes at every point,
+ *            packed per atmosphere as [L][2][2n+1] (upward at points 0..2n,
+ *            then downward), atmosphere a starting at
+ *            sum_{b<a} 2 L_b (2 n_b + 1)
  * Results are deterministic (fixed-order reductions). */
-int helios_flux_sweep(helios_plan* plan, const double* T_layer, int n_passes, int warm, double* Fup_bol,
-                      double* Fdn_bol, float* Fup_toa, cudaStream_t stream);
+int helios_flux_sweep(helios_plan* plan, const double* T_layer, int n_passes, int warm, float* Fup_warm,
+                      double* Fup_bol, double* Fdn_bol, float* Fup_toa, float* F_spec, cudaStream_t stream);
 
 /* One temperature step (Sects. 2.2.3-2.2.4, eqs. 23-29) for every atmosphere
  * whose status is HELIOS_ATM_ACTIVE:

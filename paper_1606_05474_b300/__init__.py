@@ -245,16 +245,37 @@ class Plan:
                                              _stream_ptr(stream)))
         return kap, idx.view(-1, 2), w.view(-1, 2)
 
-    def flux_sweep(self, T, n_passes=0, warm=False, want_toa=True, out=None, stream=None):
+    def flux_sweep(self, T, n_passes=0, warm=False, want_toa=True, out=None, stream=None, warm_buf=None,
+                   spec=None):
+        """One flux evaluation (helios_flux_sweep); returns (Fup_bol, Fdn_bol, Fup_toa).
+        warm_buf: optional caller-owned float32 warm-start tensor of info.warm_floats values (the
+        plan's own buffer otherwise).  spec: optional float32 tensor of info.spec_floats values
+        that receives every bin's fluxes at every point (see split_spec)."""
         torch = _torch()
         self._check_T(T)
         if out is None:
             out = (self._empty(self.info.interfaces, torch.float64), self._empty(self.info.interfaces, torch.float64),
                    self._empty(self.info.bins, torch.float32) if want_toa else None)
         Fu, Fd, toa = out
-        check(self.lib.helios_flux_sweep(self.h, T.data_ptr(), int(n_passes), 1 if warm else 0, Fu.data_ptr(),
-                                         Fd.data_ptr(), _ptr(toa), _stream_ptr(stream)))
+        for buf, size, name in ((warm_buf, self.info.warm_floats, "warm_buf"), (spec, self.info.spec_floats, "spec")):
+            if buf is not None and not (buf.is_cuda and buf.dtype == torch.float32 and buf.is_contiguous()
+                                        and buf.numel() == size):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {size} values")
+        check(self.lib.helios_flux_sweep(self.h, T.data_ptr(), int(n_passes), 1 if warm else 0, _ptr(warm_buf),
+                                         Fu.data_ptr(), Fd.data_ptr(), _ptr(toa), _ptr(spec), _stream_ptr(stream)))
         return Fu, Fd, toa
+
+    def split_spec(self, spec):
+        """The per-bin flux output of flux_sweep as one (Fup [L, 2n+1], Fdn [L, 2n+1]) numpy pair
+        per atmosphere."""
+        v = spec.cpu().numpy() if hasattr(spec, "cpu") else np.asarray(spec)
+        out, off = [], 0
+        for n, L in zip(self.n, self.L):
+            np_ = 2 * int(n) + 1
+            blk = v[off:off + 2 * int(L) * np_].reshape(int(L), 2, np_)
+            out.append((blk[:, 0, :], blk[:, 1, :]))
+            off += 2 * int(L) * np_
+        return out
 
     def emission_spectrum(self, T, n_passes=81, stream=None):
         """Emergent spectrum of converged temperatures T (Sect. 3: computed as a post-processing

@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("layers", c_int64), ("interfaces", c_int64), ("points", c_int64), ("bins", c_int64),
                 ("cells", c_int64), ("passes", c_int), ("workspace_bytes", c_int64), ("sweep_launches", c_int),
-                ("fused_finalize", c_int)]
+                ("fused_finalize", c_int), ("warm_floats", c_int64), ("spec_floats", c_int64)]
 
 
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
@@ -73,7 +73,7 @@ def load(path: str = SO_PATH):
     lib.helios_plan_destroy.argtypes = [vp]
     lib.helios_plan_info.argtypes = [vp, P(PlanInfo)]
     lib.helios_interp_opacity.argtypes = [vp, vp, vp, vp, vp, vp]
-    lib.helios_flux_sweep.argtypes = [vp, vp, c_int, c_int, vp, vp, vp, vp]
+    lib.helios_flux_sweep.argtypes = [vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]
     lib.helios_temp_update.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_re_step.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_measure_peaks.argtypes = [vp, P(c_double), P(c_double)]

@@ -243,6 +243,8 @@ struct helios_plan {
     int A, G, TB, passes, max_n;
     int64_t layers, interfaces, points, subs, bins, items, cells;
     int64_t ws_bytes;
+    int64_t warm_floats;    // floats of the warm-start block (all atmospheres)
+    int64_t spec_floats;    // floats of the optional per-bin flux output [bins][2][points]
     std::vector<AtmDesc> atms_h;
     std::vector<MGroup> groups;
     PlanDev dev;
@@ -488,7 +490,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     }
     P->TB = TB;
     std::vector<int2> items;
-    int64_t part = 0, warm = 0;
+    int64_t part = 0, warm = 0, fspec = 0;
     for (int a = 0; a < A; ++a) {
         AtmDesc& d = ad[a];
         d.n_items = (d.L + TB - 1) / TB;
@@ -499,7 +501,11 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         part += (int64_t)d.n_items * 3 * (d.n + 1);
         d.warm_off = warm;
         warm += (int64_t)d.L * G * d.cl * d.M;
+        d.fspec_off = fspec;
+        fspec += (int64_t)d.L * 2 * (2 * d.n + 1);
     }
+    P->warm_floats = warm;
+    P->spec_floats = fspec;
     P->items = (int64_t)items.size();
     // launch order per group (lanes per column, lane chunk), most expensive items first
     std::vector<std::vector<int>> byM(kGroups);
@@ -810,6 +816,8 @@ int helios_plan_info(const helios_plan* p, helios_plan_info_t* info)
     info->workspace_bytes = p->ws_bytes;
     info->sweep_launches = (int)p->groups.size();
     info->fused_finalize = p->max_items <= kFuseFinalizeItems ? 1 : 0;
+    info->warm_floats = p->warm_floats;
+    info->spec_floats = p->spec_floats;
     return HELIOS_OK;
 }
 
@@ -861,9 +869,17 @@ int launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     return HELIOS_OK;
 }
 
+// optional outputs and buffers of one sweep launch: the emergent spectrum, the per-bin fluxes at
+// every point, and a caller-owned warm-start buffer in place of the plan's own
+struct SweepIO {
+    float* Fup_toa = nullptr;
+    float* F_spec = nullptr;
+    float* warm = nullptr;
+};
+
 template <int M, int MINB, bool DIRECT, int CL = 32>
 int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
-                    float* Fup_toa, cudaStream_t s)
+                    const SweepIO& io, cudaStream_t s)
 {
     const size_t smem = sweep_smem(M, p->G, CL);
     const int threads = DIRECT ? 32 * p->G : gr.threads;
@@ -875,28 +891,30 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
         conf = p->ctx->device + 1;
     }
     const bool pdl = use_pdl(p, s);
+    PlanDev dv = p->dev;
+    if (io.warm) dv.warm = io.warm;
     if (p->prm.persistent)
         return launch_k(pdl, sweep_kernel<M, MINB, DIRECT, CL>, dim3(DIRECT ? gr.grid_direct : gr.grid), dim3(threads),
-                        smem, s, p->dev, (const int*)gr.order, gr.count, gr.counter, status, n_passes, warm_valid,
-                        Fup_toa);
-    return launch_k(pdl, sweep_kernel<M, MINB, DIRECT, CL>, dim3(gr.count), dim3(threads), smem, s, p->dev,
-                    (const int*)gr.order, gr.count, (int*)nullptr, status, n_passes, warm_valid, Fup_toa);
+                        smem, s, dv, (const int*)gr.order, gr.count, gr.counter, status, n_passes, warm_valid,
+                        io.Fup_toa, io.F_spec);
+    return launch_k(pdl, sweep_kernel<M, MINB, DIRECT, CL>, dim3(gr.count), dim3(threads), smem, s, dv,
+                    (const int*)gr.order, gr.count, (int*)nullptr, status, n_passes, warm_valid, io.Fup_toa, io.F_spec);
 }
 
 template <int M>
 int launch_sweep_M(helios_plan* p, const MGroup& gr, const int* status, int n_passes, int warm_valid,
-                   float* Fup_toa, cudaStream_t s)
+                   const SweepIO& io, cudaStream_t s)
 {
     if constexpr (cl16_chunk(M)) {
         if (gr.cl == 16 && n_passes != HELIOS_DIRECT)
-            return launch_sweep_MB<M, minb16<M>(), false, 16>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+            return launch_sweep_MB<M, minb16<M>(), false, 16>(p, gr, status, n_passes, warm_valid, io, s);
     }
     if (n_passes == HELIOS_DIRECT)
-        return launch_sweep_MB<M, sweep_minb<M, true>(), true>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
-    return launch_sweep_MB<M, sweep_minb<M, false>(), false>(p, gr, status, n_passes, warm_valid, Fup_toa, s);
+        return launch_sweep_MB<M, sweep_minb<M, true>(), true>(p, gr, status, n_passes, warm_valid, io, s);
+    return launch_sweep_MB<M, sweep_minb<M, false>(), false>(p, gr, status, n_passes, warm_valid, io, s);
 }
 
-int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, float* Fup_toa, cudaStream_t s)
+int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid, const SweepIO& io, cudaStream_t s)
 {
     if (p->timing) {
         const size_t slot = (size_t)(p->n_timed % (int64_t)(p->ev_ring.size() / 2));
@@ -916,14 +934,14 @@ int launch_sweep(helios_plan* p, const int* status, int n_passes, int warm_valid
             CUDA_TRY(cudaStreamWaitEvent(gs, p->fork, 0));
         }
         switch (n_passes == HELIOS_DIRECT ? gr.M_direct : gr.M) {
-            case 1: rc = launch_sweep_M<1>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 3: rc = launch_sweep_M<3>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 5: rc = launch_sweep_M<5>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 7: rc = launch_sweep_M<7>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 9: rc = launch_sweep_M<9>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 11: rc = launch_sweep_M<11>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 13: rc = launch_sweep_M<13>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
-            case 15: rc = launch_sweep_M<15>(p, gr, status, n_passes, warm_valid, Fup_toa, gs); break;
+            case 1: rc = launch_sweep_M<1>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 3: rc = launch_sweep_M<3>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 5: rc = launch_sweep_M<5>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 7: rc = launch_sweep_M<7>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 9: rc = launch_sweep_M<9>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 11: rc = launch_sweep_M<11>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 13: rc = launch_sweep_M<13>(p, gr, status, n_passes, warm_valid, io, gs); break;
+            case 15: rc = launch_sweep_M<15>(p, gr, status, n_passes, warm_valid, io, gs); break;
             default: rc = fail(HELIOS_EINVAL, "unsupported lane chunk %d", gr.M);
         }
         if (rc) return rc;
@@ -942,11 +960,11 @@ int launch_prep(helios_plan* p, const double* T, const int* status, int warm_val
 }
 
 int launch_eval(helios_plan* p, const double* T, const int* status, int n_passes, int warm_valid, double* Fup,
-                double* Fdn, float* Fup_toa, cudaStream_t s)
+                double* Fdn, const SweepIO& io, cudaStream_t s)
 {
     int rc = launch_prep(p, T, status, warm_valid, s);
     if (rc) return rc;
-    rc = launch_sweep(p, status, n_passes, warm_valid, Fup_toa, s);
+    rc = launch_sweep(p, status, n_passes, warm_valid, io, s);
     if (rc) return rc;
     return launch_k(use_pdl(p, s), finalize_kernel, dim3(p->max_n + 1, p->A), dim3(32), 0, s, p->dev, status, Fup, Fdn);
 }
@@ -1013,19 +1031,28 @@ int helios_interp_opacity(helios_plan* p, const double* T_layer, float* kappa_pt
     return HELIOS_OK;
 }
 
-int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int warm, double* Fup_bol,
-                      double* Fdn_bol, float* Fup_toa, cudaStream_t s)
+int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int warm, float* Fup_warm,
+                      double* Fup_bol, double* Fdn_bol, float* Fup_toa, float* F_spec, cudaStream_t s)
 {
     if (!p || !T_layer || !Fup_bol || !Fdn_bol) return fail(HELIOS_EINVAL, "helios_flux_sweep: null argument");
+    if (Fup_warm && (reinterpret_cast<uintptr_t>(Fup_warm) & 15))
+        return fail(HELIOS_EINVAL, "helios_flux_sweep: Fup_warm is not 16-byte aligned");
     if (n_passes < HELIOS_DIRECT) return fail(HELIOS_EINVAL, "helios_flux_sweep: n_passes = %d", n_passes);
     if (n_passes == HELIOS_DIRECT && p->prm.tabulate)
         return fail(HELIOS_EINVAL, "helios_flux_sweep: the exact column solve has no tabulated form");
     if (n_passes == 0) n_passes = p->passes;
     CUDA_TRY(cudaSetDevice(p->ctx->device));
-    const int warm_valid = (warm && p->warm_ready) ? 1 : 0;
-    int rc = launch_eval(p, T_layer, nullptr, n_passes, warm_valid, Fup_bol, Fdn_bol, Fup_toa, s);
+    // a caller-owned warm start is valid when the caller says so; the plan's own once it holds an
+    // evaluation.  The shift to the new temperatures uses the point temperatures of this plan's
+    // previous evaluation either way
+    const int warm_valid = (warm && (Fup_warm || p->warm_ready)) ? 1 : 0;
+    SweepIO io;
+    io.Fup_toa = Fup_toa;
+    io.F_spec = F_spec;
+    io.warm = Fup_warm;
+    int rc = launch_eval(p, T_layer, nullptr, n_passes, warm_valid, Fup_bol, Fdn_bol, io, s);
     if (rc) return rc;
-    p->warm_ready = true;
+    if (!Fup_warm) p->warm_ready = true;
     return HELIOS_OK;
 }
 
@@ -1048,7 +1075,7 @@ int helios_re_step(helios_plan* p, double* T_layer, int warm, double* mult, uint
     double* Fu = Fup_bol ? Fup_bol : p->Fup;
     double* Fd = Fdn_bol ? Fdn_bol : p->Fdn;
     int rc = launch_prep(p, T_layer, nullptr, warm_valid, s);
-    if (!rc) rc = launch_sweep(p, nullptr, p->passes, warm_valid, nullptr, s);
+    if (!rc) rc = launch_sweep(p, nullptr, p->passes, warm_valid, SweepIO(), s);
     if (!rc) rc = launch_post(p, nullptr, Fu, Fd, T_layer, mult, hist, nhist, status, iters, metric, nullptr, 0, 0, s);
     if (rc) return rc;
     p->warm_ready = true;
@@ -1078,7 +1105,7 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
     // first temperature step: the coupled stream starts from zero.  Every step ends with
     // post_kernel, which also prepares the next evaluation at the new temperatures
     int rc = launch_prep(p, T_layer, status, 0, w);
-    if (!rc) rc = launch_sweep(p, status, p->passes, 0, nullptr, w);
+    if (!rc) rc = launch_sweep(p, status, p->passes, 0, SweepIO(), w);
     if (!rc) rc = launch_post(p, status, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters, nullptr,
                               p->n_active, 1, 1, w);
     if (rc) return rc;
@@ -1117,7 +1144,7 @@ int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* st
             CUDA_TRY(cudaStreamBeginCapture(w, cudaStreamCaptureModeThreadLocal));
         }
         for (int i = 0; i < chunk && rc == HELIOS_OK; ++i) {
-            rc = launch_sweep(p, status, p->passes, 1, nullptr, w);
+            rc = launch_sweep(p, status, p->passes, 1, SweepIO(), w);
             if (rc == HELIOS_OK)
                 rc = launch_post(p, status, p->Fup, p->Fdn, T_layer, p->mult, p->hist, p->nhist, status, iters,
                                  nullptr, p->n_active, 1, 1, w);
@@ -1302,10 +1329,10 @@ extern "C" int helios_autotune(helios_ctx* ctx, const helios_batch_t* b, const h
             rc = helios_plan_create(ctx, &sub, tabs, ntab, &p, &plan);
             if (rc) break;
             float ms[3];
-            rc = helios_flux_sweep(plan, dT, 0, 0, dFu, dFd, nullptr, ctx->stream);
+            rc = helios_flux_sweep(plan, dT, 0, 0, nullptr, dFu, dFd, nullptr, nullptr, ctx->stream);
             for (int r = 0; r < 3 && rc == HELIOS_OK; ++r) {
                 cudaEventRecord(e0, ctx->stream);
-                rc = helios_flux_sweep(plan, dT, 0, 1, dFu, dFd, nullptr, ctx->stream);
+                rc = helios_flux_sweep(plan, dT, 0, 1, nullptr, dFu, dFd, nullptr, nullptr, ctx->stream);
                 cudaEventRecord(e1, ctx->stream);
                 cudaEventSynchronize(e1);
                 cudaEventElapsedTime(&ms[r], e0, e1);

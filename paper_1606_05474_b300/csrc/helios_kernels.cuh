@@ -70,6 +70,7 @@ struct AtmDesc {
     int spec_off, cl, pad1, pad2;             // cl: lanes per column of the iterated sweep (16, 32)
     long long warm_off;     // float offset of this atmosphere's warm-start block
     long long part_off;     // double offset of this atmosphere's partial sums
+    long long fspec_off;    // float offset of this atmosphere's per-bin flux block [L][2][2n+1]
 };
 
 struct TabDesc {
@@ -580,7 +581,8 @@ __host__ __device__ constexpr size_t sweep_smem_bytes(int M, int G, int CL = 32)
 // half the scan levels and fewer padded slots per column, at twice the registers per lane
 template <int M, bool DIRECT, int CL = 32>
 __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int* __restrict__ status, int n_passes,
-                                           int warm_valid, float* __restrict__ Fup_toa, unsigned char* smem_raw)
+                                           int warm_valid, float* __restrict__ Fup_toa, float* __restrict__ F_spec,
+                                           unsigned char* smem_raw)
 {
     static_assert(CL == 32 || (CL == 16 && !DIRECT), "16-lane columns: iterated passes only");
     constexpr int W = CL * M;               // point slots per column
@@ -621,7 +623,8 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     const int p4_first = vec4 ? tid / G4 : 0, g4_of = vec4 ? tid - p4_first * G4 : 0;
     const int p4_stride = vec4 ? nthreads / G4 : 1;
     const float* tab = td.kappa;
-    float* wbase = P.warm + ad.warm_off;
+    // warm-start columns (none when the launch keeps no warm start: then nothing is stored)
+    float* wbase = P.warm ? P.warm + ad.warm_off : nullptr;
 
     for (int l = l_begin; l < l_end; ++l) {
         // the next bin's inputs move into L2 while this bin is processed: its constants, the
@@ -641,7 +644,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     }
                 }
             }
-            if (!DIRECT && warm_valid) {
+            if (!DIRECT && warm_valid && wbase) {
                 const float* wn = wbase + (long long)(l + 1) * G * W;
                 for (int i = tid * 32; i < G * W; i += nthreads * 32) prefetch_l2(wn + i);
             }
@@ -776,7 +779,8 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             // chunk M'; point p at slot (p mod M') CL' + p / M').  At 32 lanes that is this warp's
             // own layout.  At 16 the column goes through the warp's shared-memory row first, so
             // that consecutive lanes write consecutive slots
-            if (ad.cl == 32) {
+            if (!wbase) {
+            } else if (ad.cl == 32) {
                 const long long col = (long long)(l * G + g) * W;
 #pragma unroll
                 for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = U[k];
@@ -873,7 +877,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const int p = sub * M + k;
-                X[k] = warm_valid ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
+                X[k] = (warm_valid && wbase) ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
             }
             X[M] = 0.0f;
             const float toa_g = bc_toa[0];
@@ -932,12 +936,25 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     }
                 }
             }
-            if (g_ok) {
+            if (g_ok && wbase) {
 #pragma unroll
                 for (int k = 0; k < M; ++k) wbase[col + k * CL + sub] = X[k];
             }
         }
         __syncthreads();
+        // optional per-bin fluxes at every point (a debug output): sum_g w_g G + 2 pi eps B in
+        // double, fixed order; [up points 0..2n][down points 0..2n] per bin
+        if (F_spec) {
+            float* fs = F_spec + ad.fspec_off + (long long)l * 2 * NP;
+            for (int t = tid; t < 2 * NP; t += nthreads) {
+                const bool up = t < NP;
+                const int q = up ? t : t - NP;
+                const float* row = (up ? upr : kap) + q;
+                double sg = 0.0;
+                for (int gg = 0; gg < G; ++gg) sg += (double)row[gg * KST];
+                fs[t] = (float)(sg + (double)bt[q]);
+            }
+        }
         // ---- phase 3: Gauss-point sums (fixed order, float) into the item's FP64 accumulators.
         // Thread t sums interface t's column of the per-warp rows (downward interfaces 0..n, then
         // upward interfaces 0..n; interface i is point 2i); the threads after them add the Planck
@@ -988,12 +1005,13 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 template <int M, int MINB, bool DIRECT = false, int CL = 32>
 __global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
                                                              int* __restrict__ counter, const int* __restrict__ status,
-                                                             int n_passes, int warm_valid, float* __restrict__ Fup_toa)
+                                                             int n_passes, int warm_valid, float* __restrict__ Fup_toa,
+                                                             float* __restrict__ F_spec)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (!counter) {
-        sweep_item<M, DIRECT, CL>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        sweep_item<M, DIRECT, CL>(P, order[blockIdx.x], status, n_passes, warm_valid, Fup_toa, F_spec, smem_raw);
         return;
     }
     __shared__ int s_next;
@@ -1002,7 +1020,7 @@ __global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const i
         __syncthreads();
         const int k = s_next;
         if (k >= count) break;
-        sweep_item<M, DIRECT, CL>(P, order[k], status, n_passes, warm_valid, Fup_toa, smem_raw);
+        sweep_item<M, DIRECT, CL>(P, order[k], status, n_passes, warm_valid, Fup_toa, F_spec, smem_raw);
         __syncthreads();                    // shared memory is reused by the next item
     }
     if (threadIdx.x == 0 && atomicAdd(counter + 1, 1) == (int)gridDim.x - 1) {

@@ -150,7 +150,7 @@ int launch_sweep(const PlanDev& P, int dev, int count, const int* order, int n_p
         NA_CUDA(cudaFuncSetAttribute(sweep_kernel<M, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         g_smem_set[dev][M] = true;
     }
-    sweep_kernel<M, MINB><<<count, 32 * P.G, smem, s>>>(P, order, count, nullptr, nullptr, n_passes, 0, toa);
+    sweep_kernel<M, MINB><<<count, 32 * P.G, smem, s>>>(P, order, count, nullptr, nullptr, n_passes, 0, toa, nullptr);
     NA_CUDA(cudaGetLastError());
     return HELIOS_OK;
 }

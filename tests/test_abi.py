@@ -38,5 +38,5 @@ def test_null_arguments_are_rejected_without_a_device():
     assert lib.helios_create(None, 0) == _lib.HELIOS_EINVAL
     assert lib.helios_plan_create(None, None, None, 0, None, None) == _lib.HELIOS_EINVAL
     assert b"null" in lib.helios_last_error()
-    assert lib.helios_flux_sweep(None, None, 0, 0, None, None, None, None) == _lib.HELIOS_EINVAL
+    assert lib.helios_flux_sweep(None, None, 0, 0, None, None, None, None, None, None) == _lib.HELIOS_EINVAL
     assert lib.helios_solve_re(None, None, None, None, None) == _lib.HELIOS_EINVAL
