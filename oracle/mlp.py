@@ -80,6 +80,31 @@ def loss_and_grad(params, dims, x, t, bf16_ops=True):
     return loss, flat
 
 
+def magnitude_sums(params, dims, x, t, bf16_ops=True):
+    """Element-wise scales for comparing a computed network with this oracle: for every element of
+    the forward output and of the gradient, the sum of the absolute values of the terms of the
+    product that forms it (|q(h)| @ |q(W)| + |b| for the output, |q(h)|^T @ |q(dz)| and
+    sum |dz| for the gradient).  Rounding one operand of a product to the other side of a
+    bfloat16 boundary, or accumulating it in float32, moves an element by a fraction of its
+    scale.  Returns (output scale [B, n_out], flat gradient scale in the library's layout)."""
+    q = bf16 if bf16_ops else (lambda v: np.asarray(v, np.float64))
+    layers = split(np.asarray(params, np.float64), dims)
+    y, zs, hs = forward(params, dims, x, bf16_ops)
+    WL, bL = layers[-1]
+    sy = np.abs(q(hs[-1])) @ np.abs(q(WL)) + np.abs(bL)
+    d = y - t
+    dz = 2.0 * d / d.size
+    scales = []
+    for l in range(len(layers) - 1, -1, -1):
+        W, b = layers[l]
+        scales.append((np.abs(q(hs[l])).T @ np.abs(q(dz)), np.abs(dz).sum(axis=0)))
+        if l > 0:
+            dz = (q(dz) @ q(W).T) * dsilu(zs[l - 1])
+    scales.reverse()
+    flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in scales])
+    return sy, flat
+
+
 def adam(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam step (bias-corrected), returns new (params, m, v)."""
     m = b1 * m + (1 - b1) * grad

@@ -1,10 +1,13 @@
 """The learned initialiser's network on the GPU vs the FP64 NumPy oracle on the same BF16-rounded
 operands, and what the trained network gains over the isothermal start.
 
-Tolerances: the GPU accumulates in FP32 and keeps activations in FP32 before the next product
-rounds them to BF16, so a rare activation lands on the other side of a BF16 rounding boundary
-than in the FP64 oracle; per tensor the relative L2 error is bounded by 2e-3 (one BF16 ulp is
-3.9e-3) and measured ~1e-4."""
+Tolerances, element by element: every output and gradient element is a product's sum of terms;
+the GPU accumulates in FP32 and keeps activations in FP32 before the next product rounds them to
+BF16, so a rare activation lands on the other side of a BF16 rounding boundary than in the FP64
+oracle and moves the elements it feeds by at most one BF16 unit (2^-8) of that term.  Each
+element must therefore lie within 2^-7 of its scale, the sum of the absolute values of its terms
+(oracle.mlp.magnitude_sums), and the typical element far inside that: the 99th percentile of the
+scaled error within 2^-12.  The loss is compared to 2e-3 relative."""
 import numpy as np
 import pytest
 
@@ -22,8 +25,12 @@ def _net(B, seed=5):
     return hp.MLP(ctx(), seed=seed, max_batch=B)
 
 
-def _rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+def _check_scaled(a, b, scale, what):
+    """Element-wise: |a - b| <= 2^-7 scale everywhere, 99th percentile <= 2^-12 scale."""
+    e = np.abs(np.asarray(a, np.float64) - b) / np.maximum(scale, 1e-30)
+    assert e.max() < 2.0 ** -7, f"{what}: max scaled error {e.max():.3e}"
+    assert np.quantile(e, 0.99) < 2.0 ** -12, f"{what}: 99th percentile {np.quantile(e, 0.99):.3e}"
+    return float(e.max())
 
 
 def _data(B, seed=1):
@@ -38,8 +45,10 @@ def test_forward_matches_oracle():
     x, _ = _data(B)
     y = net.forward(torch.from_numpy(x.astype(np.float32)).cuda()).double().cpu().numpy()
     p = net.params.double().cpu().numpy()
-    yo, _, _ = omlp.forward(p, DIMS, x.astype(np.float32).astype(np.float64), bf16_ops=True)
-    assert _rel_l2(y, yo) < 2e-3
+    x64 = x.astype(np.float32).astype(np.float64)
+    yo, _, _ = omlp.forward(p, DIMS, x64, bf16_ops=True)
+    sy, _ = omlp.magnitude_sums(p, DIMS, x64, np.zeros((B, DIMS[-1])))
+    _check_scaled(y, yo, sy, "forward")
 
 
 def test_gradients_match_oracle():
@@ -53,11 +62,12 @@ def test_gradients_match_oracle():
     g = net.grads.double().cpu().numpy()
     p = net.params.double().cpu().numpy()
     lo, go = omlp.loss_and_grad(p, DIMS, xf.astype(np.float64), tf.astype(np.float64), bf16_ops=True)
+    _, sg = omlp.magnitude_sums(p, DIMS, xf.astype(np.float64), tf.astype(np.float64))
     assert loss.item() == pytest.approx(lo, rel=2e-3)
     o = 0
-    for a, b in zip(DIMS[:-1], DIMS[1:]):
-        for n in (a * b, b):                  # weight block, then bias block
-            assert _rel_l2(g[o:o + n], go[o:o + n]) < 2e-3
+    for li, (a, b) in enumerate(zip(DIMS[:-1], DIMS[1:])):
+        for n, kind in ((a * b, "W"), (b, "b")):          # weight block, then bias block
+            _check_scaled(g[o:o + n], go[o:o + n], sg[o:o + n], f"grad {kind}{li}")
             o += n
 
 

@@ -59,3 +59,21 @@ def test_adam_first_step_is_sign_step():
     p = np.zeros(5); g = np.array([1.0, -2.0, 0.5, -1e-3, 3.0])
     p1, m, v = mlp.adam(p, g, np.zeros(5), np.zeros(5), 1, lr=0.01)
     assert np.allclose(p1, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_magnitude_sums_equal_the_values_when_every_term_is_non_negative():
+    # with non-negative inputs, weights and biases every term of every product is non-negative, so
+    # the scale of the output (the sum of |terms|) is the output itself (the last layer's input is
+    # a SiLU output, non-negative for non-negative pre-activations)
+    rng = np.random.default_rng(4)
+    dims = [3, 5, 4]
+    n = sum(a * b + b for a, b in zip(dims[:-1], dims[1:]))
+    p = rng.uniform(0.0, 1.0, n)
+    x = rng.uniform(0.0, 1.0, (7, 3))
+    y, _, _ = mlp.forward(p, dims, x, bf16_ops=False)
+    sy, sg = mlp.magnitude_sums(p, dims, x, np.zeros((7, 4)), bf16_ops=False)
+    np.testing.assert_allclose(sy, y, rtol=1e-14)
+    # y > 0 = target, so every output error and hence every gradient term of the last layer is positive
+    _, g = mlp.loss_and_grad(p, dims, x, np.zeros((7, 4)), bf16_ops=False)
+    last = slice(n - (5 * 4 + 4), n)
+    np.testing.assert_allclose(sg[last], g[last], rtol=1e-14)
