@@ -47,6 +47,8 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared",
                                "-fPIC", "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
+    from . import opcount
+    opcount.build(force)
     return _SO
 
 
