@@ -1,20 +1,33 @@
 """Benchmark of the radiative-equilibrium hot path on one B300 (or N, one process per GPU).
 
-A step is one radiative-equilibrium iteration over the whole workload: opacities, sublayer
-optical depths, two-stream coefficients, 1 + n_scat down/up passes, Gauss-point and bin sums,
-and the FP64 temperature step (helios_flux_sweep + helios_temp_update).  The workload is the
-full-size single atmosphere: 100 layers (1e-6..1e3 bar) x 3000 wavenumber bins
-(0.3-200 um) x 20 Gauss points, Rayleigh-like scattering, seeded synthetic k-table.
-Each GPU process runs its own copy of that atmosphere (atmospheres are independent; no
-collective on the data path): weak scaling.
+Metric: RE-converged atmospheres/s and flux-sweep Gcell/s, batched + surrogate vs plain.
 
-value: Gcell/s, cell = (atmosphere, layer, bin, g) of one full RE iteration.
-L2 is flushed (a 256 MB write) before every timed step; only the step is inside the events.
+Default (the headline line):
+- value: the batched solver step -- one radiative-equilibrium iteration (opacities, sublayer
+  optical depths, two-stream coefficients, 1 + 4 scattering passes, Gauss-point and bin sums,
+  FP64 temperature step) of 4096 ragged atmospheres (layers U{50..200}, bins U{300..3000} x 20 g,
+  Rayleigh-like scattering, a pool of 64 seeded k-tables) with autotuned launches, in Gcell/s
+  (cell = atmosphere x layer x bin x g of one full iteration).  W untimed steps, then K timed
+  steps between CUDA events on the launching stream; the working set (151 GB) is far larger than
+  L2, so no flush is needed.
+- surrogate_vs_plain: converged atmospheres per second of held-out planets of the learned-
+  initialiser family, solved in one batched graph-captured solve from the isothermal start
+  (plain) and from the learned network's profile (surrogate, inference inside the timed region),
+  both to eq. (29), and the multiple between them.
+- single_atmosphere: the full-size single atmosphere (100 layers x 3000 bins x 20 g, scattering):
+  per-step times with L2 flushed, back-to-back steady state, the sweep kernel, end to end, one full
+  solve, the exact column solve and the post-processing spectrum.
+- roofline: the sweep kernel of the batched step against the three floors of its work (HBM bytes,
+  FP32 instructions, SFU operations); the FP32 and SFU counts per cell come from the op-counting
+  build of the oracle on a bounded sample of the same workload (taken in the cpu_baseline leg).
+- cpu_baseline: the FP64 oracle on the host cores on a bounded sample of the batched workload.
 
---impl reference: the FP64 CPU oracle (test infrastructure) timed on the host cores on a
-bounded sample of the same workload, same metric and unit.
+--workload batched|learned|single|spectrum prints the line of one part alone.
+--impl reference: the FP64 CPU oracle timed on the host cores on the headline's workload and
+metric (bounded sample per step).
 """
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -28,7 +41,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RE-converged atmospheres/s & flux-sweep Gcell/s, batched+surrogate vs plain"
 UNIT = "Gcell/s"
-WORKLOAD = "full-size single atmosphere: 100 layers x 3000 bins x 20 g, scattering, 5 passes/step"
+BATCHED_WORKLOAD = ("batched ragged: {A} atmospheres per GPU, layers U{{50..200}}, bins U{{300..3000}} x 20 g, "
+                    "Rayleigh-like scattering, 1 + 4 passes per step, pool of 64 k-tables, autotuned")
+SINGLE_WORKLOAD = "full-size single atmosphere: 100 layers x 3000 bins x 20 g, scattering, 5 passes/step"
 
 
 def dist_env():
@@ -104,6 +119,7 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+        time.sleep(0.4)                                 # let the sampler attach before timing
 
     def stop(self):
         if not self.proc:
@@ -127,10 +143,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM traffic (read + write) of one sweep-kernel launch on the full-size single atmosphere, from
-# the ncu capture summarised in profiles/sweep_kernel_full_single_atmosphere.md, valid only for the
-# kernel source it was taken on (sha256 prefix of csrc/helios_kernels.cuh); null otherwise.
-SWEEP_TRAFFIC = {"kernels_sha256": "abf436c89c4d6f59", "bytes_per_launch": 63123200}
+# DRAM traffic (read + write) per cell of the sweep kernel, from ncu captures of the same command
+# on smaller cases (the summaries under profiles/ give each command), valid only for the kernel
+# source they were taken on (sha256 prefix of the kernels and the launch code); null otherwise.
+SWEEP_TRAFFIC = {"kernels_sha256": None, "bytes_per_cell": {}}
 
 
 def kernel_source_hash():
@@ -143,23 +159,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def algorithmic_counts(wl, n_passes):
-    """Algorithmic work of one RE step (see the design notes, roofline section).
-
-    bytes: warm-start upward fluxes read and written (4 B per column point), the k-table rows
-    the profile touches (counted from the actual (iP, iT) corners), bolometric outputs.
-    fp32: per sublayer 24 coefficient operations once per step plus 4 fused multiply-adds per
-    pass (down and up recurrences); sfu: 3 per sublayer (exp, 2 reciprocals)."""
-    cells = wl.cells
-    subs = sum(2 * a.n_layers * a.n_bins for a in wl.atms) * wl.G
-    pts = sum((2 * a.n_layers + 1) * a.n_bins for a in wl.atms) * wl.G
-    fp32 = subs * (24 + 4 * n_passes)
-    sfu = subs * 3
-    return cells, pts, fp32, sfu
+def measured_traffic(key, cells):
+    if SWEEP_TRAFFIC["kernels_sha256"] != kernel_source_hash() or key not in SWEEP_TRAFFIC["bytes_per_cell"]:
+        return None
+    return int(SWEEP_TRAFFIC["bytes_per_cell"][key] * cells)
 
 
 def touched_table_bytes(plan, wl, T):
-    """Bytes of the k-table rows (iP, iT corners) the current profile touches, from the library's
+    """Bytes of the k-table rows (iP, iT corners) the current profiles touch, from the library's
     own index output (helios_interp_opacity)."""
     _, idx, _ = plan.interp_opacity(T, want_kappa=False)
     idx = idx.cpu().numpy()
@@ -174,193 +181,56 @@ def touched_table_bytes(plan, wl, T):
     return tot
 
 
-def run_gpu(args):
+def sweep_bytes(plan, wl, T):
+    """Algorithmic DRAM bytes of one flux evaluation: the warm-start upward fluxes read and written
+    (4 B per column point each way), the k-table rows the profiles touch, the bolometric outputs."""
+    pts = sum((2 * a.n_layers + 1) * a.n_bins for a in wl.atms) * wl.G
+    return 2 * 4 * pts + touched_table_bytes(plan, wl, T) + 16 * int(plan.info.interfaces)
+
+
+def fp32_peak_derived(dev_index, sm_max_mhz):
+    """FP32 instruction peak from unit counts and the maximum SM clock: SMs x 128 FP32 lanes x f."""
     import torch
-    rank, world, local = dist_env()
-    init_replicas(world, local)
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    return sms * 128 * sm_max_mhz * 1e6 / 1e12
+
+
+def roofline(sweep_ms, cells, alg_bytes, counts, fp32_peak, sfu_peak, hbm, traffic, kernel, clocks_mhz):
+    """The sweep against its three floors: algorithmic HBM bytes at the measured copy bandwidth,
+    algorithmic FP32 instructions at the FP32 pipe's peak, SFU operations at the measured MUFU
+    rate.  The binding term is the largest floor; `frac` is achieved / peak in that term."""
+    t = sweep_ms * 1e-3
+    terms = {"hbm": {"work": alg_bytes, "unit": "GB/s", "peak": hbm, "achieved": alg_bytes / t / 1e9}}
+    if counts:
+        fp32 = counts["fp32_per_cell"] * cells
+        sfu = counts["sfu_per_cell"] * cells
+        terms["alu"] = {"work": fp32, "unit": "T FP32 inst/s", "peak": fp32_peak, "achieved": fp32 / t / 1e12}
+        terms["sfu"] = {"work": sfu, "unit": "T SFU op/s", "peak": sfu_peak, "achieved": sfu / t / 1e12}
+    for v in terms.values():
+        v["frac"] = round(v["achieved"] / v["peak"], 4)
+        v["floor_ms"] = round(sweep_ms * v["frac"], 5)
+        v["achieved"] = round(v["achieved"], 3)
+    bound = max(terms, key=lambda k: terms[k]["floor_ms"])
+    b = terms[bound]
+    return {"bound": "alu" if bound in ("alu", "sfu") else bound, "binding_term": bound, "achieved": b["achieved"],
+            "peak": b["peak"], "unit": b["unit"], "frac": b["frac"], "traffic": traffic, "kernel": kernel,
+            "kernel_ms": round(sweep_ms, 5), "algorithmic_bytes": int(alg_bytes),
+            "terms": {k: {kk: vv for kk, vv in v.items() if kk != "work"} for k, v in terms.items()},
+            "peak_source": {"hbm": "measured (MEASURED_PEAKS.json)",
+                            "alu": f"derived: SMs x 128 FP32 lanes x {clocks_mhz:.0f} MHz (max SM clock)",
+                            "sfu": "measured on the device (helios_measure_peaks: MUFU ex2 chains on every SM)"},
+            "counts_source": counts.get("source") if counts else None,
+            "fp32_per_cell": counts.get("fp32_per_cell") if counts else None,
+            "sfu_per_cell": counts.get("sfu_per_cell") if counts else None}
+
+
+# ---------------------------------------------------------------------------------------------
+# batched solver step (the headline value)
+# ---------------------------------------------------------------------------------------------
+def run_batched(args, world, rank, local, dev):
+    import torch
     import synth
     import paper_1606_05474_b300 as hp
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    wl = synth.config2()
-    wl.atms[0].T_init = synth.perturbed_profile(wl.atms[0], 11 + rank, amp=200.0)
-    ctx = hp.Context(local)
-    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
-    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(col_lanes=args.col_lanes))
-    n_passes = plan.info.passes
-    lanes = 32 if args.col_lanes == 32 else 16       # automatic: 16 lanes for 24..119 layers
-    T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).to(dev)
-    T0 = T.clone()
-    state = plan.new_state()
-    Fu = torch.empty(plan.info.interfaces, dtype=torch.float64, device=dev)
-    Fd = torch.empty_like(Fu)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step(warm):
-        plan.re_step(T, state, warm=warm, out=(Fu, Fd))
-
-    # warm-up (the first step starts the coupled stream from zero)
-    step(False)
-    for _ in range(args.warmup - 1):
-        step(True)
-    torch.cuda.synchronize()
-    # prep, sweep groups, finalize (unless fused), post
-    n_launch_per_step = 2 + plan.info.sweep_launches + (0 if plan.info.fused_finalize else 1)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.4)                                     # let the sampler attach before timing
-    barrier(world)
-    torch.cuda.synchronize()
-    t_wall = time.time()
-    for k in range(args.steps):
-        flush.zero_()                                   # evict L2 between timed steps
-        ev[k][0].record(stream)
-        step(True)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    wall = time.time() - t_wall
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    # the sweep kernel's own time: the same steps again with events around the sweep launches
-    # (kept out of the timed loop above: the events split the step's chain of dependent launches)
-    n_sweep = min(args.steps, 500)
-    plan.set_timing(n_sweep)
-    for _ in range(n_sweep):
-        flush.zero_()
-        step(True)
-    torch.cuda.synchronize()
-    sweep_ms = list(plan.sweep_times(n_sweep))
-    plan.set_timing(0)
-    total_ms = float(np.sum(step_ms))
-    total_ms = max_over_ranks(total_ms, world, dev)
-
-    cells, pts, fp32, sfu = algorithmic_counts(wl, n_passes)
-    value = cells * args.steps * world / (total_ms * 1e-3) / 1e9
-
-    # ---- end to end: host temperatures in, host temperatures and status out, every step
-    Th = torch.empty(plan.info.layers, dtype=torch.float64).pin_memory()
-    Th.copy_(T.cpu())
-    Sh = torch.empty(plan.A, dtype=torch.int32).pin_memory()
-    e2e_ms = []
-    e2e_steps = min(args.steps, 200)
-    for k in range(e2e_steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        T.copy_(Th, non_blocking=True)
-        step(True)
-        Th.copy_(T, non_blocking=True)
-        Sh.copy_(state["status"], non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        e2e_ms.append(a.elapsed_time(b))
-    e2e_total = float(np.sum(e2e_ms))
-    e2e_total = max_over_ranks(e2e_total, world, dev)
-    e2e_value = cells * e2e_steps * world / (e2e_total * 1e-3) / 1e9
-
-    # ---- one full radiative-equilibrium solve from the start profile (context)
-    solve = None
-    if not args.no_solve:
-        Ts = T0.clone()
-        torch.cuda.synchronize()
-        t0 = time.time()
-        iters, status = plan.solve_re(Ts)
-        torch.cuda.synchronize()
-        dt = time.time() - t0
-        solve = {"wall_s": round(dt, 4), "iters": int(iters.item()), "status": int(status.item()),
-                 "atm_per_s": round(1.0 / dt, 3), "tol": 1e-7}
-
-    # ---- the exact column solve (the limit of the passes, Sect. 2.2.3) against 1 + 4 passes, the
-    # RE solve with it, and the post-processing spectrum (isothermal layers, Sect. 3) with
-    # 1 + 80 passes against the exact solve; each sweep timed cold-start after an L2 flush
-    direct = None
-    if not args.no_solve:
-        def time_sweeps(pl, Tt, npass, reps=20):
-            pl.flux_sweep(Tt, n_passes=npass, warm=False, want_toa=True)
-            pl.set_timing(reps)
-            for _ in range(reps):
-                flush.zero_()
-                pl.flux_sweep(Tt, n_passes=npass, warm=False, want_toa=True)
-            torch.cuda.synchronize()
-            return round(float(np.median(pl.sweep_times(reps))), 5)
-        Tc = Ts.clone()
-        ms_dir, ms_pass = time_sweeps(plan, Tc, hp.DIRECT), time_sweeps(plan, Tc, n_passes)
-        pd = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(direct=1))
-        Td = T0.clone()
-        torch.cuda.synchronize()
-        t0 = time.time()
-        it_d, st_d = pd.solve_re(Td)
-        torch.cuda.synchronize()
-        dt_d = time.time() - t0
-        pp = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(iso_layers=1))
-        # Sect. 2.6: the same 1 + 4 passes with the tabulated Planck and transmission functions
-        pt = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(tabulate=1))
-        ms_tab = time_sweeps(pt, Tc, n_passes)
-        del pt
-        direct = {"sweep_ms_exact": ms_dir, "sweep_ms_passes": ms_pass, "passes": n_passes,
-                  "sweep_ms_passes_tabulated_functions": ms_tab,
-                  "re_solve_exact": {"wall_s": round(dt_d, 4), "iters": int(it_d.item()), "status": int(st_d.item()),
-                                     "max_dT_vs_passes_K": round(float((Td - Ts).abs().max()), 4)},
-                  "post_processing_spectrum_ms": {"isothermal_layers_81_passes": time_sweeps(pp, Tc, 81),
-                                                  "isothermal_layers_exact": time_sweeps(pp, Tc, hp.DIRECT)}}
-        del pd, pp
-
-    if rank != 0:
-        return
-    P = peaks()
-    hbm = P.get("hbm_gbs", 6400.0)
-    sweep_avg = float(np.mean(sweep_ms))
-    warm_bytes = 2 * 4 * pts                        # read + write of the warm-start upward fluxes
-    table_bytes = touched_table_bytes(plan, wl, T)
-    alg_bytes = warm_bytes + table_bytes + 16 * plan.info.interfaces
-    achieved = alg_bytes / (sweep_avg * 1e-3) / 1e9
-    # FP32 and MUFU peaks measured on this device (helios_measure_peaks): T instructions/s
-    fp32_tflops, sfu_tops = hp.measure_peaks(ctx)
-    fp32_peak = fp32_tflops / 2.0                        # an FMA counts once as an instruction
-    line = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "atmospheres_per_gpu": 1, "layers": 100, "bins": 3000, "g": 20,
-                   "passes_per_step": n_passes, "cells_per_step_per_gpu": cells, "l2": "flushed before every step",
-                   "parallelism": f"replicas x{world}", "lanes_per_column": lanes},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4),
-                     "traffic": (SWEEP_TRAFFIC["bytes_per_launch"]
-                                 if kernel_source_hash() == SWEEP_TRAFFIC["kernels_sha256"] else None),
-                     "kernel": "sweep_kernel<7> (32 lanes)" if lanes == 32 else "sweep_kernel<13> (16 lanes)",
-                     "kernel_ms": round(sweep_avg, 5),
-                     "algorithmic_bytes": int(alg_bytes), "peak_source": "measured",
-                     "fp32_frac": round(fp32 / (sweep_avg * 1e-3) / 1e12 / fp32_peak, 4),
-                     "sfu_frac": round(sfu / (sweep_avg * 1e-3) / 1e12 / sfu_tops, 4),
-                     "fp32_peak_measured_tinst_s": round(fp32_peak, 2), "sfu_peak_measured_tops": round(sfu_tops, 3)},
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(8 * plan.info.layers),
-                "d2h_bytes_per_step": int(8 * plan.info.layers + 4 * plan.A)},
-        "gpu_launches": n_launch_per_step * args.steps,
-        "clocks": clk,
-        "re_solve": solve,
-        "exact_column_solve": direct,
-        "wall_s": round(wall, 3),
-    }
-    if not args.no_cpu_baseline and world == 1:            # rank 0 at N = 1 only
-        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
-    print(json.dumps(line), flush=True)
-
-
-def run_gpu_batched(args):
-    """Batched ragged atmospheres (layers U{50..200}, bins U{300..3000}, 20 g, scattering), all in
-    flight at once: one RE step = one flux evaluation of every atmosphere + the temperature step.
-    The working set (warm-start fluxes of every column, tens of GB) is far larger than L2."""
-    import torch
-    rank, world, local = dist_env()
-    init_replicas(world, local)
-    import synth
-    import paper_1606_05474_b300 as hp
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     t0 = time.time()
     ids = replica_ids(rank, args.atmospheres)
     wl = synth.config3(A=len(ids), atm_ids=ids)
@@ -379,7 +249,6 @@ def run_gpu_batched(args):
     state = plan.new_state()
     Fu = torch.empty(plan.info.interfaces, dtype=torch.float64, device=dev)
     Fd = torch.empty_like(Fu)
-    plan.set_timing(args.steps)
     stream = torch.cuda.current_stream(dev)
 
     def step(warm):
@@ -389,126 +258,131 @@ def run_gpu_batched(args):
     for _ in range(args.warmup - 1):
         step(True)
     torch.cuda.synchronize()
+    plan.set_timing(args.steps)
     clocks = ClockSampler(local)
     clocks.start()
-    time.sleep(0.4)
     barrier(world)
+    torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(args.steps):
         step(True)
     b.record(stream)
     torch.cuda.synchronize()
+    barrier(world)
     clk = clocks.stop()
-    total_ms = a.elapsed_time(b)
-    total_ms = max_over_ranks(total_ms, world, dev)
+    total_ms = max_over_ranks(a.elapsed_time(b), world, dev)
     sweep_ms = float(np.mean(plan.sweep_times(args.steps)))
-    n_passes = plan.info.passes
-    cells, pts, fp32, sfu = algorithmic_counts(wl, n_passes)
+    plan.set_timing(0)
+    cells = wl.cells
     value = cells * args.steps * world / (total_ms * 1e-3) / 1e9
-    if rank != 0:
-        return
-    P = peaks()
-    hbm = P.get("hbm_gbs", 6400.0)
-    warm_bytes = 2 * 4 * pts
-    table_bytes = touched_table_bytes(plan, wl, T)
-    alg_bytes = warm_bytes + table_bytes + 16 * plan.info.interfaces
-    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
-    line = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step", "data": "synthetic",
-        "config": {"workload": f"batched ragged: {len(wl.atms)} atmospheres per GPU, layers U{{50..200}}, "
-                               "bins U{300..3000} x 20 g, scattering, 64-table pool",
-                   "cells_per_step_per_gpu": cells, "l2": "working set far larger than L2 (no flush)",
-                   "tuned": {"bins_per_item": tuned.bins_per_item, "persistent": tuned.persistent},
-                   "parallelism": f"replicas x{world}", "lanes_per_column": "16 for 24..119 layers, else 32"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None, "kernel": "sweep_kernel (all lane chunks)",
-                     "kernel_ms": round(sweep_ms, 3), "algorithmic_bytes": int(alg_bytes), "peak_source": "measured"},
-        "gpu_launches": (2 + plan.info.sweep_launches + (0 if plan.info.fused_finalize else 1)) * args.steps,
-        "clocks": clk,
-        "setup_s": {"inputs": round(t_gen, 2), "autotune": round(t_tune, 2), "plan": round(t_plan, 2)},
-        "workspace_gb": round(plan.info.workspace_bytes / 1e9, 2),
-    }
-    print(json.dumps(line), flush=True)
+
+    # end to end through helios_re_step_host: the temperatures of every atmosphere from pinned host
+    # memory in, the new temperatures and statuses back to the host, every step
+    Th = torch.empty(int(plan.info.layers), dtype=torch.float64).pin_memory()
+    Th.copy_(T.cpu())
+    Sh = torch.empty(plan.A, dtype=torch.int32).pin_memory()
+    Td = torch.empty_like(T)
+    torch.cuda.synchronize()
+    barrier(world)
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record(stream)
+    for _ in range(args.steps):
+        plan.re_step_host(Th, Td, state, Sh, warm=True)
+        torch.cuda.current_stream(dev).synchronize()        # the host reads the step's result
+    b2.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(a2.elapsed_time(b2), world, dev)
+    e2e = {"value": round(cells * args.steps * world / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT,
+           "h2d_bytes_per_step": int(8 * plan.info.layers), "d2h_bytes_per_step": int(8 * plan.info.layers + 4 * plan.A),
+           "path": "helios_re_step_host (host temperatures in, temperatures + statuses out, host waits every step)"}
+    out = {"value": value, "total_ms": total_ms, "sweep_ms": sweep_ms, "cells": cells, "clocks": clk, "e2e": e2e,
+           "launches_per_step": 2 + plan.info.sweep_launches + (0 if plan.info.fused_finalize else 1),
+           "tuned": {"bins_per_item": tuned.bins_per_item, "persistent": tuned.persistent},
+           "setup_s": {"inputs": round(t_gen, 2), "autotune": round(t_tune, 2), "plan": round(t_plan, 2)},
+           "workspace_gb": round(plan.info.workspace_bytes / 1e9, 2), "A": len(ids),
+           "alg_bytes": sweep_bytes(plan, wl, T) if rank == 0 else None, "ctx": ctx}
+    del plan, kap
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_gpu_learned(args):
-    """Batched radiative-equilibrium solves of held-out planets from the isothermal start (plain)
-    and from the learned initial profile (surrogate): RE-converged atmospheres per second.  The
-    planets are the learned-initialiser family (100 layers 1e-6..1e3 bar, 20 g, Rayleigh-like
-    scattering, opacity a metallicity- and C/O-weighted mixture of two seeded tables) on the
-    paper's radiative-equilibrium resolution of 300 bins (Sect. 3).  The surrogate is trained on
-    converged plain solutions of other planets of the family; its inference is inside the timed
-    region, plan set-up is not."""
+# ---------------------------------------------------------------------------------------------
+# surrogate vs plain: converged atmospheres per second
+# ---------------------------------------------------------------------------------------------
+def run_learned(args, world, rank, local, dev, ctx=None):
     import torch
-    rank, world, local = dist_env()
-    init_replicas(world, local)
     import synth
     import paper_1606_05474_b300 as hp
     from paper_1606_05474_b300.learned import LearnedInitializer, features
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     n_tr, n_te = args.train, args.test
     wl = synth.learned_dataset(n_tr + n_te, L=args.bins, n=100, first=rank * (n_tr + n_te))
-    ctx = hp.Context(local)
+    ctx = ctx or hp.Context(local)
     kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
     prm = hp.default_params(max_iter=20000)
     tr_atms, te_atms = wl.atms[:n_tr], wl.atms[n_tr:]
+    inf = {}
+    init = None
 
-    def solve(atms, starts):
+    def solve(atms, starts, pre=None):
         plan = hp.Plan(ctx, atms, wl.tables, kap, prm)
         T = torch.from_numpy(np.concatenate(starts)).to(dev)
         torch.cuda.synchronize()
+        barrier(world)
         t = time.time()
+        if pre is not None:
+            T = pre(plan)
         iters, status = plan.solve_re(T)
         torch.cuda.synchronize()
         dt = time.time() - t
-        return np.array(plan.split_layers(T.cpu().numpy())), iters.cpu().numpy(), status.cpu().numpy(), dt
+        out = np.array(plan.split_layers(T.cpu().numpy())), iters.cpu().numpy(), status.cpu().numpy(), dt
+        if pre is not None:
+            inf["starts"] = np.array(init.initial_profiles(plan, features(atms), [a.T_init for a in atms])[0])
+        return out
 
     Ttr, it_tr, st_tr, t_tr = solve(tr_atms, [a.T_init for a in tr_atms])
     ok = st_tr == 1
-    init = LearnedInitializer(ctx, seed=1, max_batch=max(256, n_te))
+    init = LearnedInitializer(ctx, seed=1, max_batch=max(256, n_te))    # noqa: F841 (used by solve)
     t = time.time()
     losses = init.fit(features(tr_atms)[ok], Ttr[ok], epochs=args.epochs, batch=256, lr=2e-3)
     torch.cuda.synchronize()
     t_fit = time.time() - t
     Tp, it_p, st_p, t_plain = solve(te_atms, [a.T_init for a in te_atms])
-    t = time.time()
-    starts, used = init.initial_profiles(features(te_atms), [a.n_layers for a in te_atms],
-                                         [a.T_init for a in te_atms])
-    t_inf = time.time() - t
-    Ts, it_s, st_s, t_sur = solve(te_atms, starts)
-    t_sur += t_inf
-    # whole job: atmospheres converged on every rank over the slowest rank's time
+
+    def predict(plan):
+        # inference inside the timed region: features -> network -> profiles on the plan's layers
+        t = time.time()
+        T, used = init.initial_profiles_device(plan, features(te_atms), [a.T_init for a in te_atms])
+        torch.cuda.synchronize()
+        inf["s"], inf["used"] = time.time() - t, used
+        return T
+
+    Ts, it_s, st_s, t_sur = solve(te_atms, [a.T_init for a in te_atms], pre=predict)
     n_conv_p = sum_over_ranks(int((st_p == 1).sum()), world, dev)
     n_conv_s = sum_over_ranks(int((st_s == 1).sum()), world, dev)
     t_plain_job = max_over_ranks(t_plain, world, dev)
     t_sur_job = max_over_ranks(t_sur, world, dev)
-    if rank != 0:
-        return
     both = (st_p == 1) & (st_s == 1)
     T0 = np.array([a.T_init for a in te_atms])
+    starts = inf["starts"]
     rms_iso = np.sqrt(((T0 - Tp) ** 2).mean(axis=1))[both]
     rms_ml = np.sqrt(((np.array(starts) - Tp) ** 2).mean(axis=1))[both]
     dT = np.abs(Ts - Tp)[both]
     flop_fwd = 2 * (6 * 256 + 2 * 256 * 256 + 256 * 100)
     n_fit = int(ok.sum()) * args.epochs
-    line = {
-        "metric": "RE-converged atmospheres/s, batched + surrogate vs plain", "value": round(n_conv_s / t_sur_job, 3),
-        "unit": "atm/s", "n_gpus": world, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step / bf16 MLP", "data": "synthetic",
-        "config": {"workload": f"learned-initialiser family: {n_te} held-out planets, 100 layers x {args.bins} bins x 20 g, "
-                               f"scattering, 2-table mixtures; surrogate trained on {int(ok.sum())} converged planets",
-                   "tol": prm.tol, "max_iter": prm.max_iter, "parallelism": f"replicas x{world}"},
-        "plain": {"atm_per_s": round(n_conv_p / t_plain_job, 3), "wall_s": round(t_plain, 3),
-                  "converged": int((st_p == 1).sum()), "iters_median": float(np.median(it_p)),
-                  "iters_mean": round(float(it_p.mean()), 1)},
-        "surrogate": {"atm_per_s": round(n_conv_s / t_sur_job, 3), "wall_s": round(t_sur, 3),
-                      "inference_s": round(t_inf, 4), "converged": int((st_s == 1).sum()),
+    plain_aps, sur_aps = n_conv_p / t_plain_job, n_conv_s / t_sur_job
+    return {
+        "workload": (f"learned-initialiser family: {n_te} held-out planets per GPU, 100 layers x {args.bins} bins x 20 g, "
+                     f"scattering, 2-table mixtures; network trained on {int(ok.sum())} converged planets "
+                     f"(the stated size is 20k planets at 3000 bins; this run is smaller so that the benchmark "
+                     f"finishes in minutes)"),
+        "unit": "atm/s", "tol": prm.tol, "multiple": round(sur_aps / plain_aps, 3),
+        "plain": {"atm_per_s": round(plain_aps, 3), "wall_s": round(t_plain, 3), "converged": int((st_p == 1).sum()),
+                  "iters_median": float(np.median(it_p)), "iters_mean": round(float(it_p.mean()), 1)},
+        "surrogate": {"atm_per_s": round(sur_aps, 3), "wall_s": round(t_sur, 3),
+                      "inference_s": round(inf["s"], 4), "converged": int((st_s == 1).sum()),
                       "iters_median": float(np.median(it_s)), "iters_mean": round(float(it_s.mean()), 1),
-                      "used_learned_start": int(used.sum())},
+                      "used_learned_start": int(np.sum(inf["used"]))},
         "initial_guess_rms_K": {"isothermal_median": round(float(np.median(rms_iso)), 2),
                                 "learned_median": round(float(np.median(rms_ml)), 2),
                                 "learned_max": round(float(rms_ml.max()), 2)},
@@ -519,6 +393,249 @@ def run_gpu_learned(args):
                      "loss_last": float(losses[-1]), "samples": int(ok.sum()), "epochs": args.epochs,
                      "mlp_tflops": round(3 * flop_fwd * n_fit / t_fit / 1e12, 4)},
     }
+
+
+# ---------------------------------------------------------------------------------------------
+# full-size single atmosphere
+# ---------------------------------------------------------------------------------------------
+def run_single(args, world, rank, local, dev, ctx=None, steps=200):
+    import torch
+    import synth
+    import paper_1606_05474_b300 as hp
+    wl = synth.config2()
+    wl.atms[0].T_init = synth.perturbed_profile(wl.atms[0], 11 + rank, amp=200.0)
+    ctx = ctx or hp.Context(local)
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(col_lanes=args.col_lanes))
+    n_passes = plan.info.passes
+    T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).to(dev)
+    T0 = T.clone()
+    state = plan.new_state()
+    Fu = torch.empty(plan.info.interfaces, dtype=torch.float64, device=dev)
+    Fd = torch.empty_like(Fu)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(warm):
+        plan.re_step(T, state, warm=warm, out=(Fu, Fd))
+
+    step(False)
+    for _ in range(max(3, args.warmup) - 1):
+        step(True)
+    torch.cuda.synchronize()
+    # (i) per step, L2 flushed before each (the flush is outside the events; the dirty warm-start
+    # lines of the previous step are written back during the flush, not inside the next step)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step(True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    flushed_ms = float(np.mean([x.elapsed_time(y) for x, y in ev]))
+    # (ii) steady state: back-to-back steps between one event pair, no flush (each step pays for
+    # its own warm-start write-back)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step(True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    steady_ms = a.elapsed_time(b) / steps
+    # (iii) the sweep kernel alone (events around the sweep launches; a separate pass, since inside
+    # the timed loops the events would split the step's chain of dependent launches)
+    plan.set_timing(steps)
+    for _ in range(steps):
+        flush.zero_()
+        step(True)
+    torch.cuda.synchronize()
+    sweep_flushed = float(np.mean(plan.sweep_times(steps)))
+    for _ in range(steps):
+        step(True)
+    torch.cuda.synchronize()
+    sweep_steady = float(np.mean(plan.sweep_times(steps)))
+    plan.set_timing(0)
+    # (iv) end to end through helios_re_step_host, the host waiting for every step's result
+    Th = torch.empty(int(plan.info.layers), dtype=torch.float64).pin_memory()
+    Th.copy_(T.cpu())
+    Sh = torch.empty(plan.A, dtype=torch.int32).pin_memory()
+    Td = torch.empty_like(T)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        plan.re_step_host(Th, Td, state, Sh, warm=True)
+        stream.synchronize()
+    e2e_ms = (time.perf_counter() - t) * 1e3 / steps
+    # the same without the copies (host waits every step): what the copies add vs the wait
+    t = time.perf_counter()
+    for _ in range(steps):
+        step(True)
+        stream.synchronize()
+    sync_ms = (time.perf_counter() - t) * 1e3 / steps
+    cells = wl.cells
+    # (v) one full radiative-equilibrium solve from the start profile (graph-captured device loop)
+    Ts = T0.clone()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    iters, status = plan.solve_re(Ts)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    solve = {"wall_s": round(dt, 4), "iters": int(iters.item()), "status": int(status.item()),
+             "atm_per_s": round(1.0 / dt, 3), "tol": 1e-7}
+
+    # (vi) the exact column solve (the limit of the passes, Sect. 2.2.3) against 1 + 4 passes, and
+    # the post-processing spectrum (isothermal layers, Sect. 3) with 1 + 80 passes against the exact
+    # solve; each sweep timed cold-start after an L2 flush
+    def time_sweeps(pl, Tt, npass, reps=20):
+        pl.flux_sweep(Tt, n_passes=npass, warm=False, want_toa=True)
+        pl.set_timing(reps)
+        for _ in range(reps):
+            flush.zero_()
+            pl.flux_sweep(Tt, n_passes=npass, warm=False, want_toa=True)
+        torch.cuda.synchronize()
+        r = round(float(np.median(pl.sweep_times(reps))), 5)
+        pl.set_timing(0)
+        return r
+    Tc = Ts.clone()
+    ms_dir, ms_pass = time_sweeps(plan, Tc, hp.DIRECT), time_sweeps(plan, Tc, n_passes)
+    pp = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(iso_layers=1))
+    pt = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(tabulate=1))
+    direct = {"sweep_ms_exact": ms_dir, "sweep_ms_passes": ms_pass, "passes": n_passes,
+              "sweep_ms_passes_tabulated_functions": time_sweeps(pt, Tc, n_passes),
+              "post_processing_spectrum_ms": {"isothermal_layers_81_passes": time_sweeps(pp, Tc, 81),
+                                              "isothermal_layers_exact": time_sweeps(pp, Tc, hp.DIRECT)}}
+    del pp, pt
+    out = {"workload": SINGLE_WORKLOAD, "cells_per_step": cells,
+           "gcell_s_l2_flushed": round(cells / (flushed_ms * 1e-3) / 1e9, 3), "ms_per_step_l2_flushed": round(flushed_ms, 5),
+           "gcell_s_steady": round(cells / (steady_ms * 1e-3) / 1e9, 3), "ms_per_step_steady": round(steady_ms, 5),
+           "sweep_ms_l2_flushed": round(sweep_flushed, 5), "sweep_ms_steady": round(sweep_steady, 5),
+           "e2e": {"value": round(cells / (e2e_ms * 1e-3) / 1e9, 3), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+                   "ms_per_step_without_copies": round(sync_ms, 4),
+                   "h2d_bytes_per_step": int(8 * plan.info.layers), "d2h_bytes_per_step": int(8 * plan.info.layers + 4),
+                   "path": "helios_re_step_host, host waits every step (wall clock)"},
+           "re_solve": solve, "exact_column_solve": direct, "passes_per_step": n_passes,
+           "l2": "flushed (256 MB write) before every step of the flushed figures"}
+    out["alg_bytes"] = sweep_bytes(plan, wl, T) if rank == 0 else None
+    del plan
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU leg: the FP64 oracle on a bounded sample of the workload, and its op counts
+# ---------------------------------------------------------------------------------------------
+def _sub_atmosphere(wl, a, l0, nb):
+    """Bins l0 .. l0+nb-1 of atmosphere a (with the matching slice of its table)."""
+    import synth
+    atm = wl.atms[a]
+    tab = wl.tables[atm.table_id]
+    st = dataclasses.replace(tab, L=nb, kappa32=np.ascontiguousarray(tab.kappa32[:, :, l0:l0 + nb, :]), kappa64=None)
+    sa = dataclasses.replace(atm, nu_edges=atm.nu_edges[l0:l0 + nb + 1].copy(), omega0=atm.omega0[l0:l0 + nb].copy(),
+                             g0=atm.g0[l0:l0 + nb].copy(), table_id=0)
+    return synth.Workload(name="sample", atms=[sa], tables=[st])
+
+
+def oracle_counts(wl, atm_ids, chunks=3, nb=8, T_of=None):
+    """FP32 and SFU instructions per cell of one flux evaluation (1 + 4 passes), from the
+    op-counting build of the oracle on chunks of nb bins spread over the spectrum of the given
+    atmospheres."""
+    from oracle import opcount
+    fp32 = sfu = cells = 0
+    for a in atm_ids:
+        L = wl.atms[a].n_bins
+        for c in range(chunks):
+            l0 = min(L - nb, (c * L) // chunks)
+            sw = _sub_atmosphere(wl, a, l0, nb)
+            T = T_of(a) if T_of else wl.atms[a].T_init
+            r = opcount.flux_evaluation(sw.atms[0], sw.tables[0], T, 1 + wl.n_scat)
+            fp32 += r["fp32"]; sfu += r["sfu"]; cells += r["cells"]
+    return {"fp32_per_cell": round(fp32 / cells, 3), "sfu_per_cell": round(sfu / cells, 3),
+            "source": f"op-counting build of the FP64 oracle (oracle/opcount.cpp) on {len(atm_ids)} atmospheres x "
+                      f"{chunks} chunks of {nb} bins ({cells} cells), 1 + {wl.n_scat} passes"}
+
+
+def cpu_baseline(wl, a=0, seconds=12.0):
+    """The FP64 oracle on the host cores: whole RE steps (flux evaluation + temperature step) of
+    atmosphere a of the workload, as many as fit in `seconds`."""
+    import oracle
+    atm = oracle.Atm.from_workload(wl, a)
+    st = oracle.State(atm, wl.atms[a].T_init)
+    p = oracle.params()
+    K = oracle.passes(atm, p)
+    cells = atm.n * atm.L * atm.G
+    t0 = time.time()
+    steps = 0
+    while True:
+        r = oracle.flux_sweep(atm, st.T, n_passes=K, warm=st.warm, warm_valid=steps > 0)
+        oracle.temp_update(atm, st, r["Fup"], r["Fdn"], p)
+        steps += 1
+        if time.time() - t0 > seconds:
+            break
+    dt = time.time() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(cells * steps / dt / 1e9, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full RE steps of atmosphere {a} of the workload ({atm.n} layers x {atm.L} bins x "
+                      f"{atm.G} g = {cells} cells each), {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------------------------
+def headline(args):
+    import torch
+    rank, world, local = dist_env()
+    init_replicas(world, local)
+    import synth
+    import paper_1606_05474_b300 as hp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    want = args.workload
+    bat = run_batched(args, world, rank, local, dev) if want in ("headline", "batched") else None
+    ctx = bat["ctx"] if bat else hp.Context(local)
+    lrn = run_learned(args, world, rank, local, dev, ctx) if want in ("headline", "learned") else None
+    sgl = run_single(args, world, rank, local, dev, ctx) if want in ("headline", "single") else None
+    if rank != 0:
+        return
+    P = peaks()
+    hbm = P.get("hbm_gbs", 6400.0)
+    sm_max = P.get("sm_max_mhz", 2032.0)
+    fp32_peak = fp32_peak_derived(local, sm_max)
+    fp32_meas, sfu_peak = hp.measure_peaks(ctx)
+    base = {"n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 sweep / f64 temperature step / bf16 MLP", "data": "synthetic"}
+    counts = cpu = None
+    if want in ("headline", "batched"):
+        wl3 = synth.config3(A=64, atm_ids=list(range(0, 4096, 64)))     # the first table pool, sampled
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(wl3, 0, seconds=args.cpu_seconds)
+            counts = oracle_counts(wl3, [0, 16, 32, 48])
+        line = {"metric": METRIC, "value": round(bat["value"], 3), "unit": UNIT,
+                "ms_per_step": round(bat["total_ms"] / args.steps, 4), **base,
+                "config": {"workload": BATCHED_WORKLOAD.format(A=bat["A"]), "cells_per_step_per_gpu": bat["cells"],
+                           "l2": "working set (151 GB) far larger than L2; no flush", "tuned": bat["tuned"],
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline(bat["sweep_ms"], bat["cells"], bat["alg_bytes"], counts, fp32_peak, sfu_peak, hbm,
+                                     measured_traffic("batched", bat["cells"]), "sweep_kernel (all launch groups)",
+                                     sm_max),
+                "e2e": bat["e2e"], "gpu_launches": bat["launches_per_step"] * args.steps, "clocks": bat["clocks"],
+                "setup_s": bat["setup_s"], "workspace_gb": bat["workspace_gb"],
+                "fp32_peak_measured_tinst_s": round(fp32_meas / 2.0, 2)}
+        if cpu:
+            line["cpu_baseline"] = cpu
+    elif want == "learned":
+        line = {"metric": METRIC, "value": lrn["surrogate"]["atm_per_s"], "unit": "atm/s", **base,
+                "config": {"workload": lrn["workload"]}}
+    else:
+        line = {"metric": METRIC, "value": sgl["gcell_s_l2_flushed"], "unit": UNIT,
+                "ms_per_step": sgl["ms_per_step_l2_flushed"], **base, "config": {"workload": SINGLE_WORKLOAD}}
+    if lrn:
+        line["surrogate_vs_plain"] = lrn
+    if sgl:
+        wl2 = synth.config2()
+        sc = oracle_counts(wl2, [0], chunks=4, nb=10, T_of=lambda a: synth.perturbed_profile(wl2.atms[0], 11, amp=200.0)) \
+            if not args.no_cpu_baseline and world == 1 else None
+        sgl["roofline_sweep_l2_flushed"] = roofline(sgl["sweep_ms_l2_flushed"], sgl["cells_per_step"], sgl.pop("alg_bytes"),
+                                                   sc, fp32_peak, sfu_peak, hbm,
+                                                   measured_traffic("single", sgl["cells_per_step"]),
+                                                   "sweep_kernel<13, 2, false, 16>", sm_max)
+        line["single_atmosphere"] = sgl
     print(json.dumps(line), flush=True)
 
 
@@ -561,13 +678,6 @@ def run_gpu_spectrum(args):
                      "sweep_ms": round(float(np.median(plan.sweep_times(args.steps))), 5)}
     if rank != 0:
         return
-    cells = plan.info.cells
-    P = peaks()
-    fp32_peak = hp.measure_peaks(ctx)[0] / 2.0           # measured, T FP32 instructions/s
-    # algorithmic FP32 instructions of the exact solve per cell: 2 sublayers x (24 for the
-    # coefficients + 14 for the three recurrences and G_up = rho G_dn + u)
-    fp32 = 2 * (24 + 14) * cells
-    achieved = fp32 / (res["exact"]["sweep_ms"] * 1e-3) / 1e12
     line = {
         "metric": "post-processing emission spectra/s (isothermal layers, exact column solve)",
         "value": round(world * 1e3 / res["exact"]["ms_per_spectrum"], 3), "unit": "spectra/s", "n_gpus": world,
@@ -575,74 +685,55 @@ def run_gpu_spectrum(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 sweep / f64 sums",
         "data": "synthetic",
         "config": {"workload": "full-size atmosphere on 100 isothermal layers x 3000 bins x 20 g, scattering, cold start",
-                   "cells": cells, "l2": "flushed before every step", "parallelism": f"replicas x{world}"},
+                   "cells": plan.info.cells, "l2": "flushed before every step", "parallelism": f"replicas x{world}"},
         "exact": res["exact"], "passes_81": res["passes_81"],
-        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-                     "unit": "T FP32 inst/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                     "kernel": "sweep_kernel<7, 2, true> (exact column solve)",
-                     "peak_source": "measured (helios_measure_peaks: independent FMA chains on every SM)"},
         "gpu_launches": 3 * 2 * args.steps,                      # prep, sweep, finalize per spectrum
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds=12.0, wl=None):
-    """The FP64 oracle on the same workload on the host cores: whole RE steps, as many as fit."""
-    import oracle
-    import synth
-    wl = wl or synth.config2()
-    atm = oracle.Atm.from_workload(wl)
-    st = oracle.State(atm, synth.perturbed_profile(wl.atms[0], 11, amp=200.0))
-    p = oracle.params()
-    K = oracle.passes(atm, p)
-    t0 = time.time()
-    steps = 0
-    while True:
-        r = oracle.flux_sweep(atm, st.T, n_passes=K, warm=st.warm, warm_valid=steps > 0)
-        oracle.temp_update(atm, st, r["Fup"], r["Fdn"], p)
-        steps += 1
-        if time.time() - t0 > seconds:
-            break
-    dt = time.time() - t0
-    v = wl.cells * steps / dt / 1e9
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full RE steps of the same atmosphere ({wl.cells} cells each), {dt:.1f} s"}
-
-
 def run_reference(args):
+    """The FP64 oracle on the host cores on the headline's workload (the batched ragged
+    atmospheres), same metric and unit: each step is one RE iteration (flux evaluation + temperature
+    step) of one atmosphere of the batch, cycling through atmospheres 0, 1, 2, ... (each with its own
+    iteration state) -- a bounded sample of the batched step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     import synth
-    wl = synth.config2()
-    atm = oracle.Atm.from_workload(wl)
-    st = oracle.State(atm, synth.perturbed_profile(wl.atms[0], 11, amp=200.0))
+    A = 8
+    wl = synth.config3(A=A, atm_ids=list(range(A)))
+    atms = [oracle.Atm.from_workload(wl, a) for a in range(A)]
+    states = [oracle.State(atm, wl.atms[a].T_init) for a, atm in enumerate(atms)]
     p = oracle.params()
-    K = oracle.passes(atm, p)
-    # a bounded sample per step: every 10th bin of the workload (300 of 3000 bins), whole column
-    sub = synth.config2(L=300)
-    satm = oracle.Atm.from_workload(sub)
-    sst = oracle.State(satm, st.T.copy())
+    done = [0] * A
+
     def one(i):
-        r = oracle.flux_sweep(satm, sst.T, n_passes=K, warm=sst.warm, warm_valid=i > 0)
-        oracle.temp_update(satm, sst, r["Fup"], r["Fdn"], p)
+        a = i % A
+        atm, st = atms[a], states[a]
+        r = oracle.flux_sweep(atm, st.T, n_passes=oracle.passes(atm, p), warm=st.warm, warm_valid=done[a] > 0)
+        oracle.temp_update(atm, st, r["Fup"], r["Fdn"], p)
+        done[a] += 1
+        return atm.n * atm.L * atm.G
+
     for i in range(args.warmup):
         one(i)
     t0 = time.time()
+    cells = 0
     for i in range(args.steps):
-        one(args.warmup + i)
+        cells += one(args.warmup + i)
     dt = time.time() - t0
-    v = sub.cells * args.steps / dt / 1e9
+    v = cells / dt / 1e9
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "300 of the 3000 bins per step (bins equal in wavenumber)"},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": BATCHED_WORKLOAD.format(A=4096),
+                       "sample": f"each step: one RE iteration of one of the batch's first {A} atmospheres, in turn"},
             "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} RE steps on 300 bins x 100 layers x 20 g"},
+                             "sample": f"{args.steps} RE iterations over atmospheres 0..{A - 1} of the batched workload "
+                                       f"({cells} cells), {dt:.1f} s"},
             "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -650,33 +741,28 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "learned", "spectrum"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "single", "batched", "learned", "spectrum"])
     ap.add_argument("--atmospheres", type=int, default=4096)
-    ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--col-lanes", type=int, default=0, choices=[0, 16, 32],
-                    help="lanes per column of the iterated sweep (16: two Gauss points per warp; 0: automatic)")
+                    help="single atmosphere: lanes per column of the iterated sweep (0: automatic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--train", type=int, default=2048, help="learned workload: training planets")
-    ap.add_argument("--test", type=int, default=512, help="learned workload: held-out planets")
-    ap.add_argument("--bins", type=int, default=300, help="learned workload: bins per planet")
-    ap.add_argument("--epochs", type=int, default=300, help="learned workload: training epochs")
+    ap.add_argument("--train", type=int, default=2048, help="surrogate vs plain: training planets per GPU")
+    ap.add_argument("--test", type=int, default=512, help="surrogate vs plain: held-out planets per GPU")
+    ap.add_argument("--bins", type=int, default=300, help="surrogate vs plain: bins per planet")
+    ap.add_argument("--epochs", type=int, default=300, help="surrogate vs plain: training epochs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batched":
-        run_gpu_batched(args)
-    elif args.workload == "learned":
-        run_gpu_learned(args)
     elif args.workload == "spectrum":
         run_gpu_spectrum(args)
     else:
-        run_gpu(args)
+        headline(args)
 
 
 if __name__ == "__main__":

@@ -288,6 +288,21 @@ int helios_re_step(helios_plan* plan, double* T_layer, int warm, double* mult, u
                    int32_t* status, int32_t* iters, double* metric, double* Fup_bol, double* Fdn_bol,
                    cudaStream_t stream);
 
+/* helios_re_step for a caller whose temperatures live in host memory: copies
+ * T_host into T_dev, makes one radiative-equilibrium iteration of every
+ * atmosphere there, and copies the new temperatures back into T_host and the
+ * statuses into status_host, all queued on `stream` (the host arrays hold the
+ * step's result once the stream has reached this point; pinned host memory
+ * makes the copies asynchronous).
+ *   T_host      host double [layers] (in/out)
+ *   T_dev       device double [layers], caller-owned scratch
+ *   status_host host int32 [A] (out)
+ *   the rest as helios_re_step (device arrays; the bolometric fluxes go to the
+ *   plan's own buffers) */
+int helios_re_step_host(helios_plan* plan, double* T_host, double* T_dev, int warm, double* mult, uint8_t* hist,
+                        uint8_t* nhist, int32_t* status, int32_t* iters, double* metric, int32_t* status_host,
+                        cudaStream_t stream);
+
 /* The radiative-equilibrium iteration (Sect. 2.2.3): flux evaluation and
  * temperature step repeated, every atmosphere dropping out when it converges,
  * until none is active or max_iter evaluations were made.  The iteration runs
@@ -322,6 +337,32 @@ int helios_mlp_grad(helios_mlp* mlp, const float* x, const float* target, int B,
 int helios_mlp_adam(helios_mlp* mlp, float lr, float beta1, float beta2, float eps, cudaStream_t stream);
 int helios_mlp_train_step(helios_mlp* mlp, const float* x, const float* target, int B, float lr, float* loss,
                           cudaStream_t stream);
+
+/* Training-data preparation of the learned initialiser: per column j of x
+ * (device float [B][n]) the mean and the population standard deviation plus
+ * eps, accumulated in double in a fixed order (helios_column_stats: mu, sd
+ * device float [n], out); and xs = (x - mu)/sd column-wise in IEEE float32
+ * (helios_standardize: xs device float [B][n], may alias x).  Asynchronous. */
+int helios_column_stats(const float* x, int B, int n, double eps, float* mu, float* sd, cudaStream_t stream);
+int helios_standardize(const float* x, const float* mu, const float* sd, int B, int n, float* xs, cudaStream_t stream);
+
+/* Start profiles of a plan's atmospheres from the learned initialiser (the
+ * iteration of Sect. 2.2.3 may start from any profile; this one is closer to
+ * equilibrium).  Per atmosphere a: its features feats[a] (device float
+ * [A][n_in], raw values) are standardised, (f - x_mu)/x_sd in IEEE float32;
+ * the network maps them to n_out standardised temperatures at evenly spaced
+ * normalised log-P positions k/(n_out - 1), bottom first; these are
+ * de-standardised, t = y * y_sd + y_mu, and interpolated linearly in log P to
+ * the atmosphere's n layer centres (evenly spaced in log P: layer i at
+ * i/(n - 1)), in double precision.  A profile with a non-finite temperature or
+ * one outside (T_min, T_max) is replaced by the atmosphere's T_fallback.
+ *   x_mu, x_sd device float [n_in]; y_mu, y_sd device float [n_out]
+ *   T_fallback, T_layer device double [layers] (T_layer: out)
+ *   used device int32 [A] (out: 1 where the network's profile was kept; may be NULL)
+ * Processes max_batch atmospheres per network pass; asynchronous on `stream`. */
+int helios_mlp_initial_profiles(helios_mlp* mlp, const helios_plan* plan, const float* feats, const float* x_mu,
+                                const float* x_sd, const float* y_mu, const float* y_sd, const double* T_fallback,
+                                double T_min, double T_max, double* T_layer, int32_t* used, cudaStream_t stream);
 
 /* Autotuner (measurement support; the paper has no counterpart): picks the work
  * item size (bins_per_item) and launch mode (persistent) for a batch by timing

@@ -105,6 +105,32 @@ def magnitude_sums(params, dims, x, t, bf16_ops=True):
     return sy, flat
 
 
+def initial_profiles(params, dims, feats, x_mu, x_sd, y_mu, y_sd, n_layers, fallback, T_min=50.0, T_max=8000.0):
+    """Start profiles from the learned initialiser: features standardised in float32 (the precision
+    in which the inputs' bfloat16 rounding is then decided), the network in FP64 on bfloat16-rounded
+    operands, de-standardised, and interpolated linearly (numpy.interp) from the outputs' evenly
+    spaced normalised log-P positions to each atmosphere's evenly spaced layer centres; an invalid
+    profile (non-finite, or outside (T_min, T_max)) is replaced by the fallback.  Returns
+    (profiles, used, network outputs in K at the output positions)."""
+    f32 = np.float32
+    xs = ((np.asarray(feats, f32) - np.asarray(x_mu, f32)) / np.asarray(x_sd, f32)).astype(np.float64)
+    y, _, _ = forward(params, dims, xs, bf16_ops=True)
+    t = y * np.asarray(x_sd_like(y_sd), np.float64) + np.asarray(y_mu, f32).astype(np.float64)
+    s_out = np.linspace(0.0, 1.0, dims[-1])
+    profiles, used = [], []
+    for i, n in enumerate(n_layers):
+        T = np.interp(np.linspace(0.0, 1.0, n), s_out, t[i])
+        ok = bool(np.all(np.isfinite(T)) and T.min() > T_min and T.max() < T_max)
+        profiles.append(T if ok else np.asarray(fallback[i], np.float64))
+        used.append(ok)
+    return profiles, np.array(used), t
+
+
+def x_sd_like(sd):
+    """The float32 statistics widened to float64 (the library stores them in float32)."""
+    return np.asarray(sd, np.float32).astype(np.float64)
+
+
 def adam(params, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam step (bias-corrected), returns new (params, m, v)."""
     m = b1 * m + (1 - b1) * grad

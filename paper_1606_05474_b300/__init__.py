@@ -316,6 +316,25 @@ class Plan:
                                       _stream_ptr(stream)))
         return state
 
+    def re_step_host(self, T_host, T_dev, state, status_host, warm=True, stream=None):
+        """helios_re_step_host: one iteration with the temperatures in host memory.  T_host: a
+        float64 CPU tensor (pinned for asynchronous copies), updated in place; T_dev: a float64
+        CUDA scratch tensor of the same size; status_host: an int32 CPU tensor of A values.  The
+        host tensors hold the result once the stream has reached this call."""
+        torch = _torch()
+        n = int(self.info.layers)
+        if not (T_host.dtype == torch.float64 and not T_host.is_cuda and T_host.is_contiguous() and T_host.numel() == n):
+            raise ValueError(f"T_host must be a contiguous float64 CPU tensor of {n} values")
+        if not (status_host.dtype == torch.int32 and not status_host.is_cuda and status_host.numel() == self.A):
+            raise ValueError(f"status_host must be an int32 CPU tensor of {self.A} values")
+        self._check_T(T_dev)
+        s = state
+        check(self.lib.helios_re_step_host(self.h, T_host.data_ptr(), T_dev.data_ptr(), 1 if warm else 0,
+                                           s["mult"].data_ptr(), s["hist"].data_ptr(), s["nhist"].data_ptr(),
+                                           s["status"].data_ptr(), _ptr(s.get("iters")), _ptr(s.get("metric")),
+                                           status_host.data_ptr(), _stream_ptr(stream)))
+        return state
+
     def solve_re(self, T, stream=None, raise_on_noconv=False):
         """Iterate to radiative equilibrium in place; returns (iters, status) CUDA tensors."""
         torch = _torch()
@@ -418,3 +437,23 @@ class MLP:
         check(self.lib.helios_mlp_train_step(self.h, x.contiguous().data_ptr(), target.contiguous().data_ptr(),
                                              x.shape[0], lr, self.loss.data_ptr(), _stream_ptr(stream)))
         return self.loss
+
+    def initial_profiles(self, plan, feats, x_mu, x_sd, y_mu, y_sd, T_fallback, T_min=50.0, T_max=8000.0, out=None,
+                         stream=None):
+        """helios_mlp_initial_profiles: start profiles of every atmosphere of `plan` (a float64 CUDA
+        tensor of plan.info.layers values) and which ones kept the network's profile (int32 [A]).
+        feats: float32 CUDA [A, n_in] (raw); x_mu, x_sd, y_mu, y_sd: float32 CUDA statistics;
+        T_fallback: float64 CUDA [layers]."""
+        torch = _torch()
+        T = out if out is not None else torch.empty(int(plan.info.layers), dtype=torch.float64, device=T_fallback.device)
+        used = torch.empty(plan.A, dtype=torch.int32, device=T_fallback.device)
+        args = [feats, x_mu, x_sd, y_mu, y_sd]
+        if any(a.dtype != torch.float32 or not a.is_cuda or not a.is_contiguous() for a in args):
+            raise ValueError("features and statistics must be contiguous float32 CUDA tensors")
+        if feats.numel() != plan.A * self.dims[0]:
+            raise ValueError(f"feats must hold {plan.A} x {self.dims[0]} values")
+        plan._check_T(T_fallback)
+        check(self.lib.helios_mlp_initial_profiles(self.h, plan.h, feats.data_ptr(), x_mu.data_ptr(), x_sd.data_ptr(),
+                                                   y_mu.data_ptr(), y_sd.data_ptr(), T_fallback.data_ptr(), T_min,
+                                                   T_max, T.data_ptr(), used.data_ptr(), _stream_ptr(stream)))
+        return T, used

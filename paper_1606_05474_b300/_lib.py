@@ -45,10 +45,11 @@ class PlanInfo(ctypes.Structure):
 
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
-           "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_solve_re", "helios_measure_peaks", "helios_device_recip", "helios_plan_set_timing",
+           "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_re_step_host", "helios_solve_re", "helios_measure_peaks", "helios_device_recip", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
            "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_forward",
-           "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step"]
+           "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step", "helios_mlp_initial_profiles",
+           "helios_column_stats", "helios_standardize"]
 
 _lib = None
 
@@ -76,6 +77,7 @@ def load(path: str = SO_PATH):
     lib.helios_flux_sweep.argtypes = [vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]
     lib.helios_temp_update.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_re_step.argtypes = [vp, vp, c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.helios_re_step_host.argtypes = [vp, vp, vp, c_int, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.helios_measure_peaks.argtypes = [vp, P(c_double), P(c_double)]
     lib.helios_device_recip.argtypes = [vp, vp, c_int, vp]
     lib.helios_solve_re.argtypes = [vp, vp, vp, vp, vp]
@@ -90,6 +92,9 @@ def load(path: str = SO_PATH):
     lib.helios_mlp_grad.argtypes = [vp, vp, vp, c_int, vp, vp]
     lib.helios_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
     lib.helios_mlp_train_step.argtypes = [vp, vp, vp, c_int, ctypes.c_float, vp, vp]
+    lib.helios_mlp_initial_profiles.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, c_double, c_double, vp, vp, vp]
+    lib.helios_column_stats.argtypes = [vp, c_int, c_int, c_double, vp, vp, vp]
+    lib.helios_standardize.argtypes = [vp, vp, vp, c_int, c_int, vp, vp]
     lib.helios_flux_sweep_noalloc.argtypes = [P(Batch), P(KTable), P(Params), vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("helios_default_params", "helios_version", "helios_last_error"):

@@ -243,6 +243,7 @@ struct helios_plan {
     int A, G, TB, passes, max_n;
     int64_t layers, interfaces, points, subs, bins, items, cells;
     int64_t ws_bytes;
+    int2* lay_nl;           // device [A]: (layers, first layer) of each atmosphere
     int64_t warm_floats;    // floats of the warm-start block (all atmospheres)
     int64_t spec_floats;    // floats of the optional per-bin flux output [bins][2][points]
     std::vector<AtmDesc> atms_h;
@@ -270,6 +271,13 @@ struct helios_plan {
 };
 
 __attribute__((visibility("hidden"))) int helios_ctx_device(const helios_ctx* c) { return c->device; }
+
+// per atmosphere (layers, offset of its first layer) on the device, for the learned initialiser
+__attribute__((visibility("hidden"))) const int2* helios_plan_layers_dev(const helios_plan* p, int* A)
+{
+    *A = p->A;
+    return p->lay_nl;
+}
 
 extern "C" {
 
@@ -689,6 +697,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     ALLOC(P->Fup, ifc); ALLOC(P->Fdn, ifc); ALLOC(P->mult, lay); ALLOC(P->hist, lay); ALLOC(P->nhist, lay);
     ALLOC(P->n_active, 1); ALLOC(P->chunks_left, 1);
     ALLOC(P->counters, 2 * kGroups);
+    ALLOC(P->lay_nl, A);
     float *d_btab = nullptr, *d_utab = nullptr;
     if (prm->tabulate) {
         ALLOC(d_btab, btab.size());
@@ -737,6 +746,14 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         (prm->tabulate && ((rc = upload(d_btab, btab)) || (rc = upload(d_utab, utab))))) {
         helios_plan_destroy(P);
         return rc;
+    }
+    {
+        std::vector<int2> nl(A);
+        for (int a = 0; a < A; ++a) nl[a] = make_int2(ad[a].n, ad[a].lay_off);
+        if ((rc = upload(P->lay_nl, nl))) {
+            helios_plan_destroy(P);
+            return rc;
+        }
     }
     cudaError_t ce = cudaMemset(dv.warm, 0, std::max<int64_t>(warm, 1) * sizeof(float));
     if (ce == cudaSuccess) ce = cudaMemset(P->counters, 0, sizeof(int) * 2 * kGroups);   // the sweeps keep them at 0
@@ -1079,6 +1096,21 @@ int helios_re_step(helios_plan* p, double* T_layer, int warm, double* mult, uint
     if (!rc) rc = launch_post(p, nullptr, Fu, Fd, T_layer, mult, hist, nhist, status, iters, metric, nullptr, 0, 0, s);
     if (rc) return rc;
     p->warm_ready = true;
+    return HELIOS_OK;
+}
+
+int helios_re_step_host(helios_plan* p, double* T_host, double* T_dev, int warm, double* mult, uint8_t* hist,
+                        uint8_t* nhist, int32_t* status, int32_t* iters, double* metric, int32_t* status_host,
+                        cudaStream_t s)
+{
+    if (!p || !T_host || !T_dev || !status_host) return fail(HELIOS_EINVAL, "helios_re_step_host: null argument");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    const size_t tb = sizeof(double) * (size_t)p->layers;
+    CUDA_TRY(cudaMemcpyAsync(T_dev, T_host, tb, cudaMemcpyHostToDevice, s));
+    const int rc = helios_re_step(p, T_dev, warm, mult, hist, nhist, status, iters, metric, nullptr, nullptr, s);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(T_host, T_dev, tb, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(status_host, status, sizeof(int32_t) * (size_t)p->A, cudaMemcpyDeviceToHost, s));
     return HELIOS_OK;
 }
 

@@ -21,6 +21,7 @@
 
 __attribute__((visibility("hidden"))) void helios_set_error_text(const char* msg);
 __attribute__((visibility("hidden"))) int helios_ctx_device(const helios_ctx* ctx);
+__attribute__((visibility("hidden"))) const int2* helios_plan_layers_dev(const helios_plan* p, int* A);
 
 namespace {
 
@@ -208,6 +209,84 @@ uint64_t mix64(uint64_t z)
 
 }  // namespace
 
+// standardised features: xs[b][j] = (f[b][j] - mu[j]) / sd[j] in IEEE float32 (correctly rounded)
+__global__ void standardize_kernel(const float* __restrict__ f, const float* __restrict__ mu, const float* __restrict__ sd,
+                                   float* __restrict__ xs, int B, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < B * n) {
+        const int j = i % n;
+        xs[i] = __fdiv_rn(__fsub_rn(f[i], mu[j]), sd[j]);
+    }
+}
+
+// column j = blockIdx.x of x [B][n]: mean and standard deviation (population) in double, fixed-order
+// sums (thread-strided partials, then a fixed tree over the block), sd + eps stored
+__global__ void column_stats_kernel(const float* __restrict__ x, int B, int n, double eps, float* __restrict__ mu,
+                                    float* __restrict__ sd)
+{
+    __shared__ double red[256];
+    const int j = blockIdx.x, t = threadIdx.x;
+    double s = 0.0;
+    for (int b = t; b < B; b += 256) s += (double)x[(size_t)b * n + j];
+    red[t] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    const double m = red[0] / (double)B;
+    __syncthreads();
+    double q = 0.0;
+    for (int b = t; b < B; b += 256) {
+        const double d = (double)x[(size_t)b * n + j] - m;
+        q += d * d;
+    }
+    red[t] = q;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        mu[j] = (float)m;
+        sd[j] = (float)(sqrt(red[0] / (double)B) + eps);
+    }
+}
+
+// one block per atmosphere a0 + blockIdx.x: the network's n_out standardised temperatures at the
+// evenly spaced normalised log-P positions s_k = k/(n_out - 1) (bottom first), de-standardised and
+// interpolated linearly to the atmosphere's n layer centres (evenly spaced in log P: s_i = i/(n-1));
+// a profile with a non-finite temperature or one outside (T_min, T_max) takes the fallback
+__global__ void profile_kernel(const int2* __restrict__ lay, int a0, const float* __restrict__ y, int n_out,
+                               const float* __restrict__ y_mu, const float* __restrict__ y_sd,
+                               const double* __restrict__ T_fb, double T_min, double T_max, double* __restrict__ T_out,
+                               int32_t* __restrict__ used)
+{
+    __shared__ int s_bad;
+    const int a = a0 + blockIdx.x;
+    const int2 nl = lay[a];
+    const int n = nl.x, off = nl.y;
+    const float* yr = y + (size_t)blockIdx.x * n_out;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double pos = n > 1 ? (double)i * (double)(n_out - 1) / (double)(n - 1) : 0.0;
+        const int k = min((int)floor(pos), n_out - 2);
+        const double w = pos - (double)k;
+        const double t0 = (double)yr[k] * (double)y_sd[k] + (double)y_mu[k];
+        const double t1 = (double)yr[k + 1] * (double)y_sd[k + 1] + (double)y_mu[k + 1];
+        const double T = t0 + w * (t1 - t0);
+        if (!(T > T_min && T < T_max)) atomicOr(&s_bad, 1);      // also catches NaN
+        T_out[off + i] = T;
+    }
+    __syncthreads();
+    const int bad = s_bad;
+    if (bad)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) T_out[off + i] = T_fb[off + i];
+    if (threadIdx.x == 0 && used) used[a] = bad ? 0 : 1;
+}
+
 struct helios_mlp {
     helios_ctx* ctx;
     int device;
@@ -219,6 +298,7 @@ struct helios_mlp {
     float* act;              // per layer: Z (hidden layers) and Y, max_B rows
     float *dA, *dB;          // backprop ping-pong buffers
     float* dout;
+    float *xin, *yout;       // initial profiles: standardised features and network outputs, max_B rows
     double* part;
     int64_t t;               // Adam step count
     std::vector<void*> allocs;
@@ -281,6 +361,10 @@ int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers
     m->allocs.push_back(m->dout);
     if (cudaMalloc((void**)&m->part, sizeof(double) * 1024) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp loss"); }
     m->allocs.push_back(m->part);
+    if (cudaMalloc((void**)&m->xin, sizeof(float) * (size_t)max_batch * n_in) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp inputs"); }
+    m->allocs.push_back(m->xin);
+    if (cudaMalloc((void**)&m->yout, sizeof(float) * (size_t)max_batch * n_out) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp outputs"); }
+    m->allocs.push_back(m->yout);
     MLP_CUDA(cudaMemcpy(m->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice));
     MLP_CUDA(cudaMemset(m->m, 0, sizeof(float) * off));
     MLP_CUDA(cudaMemset(m->v, 0, sizeof(float) * off));
@@ -410,6 +494,50 @@ int helios_mlp_adam(helios_mlp* m, float lr, float beta1, float beta2, float eps
     const float c2 = (float)(1.0 - std::pow((double)beta2, (double)m->t));
     adam_kernel<<<256, 256, 0, s>>>(m->p, m->g, m->m, m->v, m->n_params, lr, beta1, beta2, eps, c1, c2);
     MLP_CUDA(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+int helios_column_stats(const float* x, int B, int n, double eps, float* mu, float* sd, cudaStream_t s)
+{
+    if (!x || !mu || !sd) return mfail(HELIOS_EINVAL, "helios_column_stats: null argument");
+    if (B < 1 || n < 1) return mfail(HELIOS_EINVAL, "helios_column_stats: %d x %d values", B, n);
+    column_stats_kernel<<<n, 256, 0, s>>>(x, B, n, eps, mu, sd);
+    MLP_CUDA(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+int helios_standardize(const float* x, const float* mu, const float* sd, int B, int n, float* xs, cudaStream_t s)
+{
+    if (!x || !mu || !sd || !xs) return mfail(HELIOS_EINVAL, "helios_standardize: null argument");
+    if (B < 0 || n < 1) return mfail(HELIOS_EINVAL, "helios_standardize: %d x %d values", B, n);
+    if (B == 0) return HELIOS_OK;
+    const long long total = (long long)B * n;
+    if (total > (1LL << 31) - 256) return mfail(HELIOS_EINVAL, "helios_standardize: too many values");
+    standardize_kernel<<<(int)((total + 255) / 256), 256, 0, s>>>(x, mu, sd, xs, B, n);
+    MLP_CUDA(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+int helios_mlp_initial_profiles(helios_mlp* m, const helios_plan* plan, const float* feats, const float* x_mu,
+                                const float* x_sd, const float* y_mu, const float* y_sd, const double* T_fallback,
+                                double T_min, double T_max, double* T_layer, int32_t* used, cudaStream_t s)
+{
+    if (!m || !plan || !feats || !x_mu || !x_sd || !y_mu || !y_sd || !T_fallback || !T_layer)
+        return mfail(HELIOS_EINVAL, "helios_mlp_initial_profiles: null argument");
+    if (m->dims[m->nl] < 2) return mfail(HELIOS_EINVAL, "helios_mlp_initial_profiles: the network has fewer than 2 outputs");
+    int A = 0;
+    const int2* lay = helios_plan_layers_dev(plan, &A);
+    MLP_CUDA(cudaSetDevice(m->device));
+    const int n_in = m->dims[0], n_out = m->dims[m->nl];
+    for (int a0 = 0; a0 < A; a0 += m->max_B) {
+        const int B = std::min(m->max_B, A - a0);
+        standardize_kernel<<<(B * n_in + 255) / 256, 256, 0, s>>>(feats + (size_t)a0 * n_in, x_mu, x_sd, m->xin, B, n_in);
+        MLP_CUDA(cudaGetLastError());
+        const int rc = forward(m, m->xin, m->yout, B, s);
+        if (rc) return rc;
+        profile_kernel<<<B, 128, 0, s>>>(lay, a0, m->yout, n_out, y_mu, y_sd, T_fallback, T_min, T_max, T_layer, used);
+        MLP_CUDA(cudaGetLastError());
+    }
     return HELIOS_OK;
 }
 

@@ -5,15 +5,44 @@ needs depends on how far that start is from equilibrium.  This module maps six p
 parameters (T_irr, T_int, log10 g, [M/H], C/O, log10 of the mean opacity) to a 100-point
 temperature profile (bottom to top, evenly spaced in log P over the model's range) with the
 library's MLP (BF16 tensor-core products, FP32 accumulation, trained with Adam on the solver's
-own converged solutions), interpolates it to each atmosphere's layers and validates it; an
-invalid prediction falls back to the isothermal start, and the plain iteration still decides
-every result (the solver iterates to eq. 29 from the predicted start).
+own converged solutions).  Every arithmetic step runs in the library: the training data's
+statistics and standardisation (helios_column_stats, helios_standardize), training
+(helios_mlp_train_step) and the start profiles (helios_mlp_initial_profiles: standardisation,
+the network, de-standardisation, interpolation in log P to each atmosphere's layers, and the
+fallback to the isothermal start for an invalid prediction).  The plain iteration still decides
+every result: the solver iterates to eq. (29) from the predicted start.
 """
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 
-from . import MLP, Context, _torch
+from . import MLP, Context, _ptr, _stream_ptr, _torch, check
+
+
+def column_stats(x, eps, stream=None):
+    """(mu, sd + eps) of every column of a float32 CUDA tensor [B, n] (helios_column_stats)."""
+    torch = _torch()
+    x = x.contiguous()
+    B, n = x.shape
+    mu = torch.empty(n, dtype=torch.float32, device=x.device)
+    sd = torch.empty(n, dtype=torch.float32, device=x.device)
+    from . import _lib
+    check(_lib.load().helios_column_stats(x.data_ptr(), B, n, float(eps), mu.data_ptr(), sd.data_ptr(),
+                                          _stream_ptr(stream)))
+    return mu, sd
+
+
+def standardize(x, mu, sd, stream=None):
+    """(x - mu) / sd column-wise in float32 (helios_standardize); a new tensor."""
+    torch = _torch()
+    x = x.contiguous()
+    out = torch.empty_like(x)
+    from . import _lib
+    check(_lib.load().helios_standardize(x.data_ptr(), mu.data_ptr(), sd.data_ptr(), x.shape[0], x.shape[1],
+                                         out.data_ptr(), _stream_ptr(stream)))
+    return out
 
 
 class LearnedInitializer:
@@ -23,19 +52,20 @@ class LearnedInitializer:
                        max_batch=max_batch)
         self.n_points = n_points
         self.dev = self.net.params.device
-        self.x_mu = self.x_sd = self.y_mu = self.y_sd = None
+        self.x_mu = self.x_sd = self.y_mu = self.y_sd = None     # float32 CUDA tensors after fit()
 
     # ---- training
     def fit(self, feats: np.ndarray, profiles: np.ndarray, epochs: int = 300, batch: int = 256, lr: float = 1e-3,
             seed: int = 0, lr_final: float = 1e-5):
-        """Train on (features [N, 6], converged profiles [N, n_points] in K); returns the loss per epoch."""
+        """Train on (features [N, 6], converged profiles [N, n_points] in K); returns the loss per epoch.
+        The statistics and the standardised data are formed on the device by the library; the
+        host only draws the epoch's order of the samples."""
         torch = _torch()
-        feats = np.asarray(feats, np.float64)
-        prof = np.asarray(profiles, np.float64)
-        self.x_mu, self.x_sd = feats.mean(0), feats.std(0) + 1e-12
-        self.y_mu, self.y_sd = prof.mean(0), prof.std(0) + 1e-6
-        X = torch.from_numpy(((feats - self.x_mu) / self.x_sd).astype(np.float32)).to(self.dev)
-        Y = torch.from_numpy(((prof - self.y_mu) / self.y_sd).astype(np.float32)).to(self.dev)
+        F = torch.from_numpy(np.asarray(feats, np.float32)).to(self.dev)
+        Yk = torch.from_numpy(np.asarray(profiles, np.float32)).to(self.dev)
+        self.x_mu, self.x_sd = column_stats(F, 1e-12)
+        self.y_mu, self.y_sd = column_stats(Yk, 1e-6)
+        X, Y = standardize(F, self.x_mu, self.x_sd), standardize(Yk, self.y_mu, self.y_sd)
         n = X.shape[0]
         rng = np.random.default_rng(seed)
         batch = min(batch, n, self.net.max_batch)
@@ -55,28 +85,24 @@ class LearnedInitializer:
         return losses
 
     # ---- inference
-    def predict(self, feats: np.ndarray) -> np.ndarray:
-        """Profiles [N, n_points] in K (bottom first) for features [N, 6]."""
-        torch = _torch()
-        X = torch.from_numpy(((np.asarray(feats, np.float64) - self.x_mu) / self.x_sd).astype(np.float32)).to(self.dev)
-        out = []
-        for s in range(0, X.shape[0], self.net.max_batch):
-            out.append(self.net.forward(X[s:s + self.net.max_batch]).double().cpu().numpy())
-        return np.concatenate(out) * self.y_sd + self.y_mu
+    def statistics(self):
+        """The standardisation statistics (x_mu, x_sd, y_mu, y_sd), float32 CUDA tensors."""
+        return self.x_mu, self.x_sd, self.y_mu, self.y_sd
 
-    def initial_profiles(self, feats, n_layers, fallback, T_min=50.0, T_max=8000.0):
-        """Start profiles for atmospheres of n_layers[i] layers: the predicted profile interpolated
-        linearly in the normalised log-P coordinate, or fallback[i] (the isothermal start) when the
-        prediction is not finite or leaves [T_min, T_max].  Returns (profiles, used_prediction)."""
-        pred = self.predict(feats)
-        s_out = np.linspace(0.0, 1.0, self.n_points)
-        profiles, used = [], []
-        for i, n in enumerate(n_layers):
-            T = np.interp(np.linspace(0.0, 1.0, n), s_out, pred[i])
-            ok = bool(np.all(np.isfinite(T)) and T.min() > T_min and T.max() < T_max)
-            profiles.append(T if ok else np.asarray(fallback[i], np.float64))
-            used.append(ok)
-        return profiles, np.array(used)
+    def initial_profiles_device(self, plan, feats, fallback, T_min=50.0, T_max=8000.0):
+        """Start profiles for every atmosphere of `plan` (helios_mlp_initial_profiles), with
+        `fallback` (the isothermal start) where the prediction is invalid.  Returns (T float64 CUDA
+        tensor of the plan's layers, used: numpy bool [A])."""
+        torch = _torch()
+        f = torch.from_numpy(np.asarray(feats, np.float32)).to(self.dev)
+        fb = torch.from_numpy(np.concatenate([np.asarray(x, np.float64) for x in fallback])).to(self.dev)
+        T, used = self.net.initial_profiles(plan, f, *self.statistics(), fb, T_min=T_min, T_max=T_max)
+        return T, used.cpu().numpy().astype(bool)
+
+    def initial_profiles(self, plan, feats, fallback, T_min=50.0, T_max=8000.0):
+        """The same start profiles as a list of numpy arrays (one per atmosphere) and `used`."""
+        T, used = self.initial_profiles_device(plan, feats, fallback, T_min, T_max)
+        return plan.split_layers(T.cpu().numpy()), used
 
 
 def features(atms) -> np.ndarray:

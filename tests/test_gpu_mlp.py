@@ -110,14 +110,14 @@ def test_learned_initializer_saves_iterations_and_reaches_the_same_equilibrium()
     losses = init.fit(X[tr], Tc[tr], epochs=300, batch=128, lr=2e-3)
     assert losses[-1] < 0.1 * losses[0]
     test_atms = [wl.atms[i] for i in te]
-    starts, used = init.initial_profiles(X[te], [a.n_layers for a in test_atms], [a.T_init for a in test_atms])
+    test_wl = synth.Workload(name="held-out", atms=test_atms, tables=wl.tables, n_scat=4)
+    p2 = make_plan(test_wl, max_iter=20000)
+    starts, used = init.initial_profiles(p2, X[te], [a.T_init for a in test_atms])
     assert used.all()
     # the learned start is much closer to the converged profile than the isothermal one
     rms_iso = np.sqrt(((T0[te] - Tc[te]) ** 2).mean(axis=1))
     rms_ml = np.sqrt(((np.array(starts) - Tc[te]) ** 2).mean(axis=1))
     assert np.median(rms_ml) < 0.5 * np.median(rms_iso)
-    test_wl = synth.Workload(name="held-out", atms=test_atms, tables=wl.tables, n_scat=4)
-    p2 = make_plan(test_wl, max_iter=20000)
     T2 = pack(starts)
     it2, st2 = p2.solve_re(T2)
     assert (st2.cpu().numpy() == 1).mean() > 0.95
@@ -146,3 +146,70 @@ def test_learned_initializer_saves_iterations_and_reaches_the_same_equilibrium()
     # fewer iterations on average; the step law of eqs. (24)-(28) makes a step's size depend on
     # the flux imbalance only as its 0.1 power, so a closer start saves a modest fraction
     assert it2.cpu().numpy()[ok].mean() < it_plain[te][ok].mean()
+
+
+def test_column_statistics_and_standardisation():
+    # the training data's statistics: mean and population standard deviation per column
+    import torch
+    from paper_1606_05474_b300.learned import column_stats, standardize
+    rng = np.random.default_rng(7)
+    x = (rng.normal(size=(777, 9)) * rng.uniform(0.1, 300, 9) + rng.uniform(-500, 500, 9)).astype(np.float32)
+    X = torch.from_numpy(x).cuda()
+    mu, sd = column_stats(X, 1e-6)
+    x64 = x.astype(np.float64)
+    np.testing.assert_allclose(mu.cpu().numpy(), x64.mean(0).astype(np.float32), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(sd.cpu().numpy(), (x64.std(0) + 1e-6).astype(np.float32), rtol=1e-6)
+    xs = standardize(X, mu, sd).cpu().numpy()
+    m32, s32 = mu.cpu().numpy(), sd.cpu().numpy()
+    assert np.array_equal(xs, (x - m32) / s32)              # IEEE float32, element by element
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_initial_profiles_match_oracle(split):
+    # standardisation, network, de-standardisation, interpolation in log P to each atmosphere's
+    # layers, and the fallback, in the library, against the oracle's restatement; ragged layer
+    # counts (a plan of atmospheres with 2 to 239 layers), more atmospheres than one network pass
+    import torch
+    import synth
+    from helpers import make_plan
+    ns = [2, 30, 57, 100, 120, 239, 77, 64]
+    wls = [synth.small_scattering(L=3, n=n) for n in ns]
+    wl = synth.Workload(name="ragged", atms=[w.atms[0] for w in wls], tables=[wls[0].tables[0]], n_scat=4)
+    plan = make_plan(wl)
+    net = _net(5, seed=3)                     # max_batch 5 < 8 atmospheres: two network passes
+    rng = np.random.default_rng(11)
+    feats = rng.normal(size=(len(ns), 6)) * 50 + 100
+    x_mu, x_sd = rng.normal(size=6) * 50 + 100, rng.uniform(20, 80, 6)
+    y_mu, y_sd = np.linspace(1400, 900, 100), np.linspace(150, 40, 100)
+    fb = [np.full(n, 1000.0 + 10 * i) for i, n in enumerate(ns)]
+    f32 = lambda v: torch.from_numpy(np.asarray(v, np.float32)).cuda()
+    p = net.params.double().cpu().numpy()
+    T_max = 8000.0
+    if split:
+        # an upper bound between two atmospheres' hottest layers (from the oracle's profiles), far
+        # from both, so that some profiles are kept and the others fall back
+        prof0, _, _ = omlp.initial_profiles(p, DIMS, feats, x_mu, x_sd, y_mu, y_sd, ns, fb, 50.0, 1e9)
+        hot = np.sort([q.max() for q in prof0])
+        gaps = np.diff(hot)
+        j = int(np.argmax(gaps[1:-1])) + 1
+        assert gaps[j] > 2.0
+        T_max = 0.5 * (hot[j] + hot[j + 1])
+    T, used = net.initial_profiles(plan, f32(feats), f32(x_mu), f32(x_sd), f32(y_mu), f32(y_sd),
+                                   torch.from_numpy(np.concatenate(fb)).cuda(), T_min=50.0, T_max=T_max)
+    Tg = plan.split_layers(T.cpu().numpy())
+    prof, ok, t = omlp.initial_profiles(p, DIMS, feats, x_mu, x_sd, y_mu, y_sd, ns, fb, 50.0, T_max)
+    assert np.array_equal(used.cpu().numpy().astype(bool), ok)
+    xs = ((feats.astype(np.float32) - x_mu.astype(np.float32)) / x_sd.astype(np.float32)).astype(np.float64)
+    sy, _ = omlp.magnitude_sums(p, DIMS, xs, np.zeros((len(ns), 100)))
+    scale = sy * np.asarray(y_sd, np.float32)               # each output's scale in kelvin
+    for i, n in enumerate(ns):
+        if not ok[i]:
+            assert np.array_equal(Tg[i], fb[i])
+            continue
+        # element-wise: within 2^-7 of the larger scale of the two outputs a layer lies between
+        s_out, s_in = np.linspace(0, 1, 100), np.linspace(0, 1, n)
+        k = np.minimum(np.floor(s_in * 99).astype(int), 98)
+        tol = 2.0 ** -7 * np.maximum(scale[i, k], scale[i, k + 1]) + 1e-9 * np.abs(prof[i])
+        assert np.all(np.abs(Tg[i] - prof[i]) <= tol), np.max(np.abs(Tg[i] - prof[i]) / tol)
+    if split:
+        assert 0 < ok.sum() < len(ns)         # both the network's profile and the fallback occur

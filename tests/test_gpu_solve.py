@@ -216,6 +216,25 @@ def test_re_step_equals_sweep_plus_temperature_update_bitwise():
             assert bool((sa[key] == sb[key]).all()), key
 
 
+def test_re_step_with_host_temperatures_equals_re_step_bitwise():
+    # helios_re_step_host: host temperatures in, new temperatures and statuses out, the same step
+    import torch
+    wl = _small_ragged([3, 20, 41], max_bins=16)
+    T0 = [synth.perturbed_profile(a, i) for i, a in enumerate(wl.atms)]
+    pa, pb = make_plan(wl), make_plan(wl)
+    Ta = pack(T0)
+    Th = torch.from_numpy(np.concatenate(T0)).pin_memory()
+    Td = torch.empty_like(Ta)
+    Sh = torch.zeros(pb.A, dtype=torch.int32).pin_memory()
+    sa, sb = pa.new_state(), pb.new_state()
+    for k in range(4):
+        pa.re_step(Ta, sa, warm=k > 0)
+        pb.re_step_host(Th, Td, sb, Sh, warm=k > 0)
+        torch.cuda.synchronize()
+        assert np.array_equal(Th.numpy(), Ta.cpu().numpy())
+        assert np.array_equal(Sh.numpy(), sa["status"].cpu().numpy())
+
+
 def test_solve_equals_a_loop_of_re_steps():
     # helios_solve_re (graph loop; the next step's point quantities prepared by the post kernel)
     # and a host loop of helios_re_step reach the same temperatures in the same number of steps
