@@ -639,6 +639,34 @@ def headline(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """A short run for profilers: the chosen workload's plan, W warm-up and K timed RE steps
+    through helios_re_step, nothing else (no extra sections, no CPU leg)."""
+    import torch
+    import synth
+    import paper_1606_05474_b300 as hp
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.workload == "batched":
+        wl = synth.config3(A=args.atmospheres, atm_ids=list(range(args.atmospheres)))
+    else:
+        wl = synth.config2()
+        wl.atms[0].T_init = synth.perturbed_profile(wl.atms[0], 11, amp=200.0)
+    ctx = hp.Context(0)
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    prm = hp.default_params(col_lanes=args.col_lanes)
+    if args.workload == "batched":
+        prm = hp.autotune(ctx, wl.atms, wl.tables, kap, prm)
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, prm)
+    T = torch.from_numpy(np.concatenate([a.T_init for a in wl.atms])).to(dev)
+    state = plan.new_state()
+    for k in range(args.warmup + args.steps):
+        plan.re_step(T, state, warm=k > 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": args.workload, "steps": args.steps, "warmup": args.warmup,
+                      "atmospheres": len(wl.atms), "sweep_launches_per_step": plan.info.sweep_launches}))
+
+
 def run_gpu_spectrum(args):
     """Post-processing emission spectrum (Sect. 3): the full-size atmosphere (100 layers x 3000
     bins x 20 g, scattering) on isothermal layers, from a cold start, with 1 + 80 scattering
@@ -754,11 +782,15 @@ def main():
     ap.add_argument("--test", type=int, default=512, help="surrogate vs plain: held-out planets per GPU")
     ap.add_argument("--bins", type=int, default=300, help="surrogate vs plain: bins per planet")
     ap.add_argument("--epochs", type=int, default=300, help="surrogate vs plain: training epochs")
+    ap.add_argument("--profile", action="store_true",
+                    help="a short run for profilers: warm-up + timed RE steps of the workload, nothing else")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
     elif args.workload == "spectrum":
         run_gpu_spectrum(args)
     else:

@@ -401,13 +401,15 @@ int helios_device_recip(const float* x, float* y, int n, cudaStream_t stream);
  *   T_layer device double [n]; Fup_bol, Fdn_bol device double [n+1];
  *   Fup_toa device float [L] or NULL; n_passes as in helios_flux_sweep.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Atmospheres
- * that do not fit (n_layers > 239, n_bins > 8192, G > 20, or more than 64 MiB of
- * scratch) are rejected with HELIOS_EINVAL before any GPU work.  All calls share
- * the array and each call rewrites it entirely before reading it; calls whose GPU
- * work overlaps (different streams or host threads without ordering) race on it.
- * Results are identical in value to helios_flux_sweep with warm = 0 up to the
- * order of the final FP64 sums. */
+ * device current).  The call stages its inputs through static host arrays with
+ * pageable copies, so it cannot be captured in a CUDA graph: on a stream that is
+ * capturing it returns HELIOS_EINVAL without queueing work.  Atmospheres beyond
+ * n_layers 239, n_bins 8192 or G 20 are rejected with HELIOS_EINVAL before any GPU
+ * work; every atmosphere within those limits fits (no warm start is kept).  All
+ * calls share the array and each call rewrites it entirely before reading it;
+ * calls whose GPU work overlaps (different streams or host threads without
+ * ordering) race on it.  The host set-up is the plan's own; results equal
+ * helios_flux_sweep with warm = 0 up to the order of the final FP64 sums. */
 int helios_flux_sweep_noalloc(const helios_batch_t* batch, const helios_ktable_t* table,
                               const helios_params_t* params, const double* T_layer, int n_passes,
                               double* Fup_bol, double* Fdn_bol, float* Fup_toa, cudaStream_t stream);

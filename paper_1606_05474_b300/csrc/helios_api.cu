@@ -13,18 +13,12 @@
 #include <utility>
 #include <vector>
 
+#include "helios_setup.h"
+
 using namespace helios_dev;
+using namespace helios_setup;
 
 namespace {
-
-// CODATA 2018, CGS
-constexpr double kB = 1.380649e-16;
-constexpr double hP = 6.62607015e-27;
-constexpr double cL = 2.99792458e10;
-constexpr double sigmaSB = 5.670374419e-5;
-constexpr double kPi = 3.14159265358979323846;
-constexpr double mProton = 1.67262192369e-24;
-constexpr double mbarMp = 2.4;        // mean molecular mass in proton masses (Sect. 2.2.1)
 
 thread_local std::string g_err;
 
@@ -57,56 +51,6 @@ int lane_chunk(int n, int cl = 32)
     return m;
 }
 
-// IEEE double table coordinate, same formula as the device code (no contraction:
-// this file is compiled with -ffp-contract=off for the host).
-void host_table_coord(double x, double x0, double dx, int nx, int& i, double& w)
-{
-    if (nx < 2) { i = 0; w = 0.0; return; }
-    double u = (x - x0) / dx;
-    if (!(u > 0.0)) i = 0;
-    else if (u >= (double)(nx - 2)) i = nx - 2;
-    else i = (int)std::floor(u);
-    double t = (x - (x0 + (double)i * dx)) / dx;
-    if (!(t > 0.0)) t = 0.0;
-    if (t > 1.0) t = 1.0;
-    w = t;
-}
-
-// Gauss-Legendre nodes/weights on [-1, 1] (eqs. 31-32): Newton iteration on P_G in long
-// double from Tricomi's initial approximation, w = 2 / ((1 - y^2) P_G'(y)^2).
-void gauss_legendre(int G, std::vector<double>& y, std::vector<double>& w)
-{
-    y.assign(G, 0.0);
-    w.assign(G, 0.0);
-    if (G == 1) { w[0] = 2.0; return; }
-    for (int k = 1; k <= G; ++k) {
-        long double th = kPi * (4.0L * k - 1.0L) / (4.0L * G + 2.0L);
-        long double x = (1.0L - (G - 1.0L) / (8.0L * G * G * G)) * cosl(th);
-        long double dP = 1.0L;
-        for (int it = 0; it < 60; ++it) {
-            long double pm = 1.0L, pc = x;
-            for (int j = 2; j <= G; ++j) {
-                long double pn = ((2.0L * j - 1.0L) * x * pc - (j - 1.0L) * pm) / j;
-                pm = pc;
-                pc = pn;
-            }
-            dP = G * (pm - x * pc) / (1.0L - x * x);
-            long double dx = pc / dP;
-            x -= dx;
-            if (fabsl(dx) < 1e-19L) break;
-        }
-        y[G - k] = (double)x;
-        w[G - k] = (double)(2.0L / ((1.0L - x * x) * dP * dP));
-    }
-}
-
-// Planck intensity of a wavenumber bin at its centre, times the bin width (per steradian).
-double planck_bin(double nu_lo, double nu_hi, double T)
-{
-    if (!(T > 0.0)) return 0.0;
-    const double nu = 0.5 * (nu_lo + nu_hi), dnu = nu_hi - nu_lo;
-    return 2.0 * hP * cL * cL * nu * nu * nu * dnu / std::expm1(hP * cL * nu / (kB * T));
-}
 
 template <typename T>
 int dev_alloc(T** p, size_t count, size_t& total)
@@ -534,28 +478,10 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     std::vector<float> dm(sub);
     for (int a = 0; a < A; ++a) {
         const AtmDesc& d = ad[a];
-        const helios_ktable_t& k = tabs[d.tab];
-        const int n = d.n;
-        const double lb = std::log10(b->P_bot_bar[a]), lt = std::log10(b->P_top_bar[a]);
-        const double h = (lb - lt) / (double)(n - 1);
-        std::vector<double> Pp(2 * n + 1);
-        for (int p = 0; p <= 2 * n; ++p) {
-            const double lp = (lb + 0.5 * h) - (0.5 * h) * (double)p;
-            Pp[p] = 1e6 * std::pow(10.0, lp);
-            // isothermal layers: both points of layer i sit at its centre pressure (Sect. 2.3)
-            const double lq = prm->iso_layers ? lb - h * (double)std::min(p >> 1, n - 1) : lp;
-            host_table_coord(lq, k.log10P0, k.dlog10P, k.nP, iP[d.pt_off + p], wP[d.pt_off + p]);
-        }
-        for (int s = 0; s < 2 * n; ++s) {
-            // isothermal layers: sublayer 2i is layer i between its interfaces (eq. 19), sublayer
-            // 2i+1 the zero-thickness step to layer i+1
-            const double dP = prm->iso_layers ? ((s & 1) ? 0.0 : Pp[s] - Pp[s + 2]) : Pp[s] - Pp[s + 1];
-            dm[d.sub_off + s] = (float)(dP / b->grav[a]);
-        }
-        for (int i = 0; i < n; ++i) {
-            lnr[d.lay_off + i] = std::log(Pp[2 * i] / Pp[2 * i + 2]);
-            lay_atm[d.lay_off + i] = a;
-        }
+        std::vector<double> Pp(2 * d.n + 1);
+        layer_geometry(d.n, b->P_bot_bar[a], b->P_top_bar[a], b->grav[a], prm->iso_layers, tabs[d.tab], Pp.data(),
+                       &iP[d.pt_off], &wP[d.pt_off], &dm[d.sub_off], &lnr[d.lay_off]);
+        for (int i = 0; i < d.n; ++i) lay_atm[d.lay_off + i] = a;
     }
 
     // ---- per-bin constants (eqs. 8, 12-14, 20-22), double precision then rounded
@@ -582,71 +508,20 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     for (int a = 0; a < A; ++a) {
         const AtmDesc& d = ad[a];
         const double* e = b->nu_edges + nu_off;
-        double s_star = 0.0, s_int = 0.0;
-        for (int l = 0; l < d.L; ++l) {
-            s_star += planck_bin(e[l], e[l + 1], b->T_star[a]);
-            s_int += planck_bin(e[l], e[l + 1], b->T_int[a]);
-        }
-        const double Firr = sigmaSB * std::pow(b->T_irr[a], 4), Fint = sigmaSB * std::pow(b->T_int[a], 4);
-        for (int l = 0; l < d.L; ++l) {
-            BinConst& c = bc[d.bin_off + l];
-            std::memset(&c, 0, sizeof c);
-            const double nu = 0.5 * (e[l] + e[l + 1]), dnu = e[l + 1] - e[l];
-            const double xs = hP * cL * nu / kB;
-            c.xs = (float)xs;
-            c.xs_lo = (float)(xs - (double)c.xs);
-            c.E = (float)(2.0 * kPi * eps * 2.0 * hP * cL * cL * nu * nu * nu * dnu);
-            if (prm->tabulate)
+        any_scat |= bin_constants(e, b->omega0 + d.bin_off, b->g0 + d.bin_off, d.L, b->T_irr[a], b->T_int[a],
+                                  b->T_star[a], *prm, &bc[d.bin_off]);
+        if (prm->tabulate)
+            for (int l = 0; l < d.L; ++l)
                 for (int j = 0; j < kTabNT; ++j)
-                    btab[(size_t)(d.bin_off + l) * kTabNT + j] = (float)(2.0 * kPi * eps * planck_bin(e[l], e[l + 1], j * (double)kTabDT));
-            double toa = (s_star > 0.0 && Firr > 0.0) ? Firr * planck_bin(e[l], e[l + 1], b->T_star[a]) / s_star : 0.0;
-            double bint = (s_int > 0.0 && Fint > 0.0) ? Fint * planck_bin(e[l], e[l + 1], b->T_int[a]) / s_int : 0.0;
-            if (prm->grey_mode) {
-                if (l == 0) { c.flags |= BIN_GREY_DARK; toa = Firr; bint = 0.0; }
-                else { c.flags |= BIN_GREY_THERM; c.E = (float)(eps * sigmaSB); toa = 0.0; bint = Fint; }
-            }
-            c.toa = (float)toa;
-            c.bint = (float)bint;
-            if (prm->rayleigh) {
-                // Sect. 2.1.4, eqs. (16)-(17): H2 cross section at the bin centre over mbar; the
-                // sublayer constants follow from it in the sweep (rayleigh_const)
-                const double lam_cm = 1.0 / nu;
-                const double nr = 13.58e-5 * (1.0 + 7.52e-11 / (lam_cm * lam_cm)) + 1.0;
-                const double f = (nr * nr - 1.0) / (nr * nr + 2.0), nref = 2.68678e19;
-                const double sig = 24.0 * kPi * kPi * kPi / (nref * nref * lam_cm * lam_cm * lam_cm * lam_cm) * f * f;
-                const double g0 = b->g0[d.bin_off + l];
-                c.flags |= BIN_RAYLEIGH;
-                c.lam = (float)(sig / (mbarMp * mProton));
-                c.q = (float)g0;
-                c.gam = (float)(D * (1.0 - g0) / 2.0);
-                any_scat = true;
-                continue;
-            }
-            const double w0 = b->omega0[d.bin_off + l], g0 = b->g0[d.bin_off + l];
-            if (w0 != 0.0) any_scat = true;
-            if (1.0 - w0 < prm->w0_pure) c.flags |= BIN_PURE_SCAT;
-            if (w0 == 0.0) c.flags |= BIN_NO_SCAT;
-            const double one_wg = 1.0 - w0 * g0;
-            const double lam = D * std::sqrt(one_wg * (1.0 - w0));
-            c.lam = (float)lam;
-            const double kk = one_wg > 0.0 ? std::sqrt((1.0 - w0) / one_wg) : 0.0;
-            const double q = (1.0 - kk) / (1.0 + kk);
-            c.q = (float)q;
-            c.q2 = (float)(q * q);
-            c.omq2 = (float)(1.0 - q * q);
-            // S = eps/(1 - w0 g0) dB (1 - Ts + Rs)/dtau and (1 - Ts + Rs)/dtau = lam phi h
-            c.cl = (float)(lam * eps / (prm->printed_gradient ? (1.0 + w0 * g0) : one_wg));
-            c.gam = (float)(D * (1.0 - g0) / 2.0);
-        }
+                    btab[(size_t)(d.bin_off + l) * kTabNT + j] =
+                        (float)(2.0 * kPi * eps * planck_bin(e[l], e[l + 1], j * (double)kTabDT));
         nu_off += d.L + 1;
     }
     P->passes = prm->direct ? HELIOS_DIRECT : (any_scat ? 1 + prm->n_scat : 1);
 
     // ---- Gauss weights on [0, 1]
-    std::vector<double> gy, gwd;
-    gauss_legendre(G, gy, gwd);
     std::vector<float> gw(G);
-    for (int g = 0; g < G; ++g) gw[g] = (float)(0.5 * gwd[g]);
+    gauss_weights01(G, gw.data());
 
     std::vector<TabDesc> td(ntab);
     for (int t = 0; t < ntab; ++t) {

@@ -779,8 +779,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             // chunk M'; point p at slot (p mod M') CL' + p / M').  At 32 lanes that is this warp's
             // own layout.  At 16 the column goes through the warp's shared-memory row first, so
             // that consecutive lanes write consecutive slots
-            if (!wbase) {
-            } else if (ad.cl == 32) {
+            if (ad.cl == 32) {                  // (a plan always holds a warm-start buffer)
                 const long long col = (long long)(l * G + g) * W;
 #pragma unroll
                 for (int k = 0; k < M; ++k) wbase[col + k * 32 + lane] = U[k];

@@ -11,7 +11,8 @@
 // Cost of that choice: every GPU on which the library's code runs holds the
 // kScratchBytes array until the process exits, the array is shared by every call (so
 // calls whose GPU work overlaps race on it), and sizes beyond what fits are rejected.
-// The host-side staging arrays are static too and are guarded by a mutex.
+// The host-side staging arrays are static too and are guarded by a mutex.  The host set-up
+// (grid, Gauss weights, per-bin constants) is the plan's own (helios_setup.h).
 #include "helios.h"
 
 #include <cuda_runtime.h>
@@ -29,8 +30,10 @@
 // array is only loaded on devices that use this entry point)
 namespace noalloc_copy {
 #include "helios_kernels.cuh"
+#include "helios_setup.h"
 }
 using namespace noalloc_copy::helios_dev;
+using namespace noalloc_copy::helios_setup;
 
 // defined with the rest of the error handling in helios_api.cu (not exported)
 __attribute__((visibility("hidden"))) void helios_set_error_text(const char* msg);
@@ -65,9 +68,6 @@ double h_lnr[kMaxN];
 int h_lay_atm[kMaxN];
 double h_P[kMaxNP];
 
-constexpr double kB = 1.380649e-16, hP = 6.62607015e-27, cL = 2.99792458e10, sigmaSB = 5.670374419e-5;
-constexpr double kPi = 3.14159265358979323846;
-
 int err(int code, const char* fmt, ...)
 {
     char msg[256];
@@ -77,48 +77,6 @@ int err(int code, const char* fmt, ...)
     va_end(ap);
     helios_set_error_text(msg);            // reported by helios_last_error()
     return code;
-}
-
-double planck_bin(double lo, double hi, double T)
-{
-    if (!(T > 0.0)) return 0.0;
-    const double nu = 0.5 * (lo + hi);
-    return 2.0 * hP * cL * cL * nu * nu * nu * (hi - lo) / std::expm1(hP * cL * nu / (kB * T));
-}
-
-void host_table_coord(double x, double x0, double dx, int nx, int& i, double& w)
-{
-    if (nx < 2) { i = 0; w = 0.0; return; }
-    const double u = (x - x0) / dx;
-    if (!(u > 0.0)) i = 0;
-    else if (u >= (double)(nx - 2)) i = nx - 2;
-    else i = (int)std::floor(u);
-    double t = (x - (x0 + (double)i * dx)) / dx;
-    if (!(t > 0.0)) t = 0.0;
-    if (t > 1.0) t = 1.0;
-    w = t;
-}
-
-// Gauss-Legendre weights on [0, 1] (eqs. 31-32) by Newton iteration in long double
-void gauss_weights(int G, float* w01)
-{
-    if (G == 1) { w01[0] = 1.0f; return; }
-    for (int k = 1; k <= G; ++k) {
-        long double x = cosl(kPi * (4.0L * k - 1.0L) / (4.0L * G + 2.0L)), dP = 1.0L;
-        for (int it = 0; it < 60; ++it) {
-            long double pm = 1.0L, pc = x;
-            for (int j = 2; j <= G; ++j) {
-                const long double pn = ((2.0L * j - 1.0L) * x * pc - (j - 1.0L) * pm) / j;
-                pm = pc;
-                pc = pn;
-            }
-            dP = G * (pm - x * pc) / (1.0L - x * x);
-            const long double dx = pc / dP;
-            x -= dx;
-            if (fabsl(dx) < 1e-19L) break;
-        }
-        w01[G - k] = (float)(1.0L / ((1.0L - x * x) * dP * dP));    // half of the [-1, 1] weight
-    }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -164,6 +122,14 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     if (!b || !tab || !prm || !T_layer || !Fup_bol || !Fdn_bol)
         return err(HELIOS_EINVAL, "helios_flux_sweep_noalloc: null argument");
     if (b->A != 1) return err(HELIOS_EINVAL, "helios_flux_sweep_noalloc: one atmosphere per call (got %d)", b->A);
+    {
+        // the call stages its inputs from static host arrays with pageable copies, which a graph
+        // cannot capture (and a replay would read whatever a later call left there)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        NA_CUDA(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return err(HELIOS_EINVAL, "helios_flux_sweep_noalloc: the stream is capturing a graph");
+    }
     const int n = b->n_layers[0], L = b->n_bins[0], G = tab->G;
     if (n < 2 || n > kMaxN) return err(HELIOS_EINVAL, "n_layers %d outside [2, %d]", n, kMaxN);
     if (L < 1 || L > kMaxL || L > tab->L) return err(HELIOS_EINVAL, "n_bins %d outside [1, min(%d, table)]", L, kMaxL);
@@ -204,7 +170,7 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     const int TB = prm->bins_per_item > 0 ? prm->bins_per_item
                                           : std::max(1, std::min(32, (L + nsm * per_sm - 1) / (nsm * per_sm)));
     const int items = (L + TB - 1) / TB;
-    const int NP = 2 * n + 1, NS = 2 * n, W = 32 * M;
+    const int NP = 2 * n + 1, NS = 2 * n;
 
     // carve the scratch; reject what does not fit before touching the GPU
     Carve c{static_cast<char*>(g_scratch_ptr[dev]), 0};
@@ -226,66 +192,23 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     P.invT_old = c.take<float2>(NP); P.dinv_step = c.take<float>(NP); P.dT_step = c.take<float>(NP);
     P.dinv_sub = c.take<float>(NS); P.dT_sub = c.take<float>(NS);
     P.part = c.take<double>((size_t)items * 3 * (n + 1));
-    P.warm = c.take<float>((size_t)L * G * W);
+    P.warm = nullptr;                      // a cold start stores no warm start
     if (c.off > kScratchBytes)
         return err(HELIOS_EINVAL, "atmosphere needs %zu bytes of scratch, more than the %zu available", c.off,
                    kScratchBytes);
 
-    // ---- host set-up into the static staging arrays (double precision)
-    const double lb = std::log10(b->P_bot_bar[0]), lt = std::log10(b->P_top_bar[0]);
-    const double h = (lb - lt) / (double)(n - 1);
-    for (int p = 0; p < NP; ++p) {
-        const double lp = (lb + 0.5 * h) - (0.5 * h) * (double)p;
-        h_P[p] = 1e6 * std::pow(10.0, lp);
-        host_table_coord(lp, tab->log10P0, tab->dlog10P, tab->nP, h_iP[p], h_wP[p]);
-    }
-    for (int q = 0; q < NS; ++q) h_dm[q] = (float)((h_P[q] - h_P[q + 1]) / b->grav[0]);
-    for (int i = 0; i < n; ++i) { h_lnr[i] = std::log(h_P[2 * i] / h_P[2 * i + 2]); h_lay_atm[i] = 0; }
-    const double D = prm->D, eps = 1.0 / D;
-    const double* e = b->nu_edges;
-    double s_star = 0.0, s_int = 0.0;
-    for (int l = 0; l < L; ++l) {
-        s_star += planck_bin(e[l], e[l + 1], b->T_star[0]);
-        s_int += planck_bin(e[l], e[l + 1], b->T_int[0]);
-    }
-    const double Firr = sigmaSB * std::pow(b->T_irr[0], 4), Fint = sigmaSB * std::pow(b->T_int[0], 4);
-    bool any_scat = false;
-    for (int l = 0; l < L; ++l) {
-        BinConst& q = h_bins[l];
-        std::memset(&q, 0, sizeof q);
-        const double nu = 0.5 * (e[l] + e[l + 1]), dnu = e[l + 1] - e[l];
-        const double xs = hP * cL * nu / kB;
-        q.xs = (float)xs;
-        q.xs_lo = (float)(xs - (double)q.xs);
-        q.E = (float)(2.0 * kPi * eps * 2.0 * hP * cL * cL * nu * nu * nu * dnu);
-        double toa = (s_star > 0.0 && Firr > 0.0) ? Firr * planck_bin(e[l], e[l + 1], b->T_star[0]) / s_star : 0.0;
-        double bint = (s_int > 0.0 && Fint > 0.0) ? Fint * planck_bin(e[l], e[l + 1], b->T_int[0]) / s_int : 0.0;
-        if (prm->grey_mode) {
-            if (l == 0) { q.flags |= BIN_GREY_DARK; toa = Firr; bint = 0.0; }
-            else { q.flags |= BIN_GREY_THERM; q.E = (float)(eps * sigmaSB); toa = 0.0; bint = Fint; }
-        }
-        q.toa = (float)toa;
-        q.bint = (float)bint;
-        const double w0 = b->omega0[l], g0 = b->g0[l];
-        if (w0 != 0.0) any_scat = true;
-        if (1.0 - w0 < prm->w0_pure) q.flags |= BIN_PURE_SCAT;
-        if (w0 == 0.0) q.flags |= BIN_NO_SCAT;
-        const double one_wg = 1.0 - w0 * g0, lam = D * std::sqrt(one_wg * (1.0 - w0));
-        const double kk = one_wg > 0.0 ? std::sqrt((1.0 - w0) / one_wg) : 0.0, qq = (1.0 - kk) / (1.0 + kk);
-        q.lam = (float)lam;
-        q.q = (float)qq;
-        q.q2 = (float)(qq * qq);
-        q.omq2 = (float)(1.0 - qq * qq);
-        q.cl = (float)(lam * eps / (prm->printed_gradient ? (1.0 + w0 * g0) : one_wg));
-        q.gam = (float)(D * (1.0 - g0) / 2.0);
-    }
+    // ---- host set-up into the static staging arrays (double precision), as helios_plan_create
+    layer_geometry(n, b->P_bot_bar[0], b->P_top_bar[0], b->grav[0], 0, *tab, h_P, h_iP, h_wP, h_dm, h_lnr);
+    for (int i = 0; i < n; ++i) h_lay_atm[i] = 0;
+    const bool any_scat = bin_constants(b->nu_edges, b->omega0, b->g0, L, b->T_irr[0], b->T_int[0], b->T_star[0],
+                                        *prm, h_bins);
     if (n_passes < 0) return err(HELIOS_EINVAL, "n_passes = %d (the direct column solve needs a plan)", n_passes);
     if (prm->direct) return err(HELIOS_EINVAL, "the direct column solve needs a plan");
     if (prm->rayleigh) return err(HELIOS_EINVAL, "Rayleigh scattering needs a plan");
     if (prm->tabulate) return err(HELIOS_EINVAL, "tabulated functions need a plan");
     if (n_passes == 0) n_passes = any_scat ? 1 + prm->n_scat : 1;
     for (int t = 0; t < items; ++t) { h_items[t] = make_int2(0, t); h_order[t] = t; }
-    gauss_weights(G, h_gw);
+    gauss_weights01(G, h_gw);
     std::memset(&h_atm, 0, sizeof h_atm);
     h_atm.n = n; h_atm.L = L; h_atm.M = M; h_atm.cl = 32; h_atm.tab = 0; h_atm.n_items = items;
     std::memset(&h_tab, 0, sizeof h_tab);
