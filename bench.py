@@ -22,7 +22,8 @@ Default (the headline line):
   build of the oracle on a bounded sample of the same workload (taken in the cpu_baseline leg).
 - cpu_baseline: the FP64 oracle on the host cores on a bounded sample of the batched workload.
 
---workload batched|learned|single|spectrum prints the line of one part alone.
+--workload batched|learned|single|spectrum prints the line of one part alone; --workload precision
+solves the 64-atmosphere high-resolution precision-stress workload (minutes).
 --impl reference: the FP64 CPU oracle timed on the host cores on the headline's workload and
 metric (bounded sample per step).
 """
@@ -667,6 +668,42 @@ def run_profile(args):
                       "atmospheres": len(wl.atms), "sweep_launches_per_step": plan.info.sweep_launches}))
 
 
+def run_precision(args):
+    """The high-resolution precision-stress workload at its stated size: 64 atmospheres x 200 layers
+    x 30000 bins x 20 g with scattering, iterated to radiative equilibrium (eq. 29, tol 1e-7) on the
+    GPU in one batched, graph-captured solve.  Reports converged atmospheres per second and the
+    iteration statistics (the FP64 checks of sampled atmospheres are in the precision tests)."""
+    import torch
+    import synth
+    import paper_1606_05474_b300 as hp
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    wl = synth.config5(A=64)
+    t_gen = time.time() - t0
+    ctx = hp.Context(0)
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params(max_iter=20000))
+    T = torch.from_numpy(np.concatenate([a.T_init for a in wl.atms])).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    iters, status = plan.solve_re(T)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    it, st = iters.cpu().numpy(), status.cpu().numpy()
+    Tg = np.array(plan.split_layers(T.cpu().numpy()))
+    line = {"metric": METRIC, "value": round(float((st == 1).sum()) / dt, 4), "unit": "atm/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 sweep / f64 temperature step", "data": "synthetic",
+            "config": {"workload": "precision stress: 64 atmospheres x 200 layers x 30000 bins x 20 g, scattering, "
+                                   "one solve to eq. (29) at tol 1e-7", "cells_per_evaluation": wl.cells},
+            "wall_s": round(dt, 2), "converged": int((st == 1).sum()), "status_counts": np.bincount(st, minlength=4).tolist(),
+            "iterations": {"min": int(it.min()), "median": float(np.median(it)), "max": int(it.max())},
+            "T_range_K": [round(float(Tg.min()), 1), round(float(Tg.max()), 1)],
+            "workspace_gb": round(plan.info.workspace_bytes / 1e9, 2), "inputs_s": round(t_gen, 2)}
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu_spectrum(args):
     """Post-processing emission spectrum (Sect. 3): the full-size atmosphere (100 layers x 3000
     bins x 20 g, scattering) on isothermal layers, from a cold start, with 1 + 80 scattering
@@ -772,7 +809,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="headline", choices=["headline", "single", "batched", "learned", "spectrum"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "single", "batched", "learned", "spectrum", "precision"])
     ap.add_argument("--atmospheres", type=int, default=4096)
     ap.add_argument("--col-lanes", type=int, default=0, choices=[0, 16, 32],
                     help="single atmosphere: lanes per column of the iterated sweep (0: automatic)")
@@ -793,6 +830,8 @@ def main():
         run_profile(args)
     elif args.workload == "spectrum":
         run_gpu_spectrum(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         headline(args)
 

@@ -58,7 +58,9 @@ enum {
     HELIOS_ATM_ACTIVE = 0,        /* still iterating */
     HELIOS_ATM_CONVERGED = 1,     /* eq. (29) holds in every layer */
     HELIOS_ATM_NOT_CONVERGED = 2, /* hit max_iter */
-    HELIOS_ATM_NONFINITE = 3      /* a non-finite flux or temperature appeared; frozen */
+    HELIOS_ATM_NONFINITE = 3,     /* a non-finite flux or temperature appeared; frozen */
+    HELIOS_ATM_OUT_OF_RANGE = 4   /* params.tabulate: a temperature left the tabulated Planck range
+                                     (above 6000 K); frozen */
 };
 
 typedef struct helios_ctx helios_ctx;
@@ -317,7 +319,8 @@ int helios_solve_re(helios_plan* plan, double* T_layer, int32_t* iters, int32_t*
  * profile; this network supplies a better one).  A multilayer perceptron
  * n_in -> hidden_layers x n_hidden (SiLU) -> n_out (linear), FP32 master
  * parameters; every matrix product rounds both operands to BF16 and accumulates
- * in FP32 on the tensor cores.  Parameter layout (device, float): for each layer
+ * in FP32 on the 5th-generation tensor cores (tcgen05 MMAs with the accumulator
+ * in tensor memory, 128 x 128 tiles).  Parameter layout (device, float): for each layer
  * l, W_l [in][out] row-major then b_l [out].  Initial weights are uniform in
  * +-1/sqrt(fan_in) from `seed`.  Batches hold up to max_batch rows.
  *   helios_mlp_forward: y[B][n_out] = net(x[B][n_in]) (device arrays)
@@ -332,6 +335,9 @@ int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers
                       unsigned long long seed, int max_batch, helios_mlp** mlp);
 int helios_mlp_destroy(helios_mlp* mlp);
 int helios_mlp_params(helios_mlp* mlp, float** params, float** grads, long long* count);
+/* Synchronous: *flag = 1 if a matrix product of this network gave up waiting for its tensor-core
+ * operations (a bounded wait that expired; its results are then invalid), else 0. */
+int helios_mlp_error(helios_mlp* mlp, int* flag);
 int helios_mlp_forward(helios_mlp* mlp, const float* x, float* y, int B, cudaStream_t stream);
 int helios_mlp_grad(helios_mlp* mlp, const float* x, const float* target, int B, float* loss, cudaStream_t stream);
 int helios_mlp_adam(helios_mlp* mlp, float lr, float beta1, float beta2, float eps, cudaStream_t stream);

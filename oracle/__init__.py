@@ -35,7 +35,7 @@ _SO = os.path.join(_HERE, "_helios_ref.so")
 _lib = None
 
 SIGMA_SB = 5.670374419e-5
-CONVERGED, UPDATED, NOT_CONVERGED, NONFINITE = 0, 1, 2, 3
+CONVERGED, UPDATED, NOT_CONVERGED, NONFINITE, OUT_OF_RANGE = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:

@@ -974,6 +974,11 @@ int ref_temp_update(const ref_atm* a, const ref_params* p, const double* Fup_bol
         }
     }
     free(P);
+    /* with the tables of Sect. 2.6, a temperature above the Planck table's last node would take
+       that node's values: the iteration stops instead */
+    if (p->tabulate)
+        for (int i = 0; i < n; ++i)
+            if (!(T[i] <= REF_TAB_DT * (REF_TAB_NT - 1))) return REF_OUT_OF_RANGE;
     return REF_UPDATED;
 }
 
@@ -1007,6 +1012,7 @@ int ref_solve_re(const ref_atm* a, const ref_params* p, double* T, double* mult,
         int st = ref_temp_update(a, p, Fu, Fd, T, mult, hist, nhist, metric, NULL);
         if (st == REF_CONVERGED) { status = REF_CONVERGED; ++it; break; }
         if (st == REF_NONFINITE) { status = REF_NONFINITE; ++it; break; }
+        if (st == REF_OUT_OF_RANGE) { status = REF_OUT_OF_RANGE; ++it; break; }
     }
     if (iters) *iters = it;
     free(Fu); free(Fd); free(m_own); free(h_own); free(c_own); free(w_own);

@@ -67,7 +67,7 @@ typedef struct {
     int tabulate;             /* 1: Planck and transmission functions from tables (Sect. 2.6) */
 } ref_params;
 
-enum { REF_CONVERGED = 0, REF_UPDATED = 1, REF_NOT_CONVERGED = 2, REF_NONFINITE = 3 };
+enum { REF_CONVERGED = 0, REF_UPDATED = 1, REF_NOT_CONVERGED = 2, REF_NONFINITE = 3, REF_OUT_OF_RANGE = 4 };
 
 void   ref_default_params(ref_params* p);
 

@@ -13,7 +13,7 @@ from typing import Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import (ATM_ACTIVE, ATM_CONVERGED, ATM_NONFINITE, ATM_NOT_CONVERGED, HeliosError,  # noqa: F401
+from ._lib import (ATM_ACTIVE, ATM_CONVERGED, ATM_NONFINITE, ATM_NOT_CONVERGED, ATM_OUT_OF_RANGE, HeliosError,  # noqa: F401
                    check)
 
 __all__ = ["Context", "Plan", "MLP", "default_params", "autotune", "flux_sweep_noalloc", "HeliosError", "build"]
@@ -432,6 +432,13 @@ class MLP:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         check(self.lib.helios_mlp_adam(self.h, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+    def error(self):
+        """1 if a tensor-core product of this network gave up waiting (its results invalid), else 0
+        (helios_mlp_error; synchronous)."""
+        f = ctypes.c_int()
+        check(self.lib.helios_mlp_error(self.h, ctypes.byref(f)))
+        return f.value
 
     def train_step(self, x, target, lr=1e-3, stream=None):
         check(self.lib.helios_mlp_train_step(self.h, x.contiguous().data_ptr(), target.contiguous().data_ptr(),

@@ -9,7 +9,7 @@ SO_PATH = os.path.join(HERE, "libhelios.so")
 
 HELIOS_OK, HELIOS_EINVAL, HELIOS_ENOMEM, HELIOS_ECUDA, HELIOS_ENOCONV = 0, -1, -2, -3, -5
 HELIOS_DIRECT = -1          # n_passes: the exact column solve instead of scattering passes
-ATM_ACTIVE, ATM_CONVERGED, ATM_NOT_CONVERGED, ATM_NONFINITE = 0, 1, 2, 3
+ATM_ACTIVE, ATM_CONVERGED, ATM_NOT_CONVERGED, ATM_NONFINITE, ATM_OUT_OF_RANGE = 0, 1, 2, 3, 4
 
 c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
 
@@ -48,7 +48,7 @@ EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "heli
            "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_re_step_host", "helios_solve_re", "helios_measure_peaks", "helios_device_recip", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
            "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_forward",
-           "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step", "helios_mlp_initial_profiles",
+           "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step", "helios_mlp_initial_profiles", "helios_mlp_error",
            "helios_column_stats", "helios_standardize"]
 
 _lib = None
@@ -93,6 +93,7 @@ def load(path: str = SO_PATH):
     lib.helios_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]
     lib.helios_mlp_train_step.argtypes = [vp, vp, vp, c_int, ctypes.c_float, vp, vp]
     lib.helios_mlp_initial_profiles.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, c_double, c_double, vp, vp, vp]
+    lib.helios_mlp_error.argtypes = [vp, P(c_int)]
     lib.helios_column_stats.argtypes = [vp, c_int, c_int, c_double, vp, vp, vp]
     lib.helios_standardize.argtypes = [vp, vp, vp, c_int, c_int, vp, vp]
     lib.helios_flux_sweep_noalloc.argtypes = [P(Batch), P(KTable), P(Params), vp, c_int, vp, vp, vp, vp]

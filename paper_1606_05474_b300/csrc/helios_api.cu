@@ -867,6 +867,7 @@ TempArgs temp_args(const helios_plan* p)
     t.sigma = sigmaSB; t.tol = p->prm.tol; t.fpre_num = p->prm.fpre_num; t.fpre_exp = p->prm.fpre_exp;
     t.osc_down = p->prm.osc_down; t.osc_up = p->prm.osc_up; t.mult_max = p->prm.mult_max;
     t.T_floor = p->prm.T_floor; t.max_iter = p->prm.max_iter;
+    t.T_tab_max = p->prm.tabulate ? (double)kTabDT * (kTabNT - 1) : 0.0;
     return t;
 }
 

@@ -1077,6 +1077,8 @@ __global__ void finalize_kernel(PlanDev P, const int* __restrict__ status, doubl
 // temperature step, eqs. (23)-(29), FP64
 struct TempArgs {
     double sigma, tol, fpre_num, fpre_exp, osc_down, osc_up, mult_max, T_floor;
+    double T_tab_max;       // > 0: the top of the tabulated Planck range (Sect. 2.6 tables); a layer above
+                            // it ends the atmosphere as OUT_OF_RANGE
     int max_iter;
 };
 
@@ -1167,6 +1169,15 @@ __device__ __forceinline__ void temp_block(const PlanDev& P, const TempArgs& tar
             if (h == 0u || h == 0x3Fu) m = fmin(m * targ.osc_up, targ.mult_max);
             else m = m * targ.osc_down;
             mult[li] = m;
+        }
+    }
+    if (targ.T_tab_max > 0.0) {
+        // with tabulated Planck functions, a temperature above the table's last node would take
+        // that node's values: the atmosphere stops with its own status instead
+        const int out = __syncthreads_or(mine && !(T_layer[li] <= targ.T_tab_max));
+        if (out && i == 0 && status[a] == 0) {
+            status[a] = 4;
+            if (n_active) atomicSub(n_active, 1);
         }
     }
 }

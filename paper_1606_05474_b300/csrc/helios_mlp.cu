@@ -47,104 +47,165 @@ enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_SILU = 2, EPI_DSILU = 3 };
 
 __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf(-z)); }
 
-// C[M x N] = op(A)[M x K] op(B)[K x N] with both operands rounded to BF16, FP32 accumulation.
+// ---------------------------------------------------------------------------------------------
+// C[M x N] = op(A)[M x K] op(B)[K x N] on the 5th-generation tensor cores (tcgen05), both operands
+// rounded to BF16, FP32 accumulation in tensor memory, epilogue fused.
 // op(A)[m][k] = TA ? A[k*lda + m] : A[m*lda + k];  op(B)[k][n] = TB ? B[n*ldb + k] : B[k*ldb + n].
-// Block tile 64 x 64 (4 warps of 32 x 32), K step 32; epilogue fused.
-template <bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(128) mlp_gemm(int M, int N, int K, const float* __restrict__ A, int lda,
-                                                const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
-                                                const float* __restrict__ bias, float* __restrict__ Zout,
-                                                const float* __restrict__ Zin, int ldz, float scale)
-{
-    __shared__ __align__(16) __nv_bfloat16 As[64][40];     // [m][k], row stride 80 B: conflict-free fragments
-    __shared__ __align__(16) __nv_bfloat16 Bs[64][40];     // [n][k]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gid = lane >> 2, tq = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.0f;
+// One CTA of 4 warps per 128 x 128 tile of C.  Per K step of 64 the CTA stages both operands as
+// BF16 into shared memory in the canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices: element (r, k) of a 128-row tile at ((k/8) 16 + r/8) 128 + (r%8) 16 + (k%8) 2 bytes,
+// so the byte stride between core matrices along K is 2048 and along the rows 128), then one
+// thread issues four 128 x 128 x 16 MMAs reading both operands through shared-memory descriptors
+// and accumulating into 128 TMEM columns, and commits them to an mbarrier the CTA waits on before
+// the next step overwrites the tiles.  The epilogue reads the accumulator back with tcgen05.ld
+// (warp w holds rows 32w .. 32w+31, a thread one row) and applies the bias / SiLU / SiLU-derivative.
+// Every wait on the mbarrier is bounded: on expiry the kernel records an error in *err, stops
+// issuing, waits (bounded again) for what it issued, releases its tensor memory and returns.
+constexpr int UM_TILE = 128, UM_BK = 64;
+constexpr uint32_t UM_A = 0, UM_B = 16384, UM_BAR = 32768, UM_SLOT = 32776;
+constexpr size_t UM_SMEM = 72 * 1024;        // 32 KB of tiles, padded so that at most 3 CTAs (384 of the
+                                             // 512 TMEM columns) share an SM
+constexpr uint32_t UM_COLS = 128;            // FP32 accumulator columns
+constexpr long UM_WAIT_LIMIT = 1L << 22;     // mbarrier polls before the kernel gives up
+// instruction descriptor (kind::f16): F32 accumulator (bits 4-5 = 1), A and B BF16 (bits 7-9,
+// 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_TILE >> 3) << 17) |
+                              ((uint32_t)(UM_TILE >> 4) << 24);
 
-    for (int k0 = 0; k0 < K; k0 += 32) {
-        for (int e = tid; e < 64 * 32; e += 128) {
+__device__ __forceinline__ uint32_t um_core_off(int r, int k)
+{
+    return (uint32_t)((((k >> 3) * (UM_TILE / 8) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: start address, leading-dimension (K) byte offset, stride (row
+// group) byte offset, all in 16-byte units; descriptor version 1 at bit 46; no swizzle
+__device__ __forceinline__ uint64_t um_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t phase)
+{
+    for (long it = 0; it < UM_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const float* __restrict__ A, int lda,
+                                                   const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+                                                   const float* __restrict__ bias, float* __restrict__ Zout,
+                                                   const float* __restrict__ Zin, int ldz, float scale, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * UM_TILE, n0 = blockIdx.x * UM_TILE;
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t sA = s0 + UM_A, sB = s0 + UM_B, bar = s0 + UM_BAR;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s0 + UM_SLOT),
+                     "r"(UM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + UM_SLOT);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < K && ok; k0 += UM_BK) {
+        // ---- stage op(A) rows m0.. and op(B) columns n0.. of this K step as BF16, K-major
+        for (int e = tid; e < UM_TILE * UM_BK; e += 128) {
             int r, c;
-            if (!TA) { r = e >> 5; c = e & 31; } else { c = e >> 6; r = e & 63; }
+            if (!TA) { r = e >> 6; c = e & 63; } else { c = e >> 7; r = e & 127; }   // coalesced in global
             const int gm = m0 + r, gk = k0 + c;
             float v = 0.0f;
             if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            As[r][c] = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(sm + UM_A + um_core_off(r, c)) = __float2bfloat16_rn(v);
         }
-        for (int e = tid; e < 64 * 32; e += 128) {
+        for (int e = tid; e < UM_TILE * UM_BK; e += 128) {
             int r, c;       // r: n offset, c: k offset
-            if (!TB) { c = e >> 6; r = e & 63; } else { r = e >> 5; c = e & 31; }
+            if (TB) { r = e >> 6; c = e & 63; } else { c = e >> 7; r = e & 127; }
             const int gn = n0 + r, gk = k0 + c;
             float v = 0.0f;
             if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-            Bs[r][c] = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(sm + UM_B + um_core_off(r, c)) = __float2bfloat16_rn(v);
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor cores
         __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int kk = 0; kk < 32; kk += 16) {
-            uint32_t a[2][4], b[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gid;
-                a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + tq * 2]);
-                a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + tq * 2]);
-                a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + tq * 2 + 8]);
-                a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + tq * 2 + 8]);
+            for (int kk = 0; kk < UM_BK / 16; ++kk) {
+                const uint64_t da = um_desc(sA + kk * 2 * 2048, 2048, 128);
+                const uint64_t db = um_desc(sB + kk * 2 * 2048, 2048, 128);
+                const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(UM_IDESC), "r"(acc)
+                    : "memory");
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = wn + j * 8 + gid;
-                b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + tq * 2]);
-                b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + tq * 2 + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float* d = acc[i][j];
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-                        "{%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                        : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
         }
-        __syncthreads();
+        ok = __syncthreads_and(um_wait(bar, phase) ? 1 : 0) != 0;      // one decision for the CTA
+        phase ^= 1u;
+        if (!ok && tid == 0) atomicExch(err, 1);
     }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // ---- epilogue: row m0 + 32 warp + lane, 8 accumulator columns at a time
+        const int m = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < UM_TILE && n0 + c0 < N; c0 += 8) {
+            uint32_t r[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m >= M) continue;
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int c2 = 0; c2 < 2; ++c2) {
-                    const int m = m0 + wm + i * 16 + gid + h * 8, n = n0 + wn + j * 8 + tq * 2 + c2;
-                    if (m >= M || n >= N) continue;
-                    const float v = acc[i][j][h * 2 + c2];
-                    float out;
-                    if (EPI == EPI_STORE) {
-                        out = scale * v;
-                    } else if (EPI == EPI_BIAS) {
-                        out = v + bias[n];
-                    } else if (EPI == EPI_BIAS_SILU) {
-                        const float z = v + bias[n];
-                        Zout[(size_t)m * ldz + n] = z;
-                        out = z * sigmoidf_(z);
-                    } else {
-                        const float z = Zin[(size_t)m * ldz + n], s = sigmoidf_(z);
-                        out = v * s * fmaf(z, 1.0f - s, 1.0f);      // d SiLU / dz
-                    }
-                    C[(size_t)m * ldc + n] = out;
+            for (int j = 0; j < 8; ++j) {
+                const int n = n0 + c0 + j;
+                if (n >= N) break;
+                const float v = __uint_as_float(r[j]);
+                float out;
+                if (EPI == EPI_STORE) {
+                    out = scale * v;
+                } else if (EPI == EPI_BIAS) {
+                    out = v + bias[n];
+                } else if (EPI == EPI_BIAS_SILU) {
+                    const float z = v + bias[n];
+                    Zout[(size_t)m * ldz + n] = z;
+                    out = z * sigmoidf_(z);
+                } else {
+                    const float z = Zin[(size_t)m * ldz + n], sg = sigmoidf_(z);
+                    out = v * sg * fmaf(z, 1.0f - sg, 1.0f);      // d SiLU / dz
                 }
+                C[(size_t)m * ldc + n] = out;
+            }
+        }
+    } else {
+        um_wait(bar, phase ^ 1u);           // what was issued before the wait gave up (bounded)
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_COLS) : "memory");
 }
 
 // dOut = 2 (Y - T) / (B * N); per-block partial sums of the squared error (fixed order)
@@ -299,6 +360,7 @@ struct helios_mlp {
     float *dA, *dB;          // backprop ping-pong buffers
     float* dout;
     float *xin, *yout;       // initial profiles: standardised features and network outputs, max_B rows
+    int* err;                // set by a GEMM whose tensor-core wait gave up
     double* part;
     int64_t t;               // Adam step count
     std::vector<void*> allocs;
@@ -365,6 +427,9 @@ int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers
     m->allocs.push_back(m->xin);
     if (cudaMalloc((void**)&m->yout, sizeof(float) * (size_t)max_batch * n_out) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp outputs"); }
     m->allocs.push_back(m->yout);
+    if (cudaMalloc((void**)&m->err, sizeof(int)) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp flag"); }
+    m->allocs.push_back(m->err);
+    MLP_CUDA(cudaMemset(m->err, 0, sizeof(int)));
     MLP_CUDA(cudaMemcpy(m->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice));
     MLP_CUDA(cudaMemset(m->m, 0, sizeof(float) * off));
     MLP_CUDA(cudaMemset(m->v, 0, sizeof(float) * off));
@@ -381,6 +446,14 @@ int helios_mlp_destroy(helios_mlp* m)
     cudaDeviceSynchronize();
     for (void* a : m->allocs) cudaFree(a);
     delete m;
+    return HELIOS_OK;
+}
+
+int helios_mlp_error(helios_mlp* m, int* flag)
+{
+    if (!m || !flag) return mfail(HELIOS_EINVAL, "helios_mlp_error: null argument");
+    MLP_CUDA(cudaSetDevice(m->device));
+    MLP_CUDA(cudaMemcpy(flag, m->err, sizeof(int), cudaMemcpyDeviceToHost));
     return HELIOS_OK;
 }
 
@@ -401,11 +474,18 @@ float* Zbuf(helios_mlp* m, int l) { size_t o = 0; for (int k = 0; k < l; ++k) o 
 float* Ybuf(helios_mlp* m, int l) { return Zbuf(m, l) + (size_t)m->max_B * m->dims[l + 1]; }
 
 template <bool TA, bool TB, int EPI>
-int gemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc, const float* bias,
-         float* Zout, const float* Zin, int ldz, float scale, cudaStream_t s)
+int gemm(helios_mlp* m, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+         const float* bias, float* Zout, const float* Zin, int ldz, float scale, cudaStream_t s)
 {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    mlp_gemm<TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Zout, Zin, ldz, scale);
+    static thread_local int configured[64] = {};          // per device: the dynamic shared-memory limit set
+    if (m->device < 0 || m->device >= 64) return mfail(HELIOS_EINVAL, "device %d", m->device);
+    if (!configured[m->device]) {
+        MLP_CUDA(cudaFuncSetAttribute(mlp_umma<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UM_SMEM));
+        configured[m->device] = 1;
+    }
+    dim3 grid((N + UM_TILE - 1) / UM_TILE, (M + UM_TILE - 1) / UM_TILE);
+    mlp_umma<TA, TB, EPI><<<grid, 128, UM_SMEM, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Zout, Zin, ldz, scale,
+                                                      m->err);
     MLP_CUDA(cudaGetLastError());
     return HELIOS_OK;
 }
@@ -420,9 +500,9 @@ int forward(helios_mlp* m, const float* x, float* y, int B, cudaStream_t s)
         const float* b = m->p + m->boff[l];
         int rc;
         if (l + 1 < m->nl)
-            rc = gemm<false, false, EPI_BIAS_SILU>(B, N, K, in, K, W, N, Ybuf(m, l), N, b, Zbuf(m, l), nullptr, N, 1.0f, s);
+            rc = gemm<false, false, EPI_BIAS_SILU>(m, B, N, K, in, K, W, N, Ybuf(m, l), N, b, Zbuf(m, l), nullptr, N, 1.0f, s);
         else
-            rc = gemm<false, false, EPI_BIAS>(B, N, K, in, K, W, N, y, N, b, nullptr, nullptr, N, 1.0f, s);
+            rc = gemm<false, false, EPI_BIAS>(m, B, N, K, in, K, W, N, y, N, b, nullptr, nullptr, N, 1.0f, s);
         if (rc) return rc;
         in = Ybuf(m, l);
     }
@@ -449,14 +529,14 @@ int backward(helios_mlp* m, const float* x, const float* target, int B, float* l
         const int K = m->dims[l], N = m->dims[l + 1];
         const float* inp = l ? Ybuf(m, l - 1) : x;
         // dW_l = in^T dZ_l, db_l = colsum dZ_l
-        rc = gemm<true, false, EPI_STORE>(K, N, B, inp, K, dcur, N, m->g + m->woff[l], N, nullptr, nullptr, nullptr, 0,
+        rc = gemm<true, false, EPI_STORE>(m, K, N, B, inp, K, dcur, N, m->g + m->woff[l], N, nullptr, nullptr, nullptr, 0,
                                           1.0f, s);
         if (rc) return rc;
         colsum_kernel<<<(N + 127) / 128, 128, 0, s>>>(dcur, B, N, m->g + m->boff[l]);
         MLP_CUDA(cudaGetLastError());
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l^T) * SiLU'(Z_{l-1})
-            rc = gemm<false, true, EPI_DSILU>(B, K, N, dcur, N, m->p + m->woff[l], N, dnext, K, nullptr, nullptr,
+            rc = gemm<false, true, EPI_DSILU>(m, B, K, N, dcur, N, m->p + m->woff[l], N, dnext, K, nullptr, nullptr,
                                               Zbuf(m, l - 1), K, 1.0f, s);
             if (rc) return rc;
             std::swap(dcur, dnext);

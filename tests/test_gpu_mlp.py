@@ -1,5 +1,6 @@
-"""The learned initialiser's network on the GPU vs the FP64 NumPy oracle on the same BF16-rounded
-operands, and what the trained network gains over the isothermal start.
+"""The learned initialiser's network on the GPU (tcgen05 tensor-core products) vs the FP64 NumPy
+oracle on the same BF16-rounded operands, and what the trained network gains over the isothermal
+start.
 
 Tolerances, element by element: every output and gradient element is a product's sum of terms;
 the GPU accumulates in FP32 and keeps activations in FP32 before the next product rounds them to
@@ -49,6 +50,7 @@ def test_forward_matches_oracle():
     yo, _, _ = omlp.forward(p, DIMS, x64, bf16_ops=True)
     sy, _ = omlp.magnitude_sums(p, DIMS, x64, np.zeros((B, DIMS[-1])))
     _check_scaled(y, yo, sy, "forward")
+    assert net.error() == 0                   # no tensor-core wait gave up
 
 
 def test_gradients_match_oracle():
@@ -64,6 +66,7 @@ def test_gradients_match_oracle():
     lo, go = omlp.loss_and_grad(p, DIMS, xf.astype(np.float64), tf.astype(np.float64), bf16_ops=True)
     _, sg = omlp.magnitude_sums(p, DIMS, xf.astype(np.float64), tf.astype(np.float64))
     assert loss.item() == pytest.approx(lo, rel=2e-3)
+    assert net.error() == 0
     o = 0
     for li, (a, b) in enumerate(zip(DIMS[:-1], DIMS[1:])):
         for n, kind in ((a * b, "W"), (b, "b")):          # weight block, then bias block

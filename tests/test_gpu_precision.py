@@ -1,12 +1,21 @@
 """Precision stress: the float32 sweep against the FP64 oracle at high resolution.
 
-Two atmospheres of the precision-stress workload (200 layers, 1e-6..1e3 bar, 30000 bins over
-0.3-200 um, 20 Gauss points, Rayleigh-like scattering, one shared 20x20x30000x20 table) are
-iterated to radiative equilibrium on the GPU; at the converged profiles both sides then evaluate
-the fluxes from a cold start with the default 1 + 4 passes.  Tables of the errors (bolometric
-fluxes per interface, net flux, emergent spectrum per bin) are written as JSON to the path in
-HELIOS_PRECISION_REPORT when it is set.  Bounds: the parity tolerances of the smaller cases
-(1e-5), which the 30000-bin sums must keep.
+Four atmospheres sampled from the 64 of the precision-stress workload (seeds 0, 21, 42, 63: 200
+layers, 1e-6..1e3 bar, 30000 bins over 0.3-200 um, 20 Gauss points, Rayleigh-like scattering,
+one shared 20x20x30000x20 table) are iterated to radiative equilibrium on the GPU (eq. 29,
+tol 1e-7).  At the converged profiles:
+- both sides evaluate the fluxes from a cold start with the default 1 + 4 passes: bolometric
+  fluxes per interface, net flux and emergent spectrum per bin within the parity tolerance of
+  the smaller cases (1e-5);
+- the GPU's converged profile is checked to be an equilibrium by the FP64 oracle's own measure:
+  the oracle's exact column solution (the limit of the passes) at that profile gives a flux
+  divergence below 3 tol sigma T^4 in every layer.  A converged profile is any profile meeting
+  eq. (29), not a unique one (the criterion leaves up to 4 K at the BOA, Sect. 2.2.4), so the
+  check is of the equilibrium condition itself; temperatures are not compared at this size
+  (an oracle solve of 1.2e8 cells per evaluation from the start profile takes hours);
+- the temperature change the oracle's own step (eqs. 24-28, unit multipliers) would make from the
+  GPU's profile is reported, in kelvin.
+Tables of the errors are written as JSON to the path in HELIOS_PRECISION_REPORT when it is set.
 """
 import json
 import os
@@ -22,7 +31,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_precision_stress_error_tables():
-    wl = synth.config5(atm_ids=[0, 41])
+    wl = synth.config5(atm_ids=[0, 21, 42, 63])
     plan = make_plan(wl, max_iter=20000)
     T = pack([a.T_init for a in wl.atms])
     iters, status = plan.solve_re(T)
@@ -45,13 +54,23 @@ def test_precision_stress_error_tables():
         scale = np.maximum(r["Fup"], r["Fdn"])
         net_err = np.abs((Fus[i] - Fds[i]) - (r["Fup"] - r["Fdn"])) / scale
         spec_err = np.abs(toas[i] - r["toa"]) / np.maximum(np.abs(r["toa"]), inc)
+        own = np.abs(toas[i] - r["toa"]) / np.abs(r["toa"])
+        # the equilibrium condition at the GPU's profile, by the oracle's exact column solution
+        d = oracle.flux_direct(atm, Tg[i])
+        assert d["rc"] == 0
+        st = oracle.State(atm, Tg[i])
+        rc, metric, _ = oracle.temp_update(atm, st, d["Fup"], d["Fdn"], oracle.params(tol=0.0))
+        dT_step = np.abs(st.T - Tg[i])
         rows.append({"atmosphere": i, "T_irr": a.T_irr, "T_int": a.T_int, "iterations": int(iters[i].item()),
                      "T_min": float(Tg[i].min()), "T_max": float(Tg[i].max()),
                      "Fup_rel_max": float(up_err.max()), "Fup_rel_median": float(np.median(up_err)),
                      "Fdn_rel_max": float(dn_err.max()), "Fdn_rel_median": float(np.median(dn_err)),
                      "net_rel_max": float(net_err.max()),
                      "spectrum_rel_max": float(spec_err.max()), "spectrum_rel_median": float(np.median(spec_err)),
-                     "spectrum_rel_p99": float(np.quantile(spec_err, 0.99))})
+                     "spectrum_rel_p99": float(np.quantile(spec_err, 0.99)),
+                     "spectrum_own_rel_median": float(np.median(own)), "spectrum_own_rel_p99": float(np.quantile(own, 0.99)),
+                     "oracle_metric_at_gpu_profile": float(metric), "oracle_step_K_max": float(dT_step.max()),
+                     "oracle_step_K_median": float(np.median(dT_step))})
     path = os.environ.get("HELIOS_PRECISION_REPORT")
     if path:
         with open(path, "w") as f:
@@ -59,6 +78,7 @@ def test_precision_stress_error_tables():
     for r in rows:
         assert r["Fup_rel_max"] < 1e-5 and r["Fdn_rel_max"] < 1e-5 and r["net_rel_max"] < 1e-5, r
         assert r["spectrum_rel_max"] < 1e-5, r
+        assert r["oracle_metric_at_gpu_profile"] < 3e-7, r
 
 
 def test_device_reciprocal_is_within_an_ulp_and_unbiased():

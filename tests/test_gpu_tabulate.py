@@ -69,3 +69,19 @@ def test_tabulate_rejects_what_has_no_tabulated_form():
     plan = make_plan(wl, tabulate=1)
     with pytest.raises(hp.HeliosError):
         plan.flux_sweep(pack([synth.perturbed_profile(wl.atms[0], 1)]), n_passes=hp.DIRECT)
+
+
+def test_temperatures_above_the_planck_table_stop_the_atmosphere():
+    # as in the oracle: with tables, an atmosphere whose profile is above the Planck table's 6000 K
+    # stops as OUT_OF_RANGE; the other atmospheres of the batch step on
+    import paper_1606_05474_b300 as hp
+    wls = [synth.small_scattering(L=6, n=20, seed_offset=k) for k in (1, 2)]
+    atms = [w.atms[0] for w in wls]
+    atms[1].table_id = 1
+    wl = synth.Workload(name="two", atms=atms, tables=[w.tables[0] for w in wls])
+    plan = make_plan(wl, tabulate=1)
+    T = pack([np.full(20, 6100.0), np.full(20, 5000.0)])
+    state = plan.new_state()
+    plan.re_step(T, state, warm=False)
+    st = state["status"].cpu().numpy()
+    assert st[0] == hp.ATM_OUT_OF_RANGE and st[1] == hp.ATM_ACTIVE

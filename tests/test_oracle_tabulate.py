@@ -64,9 +64,10 @@ def test_tabulated_fluxes_close_to_exact():
     T = synth.perturbed_profile(wl.atms[0], 2)
     ex = oracle.flux_sweep(atm, T, n_passes=5)
     tb = oracle.flux_sweep(atm, T, n_passes=5, p=oracle.params(tabulate=1))
+    # the tables move the fluxes by ~1e-4 (measured 9.6e-5 upward, 1.9e-4 downward here)
     for k in ("Fup", "Fdn"):
         d = np.max(np.abs(tb[k] / ex[k] - 1))
-        assert 1e-6 < d < 1e-2, (k, d)
+        assert 1e-6 < d < 5e-4, (k, d)
 
 
 def test_tabulated_equilibrium_close_to_the_exact_one():
@@ -82,3 +83,18 @@ def test_tabulated_equilibrium_close_to_the_exact_one():
         Ts.append(st.T.copy())
     d = np.abs(Ts[1] - Ts[0])
     assert 1e-4 < d.max() < 0.2, d.max()
+
+
+def test_temperatures_above_the_planck_table_stop_the_iteration():
+    # the Planck table of Sect. 2.6 ends at 6000 K: a profile that reaches above it ends the
+    # iteration with its own status instead of continuing on the last node's values; below the
+    # table's top, and without tables, the step is an ordinary one
+    wl = synth.small_scattering(L=6, n=20)
+    atm = oracle.Atm.from_workload(wl)
+    for T0, tab, want in ((6100.0, 1, oracle.OUT_OF_RANGE), (5000.0, 1, oracle.UPDATED), (6100.0, 0, oracle.UPDATED)):
+        T = np.full(20, T0)
+        p = oracle.params(tabulate=tab)
+        r = oracle.flux_sweep(atm, T, n_passes=5, p=p)
+        st = oracle.State(atm, T)
+        rc, _, _ = oracle.temp_update(atm, st, r["Fup"], r["Fdn"], p)
+        assert rc == want, (T0, tab, rc)
