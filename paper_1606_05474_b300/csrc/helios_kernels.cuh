@@ -741,6 +741,13 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 kap[g_of * KST + p] = kappa_at(tab, td, P.row[q], P.wq[q], lg);
             }
         }
+        // the slots past the TOA point (KST - NP per column) hold zero opacity: with zero column mass
+        // and Planck difference there, every padding sublayer takes the zero-thickness form (Ts = 1,
+        // Rs = 0, Ss = 0) without a test per sublayer
+        if (!DIRECT) {
+            const int pad = KST - NP;
+            for (int t = tid; t < G * pad; t += nthreads) kap[(t / pad) * KST + NP + t % pad] = 0.0f;
+        }
         __syncthreads();
 
         // ---- phase 2: CL lanes per Gauss point; lane `sub` of a column holds its sublayers
@@ -806,12 +813,10 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
                     const int s = sub * M + k;
-                    float t = 1.0f, r = 0.0f, src = 0.0f;
-                    if (s < NS) {
-                        float kt;
-                        const BinConst c = rayleigh_const(bc, P, 0.5f * (krow[s] + krow[s + 1]), kt);
-                        layer_coef(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src);
-                    }
+                    float t, r, src;                                    // padding: (1, 0, 0)
+                    float kt;
+                    const BinConst c = rayleigh_const(bc, P, 0.5f * (krow[s] + krow[s + 1]), kt);
+                    layer_coef(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src);
                     Ts[k] = t;
                     Rs[k] = r;
                     Ss[k] = src;
@@ -821,11 +826,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
                     const int s = sub * M + k;
-                    float t = 1.0f, r = 0.0f, src = 0.0f;
-                    if (s < NS) {
-                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                        layer_coef<false, true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, nullptr, 0.0f, P.utab);
-                    }
+                    float t, r, src;                                    // padding: (1, 0, 0)
+                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                    layer_coef<false, true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, nullptr, 0.0f, P.utab);
                     Ts[k] = t;
                     Rs[k] = r;
                     Ss[k] = src;
@@ -835,11 +838,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 #pragma unroll
                 for (int k = 0; k < M; ++k) {
                     const int s = sub * M + k;
-                    float t = 1.0f, r = 0.0f, src = 0.0f;
-                    if (s < NS) {
-                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                        layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
-                    }
+                    float t, r, src;                                    // padding: (1, 0, 0)
+                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                    layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
                     Ts[k] = t;
                     Rs[k] = r;
                     Ss[k] = src;
