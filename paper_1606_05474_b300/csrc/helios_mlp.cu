@@ -51,30 +51,36 @@ __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf
 // C[M x N] = op(A)[M x K] op(B)[K x N] on the 5th-generation tensor cores (tcgen05), both operands
 // rounded to BF16, FP32 accumulation in tensor memory, epilogue fused.
 // op(A)[m][k] = TA ? A[k*lda + m] : A[m*lda + k];  op(B)[k][n] = TB ? B[n*ldb + k] : B[k*ldb + n].
-// One CTA of 4 warps per 128 x 128 tile of C.  Per K step of 64 the CTA stages both operands as
+// One CTA of 4 warps per 128 x 64 tile of C.  Per K step of 64 the CTA stages both operands as
 // BF16 into shared memory in the canonical K-major layout without swizzle (8-row x 16-byte core
-// matrices: element (r, k) of a 128-row tile at ((k/8) 16 + r/8) 128 + (r%8) 16 + (k%8) 2 bytes,
-// so the byte stride between core matrices along K is 2048 and along the rows 128), then one
-// thread issues four 128 x 128 x 16 MMAs reading both operands through shared-memory descriptors
-// and accumulating into 128 TMEM columns, and commits them to an mbarrier the CTA waits on before
-// the next step overwrites the tiles.  The epilogue reads the accumulator back with tcgen05.ld
-// (warp w holds rows 32w .. 32w+31, a thread one row) and applies the bias / SiLU / SiLU-derivative.
-// Every wait on the mbarrier is bounded: on expiry the kernel records an error in *err, stops
-// issuing, waits (bounded again) for what it issued, releases its tensor memory and returns.
-constexpr int UM_TILE = 128, UM_BK = 64;
-constexpr uint32_t UM_A = 0, UM_B = 16384, UM_BAR = 32768, UM_SLOT = 32776;
-constexpr size_t UM_SMEM = 72 * 1024;        // 32 KB of tiles, padded so that at most 3 CTAs (384 of the
-                                             // 512 TMEM columns) share an SM
-constexpr uint32_t UM_COLS = 128;            // FP32 accumulator columns
+// matrices: element (r, k) of an R-row tile at ((k/8)(R/8) + r/8) 128 + (r%8) 16 + (k%8) 2 bytes,
+// so the byte stride between core matrices along K is 16 R and along the rows 128), one thread
+// issues four 128 x 64 x 16 MMAs reading both operands through shared-memory descriptors and
+// accumulating into 64 tensor-memory columns, and commits them to an mbarrier.  The tiles are
+// double-buffered: the next K step is staged while the MMAs of this one run, and a buffer is
+// overwritten only after the MMAs that read it have completed.  Staging issues all of a thread's
+// global loads (float4 along the contiguous dimension where the rows are 16-byte aligned) before
+// converting and storing any, so their latencies overlap.  The epilogue reads the accumulator back
+// with tcgen05.ld (warp w holds rows 32w .. 32w+31, a thread one row) and applies the bias / SiLU /
+// SiLU-derivative.  Every wait on the mbarrier is bounded: on expiry the kernel records an error
+// in *err, stops issuing, waits (bounded again) for what it issued, releases its tensor memory and
+// returns.
+constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 64;
+constexpr uint32_t UM_ABYTES = UM_BM * UM_BK * 2, UM_BBYTES = UM_BN * UM_BK * 2;
+constexpr uint32_t UM_STAGE = UM_ABYTES + UM_BBYTES;                 // one buffer: A then B
+constexpr uint32_t UM_BAR = 2 * UM_STAGE, UM_SLOT = UM_BAR + 8;
+constexpr size_t UM_SMEM = 72 * 1024;        // 48 KB of tiles, padded so that at most 3 CTAs share an SM
+constexpr uint32_t UM_COLS = 64;             // FP32 accumulator columns (a power of two >= 32)
 constexpr long UM_WAIT_LIMIT = 1L << 22;     // mbarrier polls before the kernel gives up
 // instruction descriptor (kind::f16): F32 accumulator (bits 4-5 = 1), A and B BF16 (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_TILE >> 3) << 17) |
-                              ((uint32_t)(UM_TILE >> 4) << 24);
+constexpr uint32_t UM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UM_BN >> 3) << 17) |
+                              ((uint32_t)(UM_BM >> 4) << 24);
 
+template <int R>
 __device__ __forceinline__ uint32_t um_core_off(int r, int k)
 {
-    return (uint32_t)((((k >> 3) * (UM_TILE / 8) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+    return (uint32_t)((((k >> 3) * (R / 8) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
 // shared-memory matrix descriptor: start address, leading-dimension (K) byte offset, stride (row
@@ -99,6 +105,51 @@ __device__ __forceinline__ bool um_wait(uint32_t bar, uint32_t phase)
     return false;
 }
 
+// Stage rows r0 .. r0+R-1 and k0 .. k0+63 of an operand as BF16 into dst (K-major core layout).
+// KC: element (r, k) at X[r*ld + k] (contiguous in k); otherwise at X[k*ld + r] (contiguous in r).
+// Outside rows x K: zero.  vec: 16-byte aligned rows (float4 loads along the contiguous dimension).
+template <int R, bool KC>
+__device__ __forceinline__ void um_stage(unsigned char* dst, const float* __restrict__ X, int ld, int r0, int rows,
+                                         int k0, int K, int tid, bool vec)
+{
+    constexpr int NV = R * UM_BK / 4 / 128;              // float4 groups per thread
+    float v[NV][4];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int e = tid + 128 * i;
+        int r, c;                                        // the group's first (row, k)
+        if (KC) { r = e / (UM_BK / 4); c = (e % (UM_BK / 4)) * 4; } else { c = e / (R / 4); r = (e % (R / 4)) * 4; }
+        const int gr = r0 + r, gk = k0 + c;
+        if (vec && (KC ? (gr < rows && gk + 3 < K) : (gk < K && gr + 3 < rows))) {
+            const float4 q = *reinterpret_cast<const float4*>(KC ? X + (size_t)gr * ld + gk : X + (size_t)gk * ld + gr);
+            v[i][0] = q.x; v[i][1] = q.y; v[i][2] = q.z; v[i][3] = q.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int rr = KC ? gr : gr + j, kk = KC ? gk + j : gk;
+                v[i][j] = (rr < rows && kk < K) ? X[KC ? (size_t)rr * ld + kk : (size_t)kk * ld + rr] : 0.0f;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int e = tid + 128 * i;
+        int r, c;
+        if (KC) { r = e / (UM_BK / 4); c = (e % (UM_BK / 4)) * 4; } else { c = e / (R / 4); r = (e % (R / 4)) * 4; }
+        if (KC) {        // four consecutive k of one row: 8 contiguous bytes of a core-matrix row
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[i][0], v[i][1]), hi = __floats2bfloat162_rn(v[i][2], v[i][3]);
+            uint2 w;
+            w.x = *reinterpret_cast<uint32_t*>(&lo);
+            w.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(dst + um_core_off<R>(r, c)) = w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                *reinterpret_cast<__nv_bfloat16*>(dst + um_core_off<R>(r + j, c)) = __float2bfloat16_rn(v[i][j]);
+        }
+    }
+}
+
 template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const float* __restrict__ A, int lda,
                                                    const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
@@ -107,9 +158,11 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * UM_TILE, n0 = blockIdx.x * UM_TILE;
+    const int m0 = blockIdx.y * UM_BM, n0 = blockIdx.x * UM_BN;
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(sm);
-    const uint32_t sA = s0 + UM_A, sB = s0 + UM_B, bar = s0 + UM_BAR;
+    const uint32_t bar = s0 + UM_BAR;
+    const bool va = (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    const bool vb = (ldb & 3) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s0 + UM_SLOT),
                      "r"(UM_COLS)
@@ -120,39 +173,25 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // the first K step's tiles into buffer 0
+    um_stage<UM_BM, !TA>(sm, A, lda, m0, M, 0, K, tid, va);
+    um_stage<UM_BN, TB>(sm + UM_ABYTES, B, ldb, n0, N, 0, K, tid, vb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");      // visible to the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + UM_SLOT);
-    uint32_t phase = 0;
+    const int steps = (K + UM_BK - 1) / UM_BK;
     bool ok = true;
-    for (int k0 = 0; k0 < K && ok; k0 += UM_BK) {
-        // ---- stage op(A) rows m0.. and op(B) columns n0.. of this K step as BF16, K-major
-        for (int e = tid; e < UM_TILE * UM_BK; e += 128) {
-            int r, c;
-            if (!TA) { r = e >> 6; c = e & 63; } else { c = e >> 7; r = e & 127; }   // coalesced in global
-            const int gm = m0 + r, gk = k0 + c;
-            float v = 0.0f;
-            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            *reinterpret_cast<__nv_bfloat16*>(sm + UM_A + um_core_off(r, c)) = __float2bfloat16_rn(v);
-        }
-        for (int e = tid; e < UM_TILE * UM_BK; e += 128) {
-            int r, c;       // r: n offset, c: k offset
-            if (TB) { r = e >> 6; c = e & 63; } else { c = e >> 7; r = e & 127; }
-            const int gn = n0 + r, gk = k0 + c;
-            float v = 0.0f;
-            if (gn < N && gk < K) v = TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-            *reinterpret_cast<__nv_bfloat16*>(sm + UM_B + um_core_off(r, c)) = __float2bfloat16_rn(v);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor cores
-        __syncthreads();
+    uint32_t gave_up = 0;                    // the parity of the commit a failed wait gave up on
+    for (int st = 0; st < steps && ok; ++st) {
+        const uint32_t buf = (uint32_t)(st & 1) * UM_STAGE;
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int kk = 0; kk < UM_BK / 16; ++kk) {
-                const uint64_t da = um_desc(sA + kk * 2 * 2048, 2048, 128);
-                const uint64_t db = um_desc(sB + kk * 2 * 2048, 2048, 128);
-                const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+                const uint64_t da = um_desc(s0 + buf + kk * 2 * (16 * UM_BM), 16 * UM_BM, 128);
+                const uint64_t db = um_desc(s0 + buf + UM_ABYTES + kk * 2 * (16 * UM_BN), 16 * UM_BN, 128);
+                const uint32_t acc = (st > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -162,15 +201,22 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                          : "memory");
         }
-        ok = __syncthreads_and(um_wait(bar, phase) ? 1 : 0) != 0;      // one decision for the CTA
-        phase ^= 1u;
+        // the next K step into the other buffer while these MMAs run (its MMAs completed last step)
+        if (st + 1 < steps) {
+            const uint32_t nb = (uint32_t)((st + 1) & 1) * UM_STAGE;
+            um_stage<UM_BM, !TA>(sm + nb, A, lda, m0, M, (st + 1) * UM_BK, K, tid, va);
+            um_stage<UM_BN, TB>(sm + nb + UM_ABYTES, B, ldb, n0, N, (st + 1) * UM_BK, K, tid, vb);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        ok = __syncthreads_and(um_wait(bar, (uint32_t)(st & 1)) ? 1 : 0) != 0;     // one decision for the CTA
+        if (!ok) gave_up = (uint32_t)(st & 1);
         if (!ok && tid == 0) atomicExch(err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
         // ---- epilogue: row m0 + 32 warp + lane, 8 accumulator columns at a time
         const int m = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < UM_TILE && n0 + c0 < N; c0 += 8) {
+        for (int c0 = 0; c0 < UM_BN && n0 + c0 < N; c0 += 8) {
             uint32_t r[8];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
@@ -200,7 +246,8 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
             }
         }
     } else {
-        um_wait(bar, phase ^ 1u);           // what was issued before the wait gave up (bounded)
+        // the commit the wait gave up on (bounded again): its MMAs may still read the tiles
+        um_wait(bar, gave_up);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -483,7 +530,7 @@ int gemm(helios_mlp* m, int M, int N, int K, const float* A, int lda, const floa
         MLP_CUDA(cudaFuncSetAttribute(mlp_umma<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UM_SMEM));
         configured[m->device] = 1;
     }
-    dim3 grid((N + UM_TILE - 1) / UM_TILE, (M + UM_TILE - 1) / UM_TILE);
+    dim3 grid((N + UM_BN - 1) / UM_BN, (M + UM_BM - 1) / UM_BM);
     mlp_umma<TA, TB, EPI><<<grid, 128, UM_SMEM, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Zout, Zin, ldz, scale,
                                                       m->err);
     MLP_CUDA(cudaGetLastError());

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI vs the FP64 CPU oracle on the same seeded inputs.
 
-Tolerances (stated in the design notes): table indices and weights bit-exact; opacities 2e-6
+Tolerances: table indices and weights bit-exact; opacities 2e-6
 relative (float32 bilinear of the float32 table); bolometric fluxes 1e-5 relative; net flux 1e-5
 of the local flux; emergent spectrum 1e-5 of the bin's larger TOA stream; one temperature step
 1e-12 relative with bit-exact multipliers and sign histories; converged temperatures 0.1 K.
