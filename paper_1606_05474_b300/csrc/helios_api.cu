@@ -79,13 +79,6 @@ size_t sweep_smem(int M, int G, int cl = 32) { return sweep_smem_bytes(M, G, cl)
 // per-atmosphere temperature-step block (post_kernel); wider ones by finalize_kernel
 constexpr int kFuseFinalizeItems = 64;
 
-// lane chunks up to 7 fit two 640-thread blocks per SM within the register file (48 registers)
-// Two 640-thread blocks per SM (48 registers, some spilled to L1) up to lane chunk 11 for the
-// passes and 7 for the exact column solve, which holds more per-lane arrays; one block (96
-// registers) beyond.  Measured: occupancy outweighs the spills up to there (2 blocks at chunk 13
-// were slower again).
-template <int M, bool DIRECT> constexpr int sweep_minb() { return (M <= (DIRECT ? 7 : 11)) ? 2 : 1; }
-
 // 16-lane columns (two per warp), 320-thread blocks: three per SM (64 registers, a few spilled)
 // up to lane chunk 11, two (96 registers) beyond.  Measured on the full-size bins: three blocks
 // are 5-14 % faster than two up to chunk 11; four at chunks 5-7 were slower again
@@ -427,8 +420,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     // ---- work items: tiles of TB bins
     // bins per work item: one resident wave of blocks (at the sweep occupancy of the widest
     // atmosphere) for a single atmosphere, capped for long batches so the tail stays short.
-    // Block: one warp per Gauss point, or per two with 16-lane columns
-    auto block_threads = [G](int cl) { return cl == 16 ? 32 * ((G + 1) / 2) : 32 * G; };
+    // Block (iterated passes): one warp per two Gauss points
+    const int threads = sweep_block_threads(G, false);
     int amax = 0;
     for (int a = 0; a < A; ++a)
         if (ad[a].n > ad[amax].n) amax = a;
@@ -437,7 +430,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
         const int cm = ad[amax].cl, mm = ad[amax].M;
-        const int per_sm = std::max(1, sweep_occupancy(mm, block_threads(cm), sweep_smem(mm, G, cm), false, cm));
+        const int per_sm = std::max(1, sweep_occupancy(mm, threads, sweep_smem(mm, G, cm), false, cm));
         TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + (int64_t)nsm * per_sm - 1) / ((int64_t)nsm * per_sm)));
     }
     P->TB = TB;
@@ -588,7 +581,7 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         std::memset(&gr, 0, sizeof gr);
         gr.cl = key > kMaxM ? 16 : 32;
         gr.M = key - (gr.cl == 16 ? kMaxM + 1 : 0);
-        gr.threads = block_threads(gr.cl);
+        gr.threads = threads;
         // the exact solve runs 32 lanes per column: a chunk covering the group's longest column
         gr.M_direct = gr.cl == 32 ? gr.M : lane_chunk((gr.cl * gr.M - 1) / 2, 32);
         gr.count = (int)byM[key].size();

@@ -575,9 +575,27 @@ __host__ __device__ constexpr size_t sweep_smem_bytes(int M, int G, int CL = 32)
            (2 * (size_t)G * (CL * M + 1) + 4 * (size_t)(CL * M) + 1) * sizeof(float);
 }
 
+// threads of a sweep block: the exact solve takes one warp per Gauss point; the iterated passes
+// take one warp per two Gauss points -- with 16-lane columns both at once (lanes 0-15 and 16-31),
+// with 32-lane columns one after the other
+__host__ __device__ constexpr int sweep_block_threads(int G, bool direct)
+{
+    return direct ? 32 * G : 32 * ((G + 1) / 2);
+}
+
+// resident blocks per SM that a sweep kernel is compiled for (its register budget): 32-lane
+// columns, iterated passes -- three 320-thread blocks (64 registers) up to lane chunk 7, two (96)
+// beyond; the exact solve -- two 640-thread blocks (48 registers) up to chunk 7, one beyond
+template <int M, bool DIRECT>
+constexpr int sweep_minb()
+{
+    return DIRECT ? (M <= 7 ? 2 : 1) : (M <= 7 ? 3 : 2);
+}
+
 // ---------------------------------------------------------------------------
 // one work item = (atmosphere, tile of bins); the whole block cooperates
-// CL = 32: one warp per Gauss point; CL = 16: two Gauss points per warp (lanes 0-15 and 16-31),
+// CL = 32: a warp per Gauss point (the exact solve: all at once; the passes: the block's warps
+// take the Gauss points in rounds); CL = 16: two Gauss points per warp (lanes 0-15 and 16-31),
 // half the scan levels and fewer padded slots per column, at twice the registers per lane
 template <int M, bool DIRECT, int CL = 32>
 __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int* __restrict__ status, int n_passes,
@@ -590,10 +608,11 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     constexpr int LV = CL == 32 ? 5 : 4;    // scan levels
     const int G = P.G;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int g_raw = CL == 32 ? tid >> 5 : 2 * (tid >> 5) + (lane >> 4);
+    // the Gauss point of this thread's column in the first round, and the Gauss points a round
+    // covers (the exact solve: every point in one round)
+    const int g_first = CL == 32 ? tid >> 5 : 2 * (tid >> 5) + (lane >> 4);
+    const int g_round = CL == 32 ? (int)(blockDim.x >> 5) : 2 * (int)(blockDim.x >> 5);
     const int sub = lane & (CL - 1);        // the lane's place in its column
-    const bool g_ok = g_raw < G;            // odd G, CL = 16: the last warp's upper half is idle
-    const int g = g_ok ? g_raw : G - 1;
     const int2 it = P.items[item];
     if (status && status[it.x] != 0) return;
     const AtmDesc ad = P.atms[it.x];
@@ -614,7 +633,6 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
     const int nthreads = blockDim.x;
     for (int t = tid; t < W; t += nthreads) dm[t] = t < NS ? P.dm[ad.sub_off + t] : 0.0f;
     for (int t = tid; t < 3 * (n + 1); t += nthreads) acc[t] = 0.0;
-    const float wg = g_ok ? P.gw[g] : 0.0f;
     const int p_first = tid / G, g_of = tid - p_first * G;     // gather mapping: consecutive g
     const int p_stride = nthreads / G;
     // float4 gather over four consecutive g when rows stay 16-byte aligned
@@ -753,7 +771,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         // ---- phase 2: CL lanes per Gauss point; lane `sub` of a column holds its sublayers
         // sub*M .. sub*M+M-1 (the exact solve: CL = 32)
         if constexpr (DIRECT) {
-            // the exact column solution (no passes, no warm start needed)
+            // the exact column solution (no passes, no warm start needed); a warp per Gauss point
+            const int g = g_first;
+            const float wg = P.gw[g];
             float Ts[M], Rs[M], Ss[M], Es[M], U[M], Dn[M];
             const float* krow = kap + g * KST;
             const float omq = __fdiv_rn(bc.omq2, 1.0f + bc.q);     // 1 - q
@@ -806,139 +826,150 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 red_up[k] = wg * U[k];
             }
         } else {
-            float Ts[M], Rs[M], Ss[M], X[M + 1];
-            float Ap = 1.0f;
-            const float* krow = kap + g * KST;
-            if (bc.flags & BIN_RAYLEIGH) {                                      // uniform per bin
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const int s = sub * M + k;
-                    float t, r, src;                                    // padding: (1, 0, 0)
-                    float kt;
-                    const BinConst c = rayleigh_const(bc, P, 0.5f * (krow[s] + krow[s + 1]), kt);
-                    layer_coef(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src);
-                    Ts[k] = t;
-                    Rs[k] = r;
-                    Ss[k] = src;
-                    Ap *= t;
-                }
-            } else if (P.utab) {                                                // uniform per launch
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const int s = sub * M + k;
-                    float t, r, src;                                    // padding: (1, 0, 0)
-                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                    layer_coef<false, true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, nullptr, 0.0f, P.utab);
-                    Ts[k] = t;
-                    Rs[k] = r;
-                    Ss[k] = src;
-                    Ap *= t;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const int s = sub * M + k;
-                    float t, r, src;                                    // padding: (1, 0, 0)
-                    const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                    layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
-                    Ts[k] = t;
-                    Rs[k] = r;
-                    Ss[k] = src;
-                    Ap *= t;
-                }
-            }
-            // scan multipliers (depend on the transmissions only)
-            float adn[LV], aup[LV], adn_fin, aup_fin;
-            {
-                float a = Ap;
-#pragma unroll
-                for (int lv = 0; lv < LV; ++lv) {
-                    const int d = 1 << lv;
-                    const float ao = __shfl_down_sync(FULL, a, d, CL);
-                    const bool ok = sub + d < CL;
-                    adn[lv] = ok ? a : 0.0f;
-                    a = ok ? a * ao : a;
-                }
-                adn_fin = a;
-                a = Ap;
-#pragma unroll
-                for (int lv = 0; lv < LV; ++lv) {
-                    const int d = 1 << lv;
-                    const float ao = __shfl_up_sync(FULL, a, d, CL);
-                    const bool ok = sub >= d;
-                    aup[lv] = ok ? a : 0.0f;
-                    a = ok ? a * ao : a;
-                }
-                aup_fin = a;
-            }
-            // initial upward deviation: previous evaluation shifted to the new Planck values, or
-            // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero)
-            const long long col = (long long)(l * G + g) * W;
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-                const int p = sub * M + k;
-                X[k] = (warm_valid && wbase) ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
-            }
-            X[M] = 0.0f;
-            const float toa_g = bc_toa[0];
-            const float bint = bc.bint;
-            __syncwarp();
-            // weighted deviations of every point of the column (phase 3 reads the interfaces);
-            // the opacity row is free now
-            float* red_dn = kap + g * KST + sub * M;
-            float* red_up = upr + g * KST + sub * M;
-            const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
-            for (int pass = 0; pass < K; ++pass) {
-                const bool last = pass == K - 1;
-                // downward sweep: G_dn[s] = Ts G_dn[s+1] + (Rs G_up[s] - Ss), from the TOA
-                {
-                    // G_up[s] enters only through Rs G_up[s] - Ss: X[k] is replaced by that term
-                    float b = 0.0f;
-#pragma unroll
-                    for (int k = M - 1; k >= 0; --k) {
-                        X[k] = fmaf(Rs[k], X[k], -Ss[k]);
-                        b = fmaf(Ts[k], b, X[k]);
-                    }
-#pragma unroll
-                    for (int lv = 0; lv < LV; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv, CL), b);
-                    const float outv = fmaf(adn_fin, toa_g, b);
-                    float inv = __shfl_down_sync(FULL, outv, 1, CL);
-                    if (sub == CL - 1) inv = toa_g;
-                    X[M] = inv;
-#pragma unroll
-                    for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], X[k]);
-                    if (last && g_ok) {
-#pragma unroll
-                        for (int k = 0; k < M; ++k) red_dn[k] = wg * X[k];
-                    }
-                }
-                // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
-                {
-                    // G_dn[s+1] enters only through Rs G_dn[s+1] + Ss: X[k+1] is replaced by that term
-                    float c = 0.0f;
+            // the Gauss points in rounds of g_round (the block holds a warp per two Gauss points:
+            // one round of two columns per warp at CL = 16, two rounds at CL = 32; odd G: the last
+            // warp idles in the last round, or its upper half does)
+            constexpr int ROUNDS = CL == 16 ? 1 : 2;
+#pragma unroll 1
+            for (int r = 0; r < ROUNDS; ++r) {
+                const int g_raw = r * g_round + g_first;
+                const bool g_ok = g_raw < G;
+                const int g = g_ok ? g_raw : G - 1;
+                const float wg = g_ok ? P.gw[g] : 0.0f;
+                float Ts[M], Rs[M], Ss[M], X[M + 1];
+                float Ap = 1.0f;
+                const float* krow = kap + g * KST;
+                if (bc.flags & BIN_RAYLEIGH) {                                      // uniform per bin
 #pragma unroll
                     for (int k = 0; k < M; ++k) {
-                        X[k + 1] = fmaf(Rs[k], X[k + 1], Ss[k]);
-                        c = fmaf(Ts[k], c, X[k + 1]);
+                        const int s = sub * M + k;
+                        float t, r, src;                                    // padding: (1, 0, 0)
+                        float kt;
+                        const BinConst c = rayleigh_const(bc, P, 0.5f * (krow[s] + krow[s + 1]), kt);
+                        layer_coef(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src);
+                        Ts[k] = t;
+                        Rs[k] = r;
+                        Ss[k] = src;
+                        Ap *= t;
                     }
+                } else if (P.utab) {                                                // uniform per launch
 #pragma unroll
-                    for (int lv = 0; lv < LV; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv, CL), c);
-                    const float boa = __shfl_sync(FULL, X[0], 0, CL) + bint;
-                    const float outv = fmaf(aup_fin, boa, c);
-                    float inv = __shfl_up_sync(FULL, outv, 1, CL);
-                    if (sub == 0) inv = boa;
-                    X[0] = inv;
+                    for (int k = 0; k < M; ++k) {
+                        const int s = sub * M + k;
+                        float t, r, src;                                    // padding: (1, 0, 0)
+                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                        layer_coef<false, true>(bc, dtau, dbt[s], P.dtau_iso, t, r, src, nullptr, 0.0f, P.utab);
+                        Ts[k] = t;
+                        Rs[k] = r;
+                        Ss[k] = src;
+                        Ap *= t;
+                    }
+                } else {
 #pragma unroll
-                    for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], X[k + 1]);
-                    if (last && g_ok) {
-#pragma unroll
-                        for (int k = 0; k < M; ++k) red_up[k] = wg * X[k];
+                    for (int k = 0; k < M; ++k) {
+                        const int s = sub * M + k;
+                        float t, r, src;                                    // padding: (1, 0, 0)
+                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
+                        layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
+                        Ts[k] = t;
+                        Rs[k] = r;
+                        Ss[k] = src;
+                        Ap *= t;
                     }
                 }
-            }
-            if (g_ok && wbase) {
+                // scan multipliers (depend on the transmissions only)
+                float adn[LV], aup[LV], adn_fin, aup_fin;
+                {
+                    float a = Ap;
 #pragma unroll
-                for (int k = 0; k < M; ++k) wbase[col + k * CL + sub] = X[k];
+                    for (int lv = 0; lv < LV; ++lv) {
+                        const int d = 1 << lv;
+                        const float ao = __shfl_down_sync(FULL, a, d, CL);
+                        const bool ok = sub + d < CL;
+                        adn[lv] = ok ? a : 0.0f;
+                        a = ok ? a * ao : a;
+                    }
+                    adn_fin = a;
+                    a = Ap;
+#pragma unroll
+                    for (int lv = 0; lv < LV; ++lv) {
+                        const int d = 1 << lv;
+                        const float ao = __shfl_up_sync(FULL, a, d, CL);
+                        const bool ok = sub >= d;
+                        aup[lv] = ok ? a : 0.0f;
+                        a = ok ? a * ao : a;
+                    }
+                    aup_fin = a;
+                }
+                // initial upward deviation: previous evaluation shifted to the new Planck values, or
+                // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero)
+                const long long col = (long long)(l * G + g) * W;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int p = sub * M + k;
+                    X[k] = (warm_valid && wbase) ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
+                }
+                X[M] = 0.0f;
+                const float toa_g = bc_toa[0];
+                const float bint = bc.bint;
+                __syncwarp();
+                // weighted deviations of every point of the column (phase 3 reads the interfaces);
+                // the opacity row is free now
+                float* red_dn = kap + g * KST + sub * M;
+                float* red_up = upr + g * KST + sub * M;
+                const int K = (bc.flags & BIN_NO_SCAT) ? 1 : n_passes;
+                for (int pass = 0; pass < K; ++pass) {
+                    const bool last = pass == K - 1;
+                    // downward sweep: G_dn[s] = Ts G_dn[s+1] + (Rs G_up[s] - Ss), from the TOA
+                    {
+                        // G_up[s] enters only through Rs G_up[s] - Ss: X[k] is replaced by that term
+                        float b = 0.0f;
+#pragma unroll
+                        for (int k = M - 1; k >= 0; --k) {
+                            X[k] = fmaf(Rs[k], X[k], -Ss[k]);
+                            b = fmaf(Ts[k], b, X[k]);
+                        }
+#pragma unroll
+                        for (int lv = 0; lv < LV; ++lv) b = fmaf(adn[lv], __shfl_down_sync(FULL, b, 1 << lv, CL), b);
+                        const float outv = fmaf(adn_fin, toa_g, b);
+                        float inv = __shfl_down_sync(FULL, outv, 1, CL);
+                        if (sub == CL - 1) inv = toa_g;
+                        X[M] = inv;
+#pragma unroll
+                        for (int k = M - 1; k >= 0; --k) X[k] = fmaf(Ts[k], X[k + 1], X[k]);
+                        if (last && g_ok) {
+#pragma unroll
+                            for (int k = 0; k < M; ++k) red_dn[k] = wg * X[k];
+                        }
+                    }
+                    // upward sweep: G_up[s+1] = Ts G_up[s] + (Rs G_dn[s+1] + Ss), from the BOA (eq. 22)
+                    {
+                        // G_dn[s+1] enters only through Rs G_dn[s+1] + Ss: X[k+1] is replaced by that term
+                        float c = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < M; ++k) {
+                            X[k + 1] = fmaf(Rs[k], X[k + 1], Ss[k]);
+                            c = fmaf(Ts[k], c, X[k + 1]);
+                        }
+#pragma unroll
+                        for (int lv = 0; lv < LV; ++lv) c = fmaf(aup[lv], __shfl_up_sync(FULL, c, 1 << lv, CL), c);
+                        const float boa = __shfl_sync(FULL, X[0], 0, CL) + bint;
+                        const float outv = fmaf(aup_fin, boa, c);
+                        float inv = __shfl_up_sync(FULL, outv, 1, CL);
+                        if (sub == 0) inv = boa;
+                        X[0] = inv;
+#pragma unroll
+                        for (int k = 0; k < M; ++k) X[k + 1] = fmaf(Ts[k], X[k], X[k + 1]);
+                        if (last && g_ok) {
+#pragma unroll
+                            for (int k = 0; k < M; ++k) red_up[k] = wg * X[k];
+                        }
+                    }
+                }
+                if (g_ok && wbase) {
+#pragma unroll
+                    for (int k = 0; k < M; ++k) wbase[col + k * CL + sub] = X[k];
+                }
             }
         }
         __syncthreads();
@@ -1003,10 +1034,10 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
 // counts the blocks that have left, and the last one to leave returns both to zero for the
 // next launch (every block has then stopped pulling), so no reset is needed between launches.
 template <int M, int MINB, bool DIRECT = false, int CL = 32>
-__global__ void __launch_bounds__(20 * CL, MINB) sweep_kernel(PlanDev P, const int* __restrict__ order, int count,
-                                                             int* __restrict__ counter, const int* __restrict__ status,
-                                                             int n_passes, int warm_valid, float* __restrict__ Fup_toa,
-                                                             float* __restrict__ F_spec)
+__global__ void __launch_bounds__(sweep_block_threads(20, DIRECT), MINB)
+    sweep_kernel(PlanDev P, const int* __restrict__ order, int count, int* __restrict__ counter,
+                 const int* __restrict__ status, int n_passes, int warm_valid, float* __restrict__ Fup_toa,
+                 float* __restrict__ F_spec)
 {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -102,13 +102,14 @@ struct Carve {
 template <int M>
 int launch_sweep(const PlanDev& P, int dev, int count, const int* order, int n_passes, float* toa, cudaStream_t s)
 {
-    constexpr int MINB = M <= 7 ? 2 : 1;
+    constexpr int MINB = sweep_minb<M, false>();
     const size_t smem = sweep_smem_bytes(M, P.G);
     if (!g_smem_set[dev][M]) {
         NA_CUDA(cudaFuncSetAttribute(sweep_kernel<M, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         g_smem_set[dev][M] = true;
     }
-    sweep_kernel<M, MINB><<<count, 32 * P.G, smem, s>>>(P, order, count, nullptr, nullptr, n_passes, 0, toa, nullptr);
+    sweep_kernel<M, MINB><<<count, sweep_block_threads(P.G, false), smem, s>>>(P, order, count, nullptr, nullptr,
+                                                                              n_passes, 0, toa, nullptr);
     NA_CUDA(cudaGetLastError());
     return HELIOS_OK;
 }
