@@ -395,12 +395,16 @@ __device__ __forceinline__ BinConst rayleigh_const(const BinConst& b, const Plan
 // With WANT_E the absorption Es = 1 - Ts - Rs of the sublayer is returned too, formed without
 // cancellation: expanding eqs. (12)-(13), 1 - Ts - Rs = (1 - q)(1 - trans)(1 - q trans) d
 // (zero for pure scattering); omq = 1 - q of the bin.
-template <bool WANT_E = false, bool TAB = false>
+// KIND names the bin's kind when the caller knows it (its flags are uniform over a bin), so that
+// the tests of the other kinds' branches drop out of an unrolled loop over the sublayers
+enum { COEF_ANY = 0, COEF_GENERAL = 1, COEF_NO_SCAT = 2, COEF_PURE_SCAT = 3 };
+
+template <bool WANT_E = false, bool TAB = false, int KIND = COEF_ANY>
 __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
                                            float& Ts, float& Rs, float& Ss, float* Es = nullptr, float omq = 0.0f,
                                            const float* utab = nullptr)
 {
-    if (b.flags & BIN_PURE_SCAT) {          // eq. (14): no thermal source
+    if (KIND == COEF_PURE_SCAT || (KIND == COEF_ANY && (b.flags & BIN_PURE_SCAT))) {   // eq. (14): no thermal source
         const float a = b.gam * dtau;
         const float t = __frcp_rn(1.0f + a);
         Ts = t;
@@ -416,7 +420,7 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     if constexpr (TAB) phi_u_t_tab(b.lam * dtau, utab, phi, u, tr);     // Sect. 2.6 table
     else phi_u_t(b.lam * dtau, phi, u, tr); // eq. (8): tr = exp(-lam dtau), u = 1 - tr
     const bool iso = dtau < dtau_iso;       // Sect. 2.2.1: thin sublayers use eq. (11)
-    if (b.flags & BIN_NO_SCAT) {            // zeta_- = 0: Ts = trans, Rs = 0
+    if (KIND == COEF_NO_SCAT || (KIND == COEF_ANY && (b.flags & BIN_NO_SCAT))) {   // zeta_- = 0: Ts = trans, Rs = 0
         Ts = tr;
         Rs = 0.0f;
         Ss = (iso || dtau == 0.0f) ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
@@ -440,6 +444,24 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     Rs = step ? 0.0f : Rs;
     Ss = step ? dB : Ss;
     if constexpr (WANT_E) *Es = step ? 0.0f : omq * u * fmaf(-b.q, tr, 1.0f) * d;
+}
+
+// (Ts, Rs, Ss) of the M sublayers of lane `sub` of a column (sublayer s between points s and
+// s + 1; opacity the mean of the two points', Sect. 2.3, eq. 19) for a bin of kind KIND, and the
+// product Ap of their transmissions.  Padding slots (zero opacity, column mass and Planck
+// difference) take the zero-thickness form (1, 0, 0)
+template <int KIND, int M>
+__device__ __forceinline__ void coef_chunk(const BinConst& bc, const float* krow, const float* dm, const float* dbt,
+                                           int sub, float dtau_iso, float (&Ts)[M], float (&Rs)[M], float (&Ss)[M],
+                                           float& Ap)
+{
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const int s = sub * M + k;
+        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];
+        layer_coef<false, false, KIND>(bc, dtau, dbt[s], dtau_iso, Ts[k], Rs[k], Ss[k]);
+        Ap *= Ts[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -864,18 +886,12 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                         Ss[k] = src;
                         Ap *= t;
                     }
+                } else if (bc.flags & BIN_PURE_SCAT) {                              // uniform per bin
+                    coef_chunk<COEF_PURE_SCAT>(bc, krow, dm, dbt, sub, P.dtau_iso, Ts, Rs, Ss, Ap);
+                } else if (bc.flags & BIN_NO_SCAT) {
+                    coef_chunk<COEF_NO_SCAT>(bc, krow, dm, dbt, sub, P.dtau_iso, Ts, Rs, Ss, Ap);
                 } else {
-#pragma unroll
-                    for (int k = 0; k < M; ++k) {
-                        const int s = sub * M + k;
-                        float t, r, src;                                    // padding: (1, 0, 0)
-                        const float dtau = 0.5f * (krow[s] + krow[s + 1]) * dm[s];   // Sect. 2.3, eq. (19)
-                        layer_coef(bc, dtau, dbt[s], P.dtau_iso, t, r, src);
-                        Ts[k] = t;
-                        Rs[k] = r;
-                        Ss[k] = src;
-                        Ap *= t;
-                    }
+                    coef_chunk<COEF_GENERAL>(bc, krow, dm, dbt, sub, P.dtau_iso, Ts, Rs, Ss, Ap);
                 }
                 // scan multipliers (depend on the transmissions only)
                 float adn[LV], aup[LV], adn_fin, aup_fin;
