@@ -5,6 +5,7 @@
 #include "helios_kernels.cuh"
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -630,7 +631,8 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
     dv.iP = d_iP; dv.wP = d_wP; dv.dm = d_dm; dv.lnr = d_lnr; dv.lay_atm = d_lay_atm;
     dv.spec_tab = d_spec_tab; dv.spec_w = d_spec_w;
     dv.btab = d_btab; dv.utab = d_utab;
-    dv.G = G; dv.TB = TB; dv.A = A; dv.dtau_iso = (float)prm->dtau_iso; dv.iso_layers = prm->iso_layers;
+    dv.G = G; dv.TB = TB; dv.A = A; dv.iso_layers = prm->iso_layers;
+    dv.dtau_iso = std::max((float)prm->dtau_iso, FLT_MIN);
     dv.D = (float)prm->D; dv.eps = (float)(1.0 / prm->D); dv.w0_pure = (float)prm->w0_pure;
     dv.printed_gradient = prm->printed_gradient;
     P->atms_h = ad;

@@ -48,7 +48,7 @@ constexpr int BIN_GREY_THERM = 8;   // grey mode thermal band: pi B = sigma T^4
 constexpr int BIN_RAYLEIGH = 16;    // H2 Rayleigh opacity kappa_R (in `lam`) added to every sublayer;
                                     // omega0 per sublayer and g (g0 in `q`), constants per sublayer
 
-struct BinConst {
+struct __align__(16) BinConst {
     float xs;      // h c nu_c / k_B  (x = xs / T), high part
     float xs_lo;   // low part of h c nu_c / k_B (float-float)
     float E;       // 2 pi eps * 2 h c^2 nu_c^3 dnu  (2 pi eps B_l(T) = E / (e^x - 1)); eps sigma in grey mode
@@ -56,11 +56,14 @@ struct BinConst {
     float bint;    // internal flux entering at the BOA (eq. 22)
     float lam;     // D sqrt((1 - w0 g0)(1 - w0))  (eq. 8 exponent per unit dtau)
     float q;       // zeta_- / zeta_+  (eq. 13)
-    float q2;      // q^2
-    float omq2;    // 1 - q^2
+    float c2;      // q^2 / (1 - q^2)
+    float qo;      // q / (1 - q^2)
+    float hoh;     // 1 / (2 (1 - q))
     float cl;      // lam * eps / (1 - w0 g0): gradient prefactor of eq. (15) times lam
+    float clh;     // cl / (1 - q)
     float gam;     // D (1 - g0) / 2: pure-scattering coupling, eq. (14)
     int flags;
+    float pad[2];
 };
 
 struct AtmDesc {
@@ -112,7 +115,7 @@ struct PlanDev {
     float* warm;                // warm-start G_up per column, lane-interleaved
     double* part;               // per-item partial sums [3][n+1]
     int G, TB, A;
-    float dtau_iso;
+    float dtau_iso;             // at least FLT_MIN: a zero-thickness sublayer takes the isothermal form
     float D, eps, w0_pure;      // per-sublayer two-stream constants (Rayleigh scattering)
     int printed_gradient;
     int iso_layers;             // 1: isothermal-layer grid (both points of layer i at T_i)
@@ -384,24 +387,31 @@ __device__ __forceinline__ BinConst rayleigh_const(const BinConst& b, const Plan
     const float q = __fdiv_rn(omr, 1.0f + r);
     c.lam = P.D * sqrtf(omwg * omw);                           // eq. (8)
     c.q = q;
-    c.q2 = q * q;
-    c.omq2 = __fdiv_rn(4.0f * r, (1.0f + r) * (1.0f + r));     // 1 - q^2
+    // with 1 - q = 2 r / (1 + r) and 1 - q^2 = 4 r / (1 + r)^2
+    const float i4r = __frcp_rn(4.0f * r);
+    c.hoh = (1.0f + r) * i4r;
+    c.c2 = omr * omr * i4r;
+    c.qo = omr * (1.0f + r) * i4r;
     c.cl = c.lam * __fdiv_rn(P.eps, P.printed_gradient ? fmaf(kR * inv, g0, 1.0f) : omwg);
+    c.clh = 2.0f * c.cl * c.hoh;
     return c;
 }
 
 // Two-stream coefficients of one sublayer in deviation form (see file header).
 // dB = 2 pi eps (B_bottom - B_top).
 // With WANT_E the absorption Es = 1 - Ts - Rs of the sublayer is returned too, formed without
-// cancellation: expanding eqs. (12)-(13), 1 - Ts - Rs = (1 - q)(1 - trans)(1 - q trans) d
-// (zero for pure scattering); omq = 1 - q of the bin.
+// cancellation: expanding eqs. (12)-(13), 1 - Ts - Rs = (1 - trans)(1 - q trans) d / (1 + q)
+// (zero for pure scattering); eo = 1 / (1 + q) of the bin.
+// A zero-thickness sublayer (the step between two isothermal layers, or a padding slot) gives
+// exactly (1, 0, dB): trans = 1 and 1 - trans = 0 exactly, d = 1, and it takes the isothermal
+// form (the threshold dtau_iso is at least the smallest normal float)
 // KIND names the bin's kind when the caller knows it (its flags are uniform over a bin), so that
 // the tests of the other kinds' branches drop out of an unrolled loop over the sublayers
 enum { COEF_ANY = 0, COEF_GENERAL = 1, COEF_NO_SCAT = 2, COEF_PURE_SCAT = 3 };
 
 template <bool WANT_E = false, bool TAB = false, int KIND = COEF_ANY>
 __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float dB, float dtau_iso,
-                                           float& Ts, float& Rs, float& Ss, float* Es = nullptr, float omq = 0.0f,
+                                           float& Ts, float& Rs, float& Ss, float* Es = nullptr, float eo = 0.0f,
                                            const float* utab = nullptr)
 {
     if (KIND == COEF_PURE_SCAT || (KIND == COEF_ANY && (b.flags & BIN_PURE_SCAT))) {   // eq. (14): no thermal source
@@ -423,27 +433,24 @@ __device__ __forceinline__ void layer_coef(const BinConst& b, float dtau, float 
     if (KIND == COEF_NO_SCAT || (KIND == COEF_ANY && (b.flags & BIN_NO_SCAT))) {   // zeta_- = 0: Ts = trans, Rs = 0
         Ts = tr;
         Rs = 0.0f;
-        Ss = (iso || dtau == 0.0f) ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
+        Ss = iso ? 0.5f * dB * (1.0f + tr) : b.cl * dB * phi;
         if constexpr (WANT_E) *Es = u;
         return;
     }
-    // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha.  The reciprocal that
-    // enters Ts, Rs and Ss is accurate to an ulp without bias: the bare approximate one rounds
-    // with a bias that adds up coherently over the layers a reflected flux crosses (1e-5 in
-    // scattering bins)
+    // eqs. (12)-(13) divided by -zeta_+^2: Ts = xi/alpha, Rs = -beta/alpha, i.e. with
+    // d = (1 - q^2) / (1 - q^2 trans^2) = 1 / (1 + c2 (1 - trans^2)):  Ts = trans d and
+    // Rs = qo (1 - trans^2) d; the source term's (1 - Ts + Rs)/u = (1 + q - q u) d / (1 - q).
+    // The reciprocal is accurate to an ulp without bias: the bare approximate one rounds with a
+    // bias that adds up coherently over the layers a reflected flux crosses (1e-5 in scattering
+    // bins)
     const float t2u = u * (2.0f - u);                                   // 1 - trans^2
-    const float d = recip_nr(fmaf(b.q2, t2u, b.omq2));                  // 1 / (1 - q^2 trans^2) >= 1
-    Ts = b.omq2 * tr * d;
-    Rs = b.q * t2u * d;
-    const float h = d * (1.0f + b.q) * fmaf(-b.q, u, 1.0f + b.q);       // (1 - Ts + Rs) / u
-    Ss = iso ? 0.5f * dB * fmaf(-h, u, 2.0f) : b.cl * dB * phi * h;
-    // zero thickness (the step between two isothermal layers): the flux passes unchanged, so
-    // the deviation from the local Planck flux steps by the Planck difference (exact 1, 0, dB)
-    const bool step = dtau == 0.0f;
-    Ts = step ? 1.0f : Ts;
-    Rs = step ? 0.0f : Rs;
-    Ss = step ? dB : Ss;
-    if constexpr (WANT_E) *Es = step ? 0.0f : omq * u * fmaf(-b.q, tr, 1.0f) * d;
+    const float d = recip_nr(fmaf(b.c2, t2u, 1.0f));
+    Ts = tr * d;
+    Rs = b.qo * t2u * d;
+    const float md = d * fmaf(-b.q, u, 1.0f + b.q);
+    // isothermal (eq. 11): dB (1 - (1 - Ts + Rs)/2); otherwise eq. (15): cl phi dB (1 - Ts + Rs)/u
+    Ss = dB * (iso ? fmaf(-b.hoh * md, u, 1.0f) : b.clh * phi * md);
+    if constexpr (WANT_E) *Es = eo * u * fmaf(-b.q, tr, 1.0f) * d;
 }
 
 // (Ts, Rs, Ss) of the M sublayers of lane `sub` of a column (sublayer s between points s and
@@ -798,7 +805,7 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             const float wg = P.gw[g];
             float Ts[M], Rs[M], Ss[M], Es[M], U[M], Dn[M];
             const float* krow = kap + g * KST;
-            const float omq = __fdiv_rn(bc.omq2, 1.0f + bc.q);     // 1 - q
+            const float eo = __frcp_rn(1.0f + bc.q);               // 1 / (1 + q)
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const int s = lane * M + k;
@@ -809,9 +816,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                         float kt;
                         const BinConst c = rayleigh_const(bc, P, kabs, kt);
                         layer_coef<true>(c, kt * dm[s], dbt[s], P.dtau_iso, t, r, src, &e,
-                                         __fdiv_rn(c.omq2, 1.0f + c.q));
+                                         __frcp_rn(1.0f + c.q));
                     } else {
-                        layer_coef<true>(bc, kabs * dm[s], dbt[s], P.dtau_iso, t, r, src, &e, omq);   // eq. (19)
+                        layer_coef<true>(bc, kabs * dm[s], dbt[s], P.dtau_iso, t, r, src, &e, eo);    // eq. (19)
                     }
                 }
                 Ts[k] = t;

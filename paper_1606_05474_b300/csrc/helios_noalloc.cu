@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -233,7 +234,7 @@ extern "C" int helios_flux_sweep_noalloc(const helios_batch_t* b, const helios_k
     NA_CUDA(cudaMemcpyAsync(d_lay, h_lay_atm, sizeof(int) * n, cudaMemcpyHostToDevice, s));
     P.atms = d_atm; P.tabs = d_tab; P.bins = d_bins; P.items = d_items; P.gw = d_gw; P.iP = d_iP; P.wP = d_wP;
     P.dm = d_dm; P.lnr = d_lnr; P.lay_atm = d_lay;
-    P.G = G; P.TB = TB; P.A = 1; P.dtau_iso = (float)prm->dtau_iso;
+    P.G = G; P.TB = TB; P.A = 1; P.dtau_iso = std::max((float)prm->dtau_iso, FLT_MIN);
 
     // ---- one cold-start evaluation: nothing in the scratch is read before this call writes it
     prep_kernel<<<dim3((NP + 63) / 64, 1), 64, 0, s>>>(P, T_layer, nullptr, 0);

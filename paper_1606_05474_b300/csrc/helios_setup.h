@@ -144,11 +144,17 @@ inline bool bin_constants(const double* e, const float* omega0, const float* g0s
         c.lam = (float)lam;
         const double kk = one_wg > 0.0 ? std::sqrt((1.0 - w0) / one_wg) : 0.0;
         const double q = (1.0 - kk) / (1.0 + kk);
-        c.q = (float)q;
-        c.q2 = (float)(q * q);
-        c.omq2 = (float)(1.0 - q * q);
+        const double omq = 2.0 * kk / (1.0 + kk), omq2 = omq * (1.0 + q);     // 1 - q, 1 - q^2
         // S = eps/(1 - w0 g0) dB (1 - Ts + Rs)/dtau and (1 - Ts + Rs)/dtau = lam phi h
-        c.cl = (float)(lam * eps / (prm.printed_gradient ? (1.0 + w0 * g0) : one_wg));
+        const double cl = lam * eps / (prm.printed_gradient ? (1.0 + w0 * g0) : one_wg);
+        c.q = (float)q;
+        c.cl = (float)cl;
+        if (kk > 0.0) {                     // (kk = 0: conservative scattering, the eq. 14 branch)
+            c.c2 = (float)(q * q / omq2);
+            c.qo = (float)(q / omq2);
+            c.hoh = (float)(0.5 / omq);
+            c.clh = (float)(cl / omq);
+        }
         c.gam = (float)(D * (1.0 - g0) / 2.0);
     }
     return any_scat;
