@@ -868,6 +868,16 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                 float Ts[M], Rs[M], Ss[M], X[M + 1];
                 float Ap = 1.0f;
                 const float* krow = kap + g * KST;
+                // initial upward deviation: previous evaluation shifted to the new Planck values, or
+                // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero); loaded first, so that
+                // the loads complete under the coefficients
+                const long long col = (long long)(l * G + g) * W;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const int p = sub * M + k;
+                    X[k] = (warm_valid && wbase) ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
+                }
+                X[M] = 0.0f;
                 if (bc.flags & BIN_RAYLEIGH) {                                      // uniform per bin
 #pragma unroll
                     for (int k = 0; k < M; ++k) {
@@ -924,15 +934,6 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
                     }
                     aup_fin = a;
                 }
-                // initial upward deviation: previous evaluation shifted to the new Planck values, or
-                // F_up = 0 (Sect. 2.2.3: the coupled stream starts from zero)
-                const long long col = (long long)(l * G + g) * W;
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const int p = sub * M + k;
-                    X[k] = (warm_valid && wbase) ? wbase[col + k * CL + sub] + dbs[p] : -bt[p];
-                }
-                X[M] = 0.0f;
                 const float toa_g = bc_toa[0];
                 const float bint = bc.bint;
                 __syncwarp();
