@@ -17,6 +17,10 @@ Default (the headline line):
 - single_atmosphere: the full-size single atmosphere (100 layers x 3000 bins x 20 g, scattering):
   per-step times with L2 flushed, back-to-back steady state, the sweep kernel, end to end, one full
   solve, the exact column solve and the post-processing spectrum.
+- plain_single_atmosphere: the plain single atmosphere (50 layers x 30 bins x 8 g, pure
+  absorption; latency-bound): microseconds per RE iteration back to back and inside one
+  graph-captured solve, and (in the cpu_baseline leg) the oracle on one host core and on all of
+  them: its full solve of this atmosphere and one full-size flux evaluation.
 - roofline: the sweep kernel of the batched step against the three floors of its work (HBM bytes,
   FP32 instructions, SFU operations); the FP32 and SFU counts per cell come from the op-counting
   build of the oracle on a bounded sample of the same workload (taken in the cpu_baseline leg).
@@ -566,6 +570,78 @@ def oracle_counts(wl, atm_ids, chunks=3, nb=8, T_of=None):
                       f"{chunks} chunks of {nb} bins ({cells} cells), 1 + {wl.n_scat} passes"}
 
 
+def run_plain(args, dev, ctx, steps=200):
+    """The plain single atmosphere (50 layers x 30 bins x 8 g, pure absorption, one pass per step):
+    latency-bound (240 columns, far below one wave), so microseconds per RE iteration -- back to
+    back through helios_re_step, and inside one graph-captured solve from the isothermal start --
+    not a roofline."""
+    import torch
+    import synth
+    import paper_1606_05474_b300 as hp
+    wl = synth.config1()
+    kap = [torch.from_numpy(t.kappa32).to(dev) for t in wl.tables]
+    plan = hp.Plan(ctx, wl.atms, wl.tables, kap, hp.default_params())
+    T = torch.from_numpy(np.asarray(wl.atms[0].T_init, np.float64)).to(dev)
+    T0 = T.clone()
+    state = plan.new_state()
+    stream = torch.cuda.current_stream(dev)
+    plan.re_step(T, state, warm=False)
+    for _ in range(max(3, args.warmup)):
+        plan.re_step(T, state, warm=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        plan.re_step(T, state, warm=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    step_us = a.elapsed_time(b) * 1e3 / steps
+    Ts = T0.clone()
+    plan.solve_re(Ts)                                   # first solve: graph capture
+    Ts = T0.clone()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    iters, status = plan.solve_re(Ts)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    return {"workload": "plain single atmosphere: 50 layers x 30 bins x 8 g, pure absorption, 1 pass per step, "
+                        "isothermal 1000 K start", "cells_per_step": wl.cells,
+            "us_per_step_back_to_back": round(step_us, 2),
+            "re_solve": {"wall_s": round(dt, 4), "iters": int(iters.item()), "status": int(status.item()),
+                         "us_per_iteration": round(dt * 1e6 / max(1, int(iters.item())), 2),
+                         "atm_per_s": round(1.0 / dt, 2), "tol": 1e-7}}
+
+
+def oracle_timings(gpu_iters_config2=None):
+    """The FP64 oracle on one host core and on all of them: a full RE solve of the plain single
+    atmosphere from its isothermal start, and one flux evaluation (1 + 4 passes) of the full-size
+    single atmosphere; a converged full-size atmosphere is estimated as that evaluation's time
+    times the GPU solve's iteration count (a full oracle solve takes tens of minutes)."""
+    import oracle
+    import synth
+    wl1 = synth.config1()
+    a1 = oracle.Atm.from_workload(wl1)
+    wl2 = synth.config2()
+    a2 = oracle.Atm.from_workload(wl2)
+    T2 = synth.perturbed_profile(wl2.atms[0], 11, amp=200.0)
+    all_cores = oracle.max_threads()
+    out = {"kind": "oracle", "cores_all": all_cores}
+    for tag, nt in (("1_core", 1), ("all_cores", all_cores)):
+        oracle.set_threads(nt)
+        st = oracle.State(a1, wl1.atms[0].T_init)
+        t0 = time.time()
+        rc, it, _ = oracle.solve_re(a1, st)
+        t1 = time.time()
+        oracle.flux_sweep(a2, T2, n_passes=5)
+        t2 = time.time()
+        out[tag] = {"plain_single_solve_s": round(t1 - t0, 3), "plain_single_iters": it, "plain_single_status": rc,
+                    "full_size_eval_s": round(t2 - t1, 3)}
+        if gpu_iters_config2:
+            out[tag]["full_size_converged_s_estimate"] = round((t2 - t1) * gpu_iters_config2, 1)
+    oracle.set_threads(all_cores)
+    return out
+
+
 def cpu_baseline(wl, a=0, seconds=12.0):
     """The FP64 oracle on the host cores: whole RE steps (flux evaluation + temperature step) of
     atmosphere a of the workload, as many as fit in `seconds`."""
@@ -604,6 +680,7 @@ def headline(args):
     ctx = bat["ctx"] if bat else hp.Context(local)
     lrn = run_learned(args, world, rank, local, dev, ctx) if want in ("headline", "learned") else None
     sgl = run_single(args, world, rank, local, dev, ctx) if want in ("headline", "single") else None
+    pln = run_plain(args, dev, ctx) if want in ("headline", "single") and rank == 0 else None
     if rank != 0:
         return
     P = peaks()
@@ -649,6 +726,10 @@ def headline(args):
                                                    measured_traffic("single", sgl["cells_per_step"]),
                                                    "sweep_kernel<13, 2, false, 16>", sm_max)
         line["single_atmosphere"] = sgl
+    if pln:
+        if not args.no_cpu_baseline and world == 1:
+            pln["oracle_host"] = oracle_timings(sgl["re_solve"]["iters"] if sgl else None)
+        line["plain_single_atmosphere"] = pln
     print(json.dumps(line), flush=True)
 
 

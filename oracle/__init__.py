@@ -112,6 +112,10 @@ def _load():
     lib.ref_solve_re.argtypes = [P(RefAtm), P(RefParams), vp, vp, vp, vp, vp, vp, vp]
     lib.ref_passes.restype = i
     lib.ref_passes.argtypes = [P(RefAtm), P(RefParams)]
+    lib.ref_set_threads.restype = None
+    lib.ref_set_threads.argtypes = [i]
+    lib.ref_max_threads.restype = i
+    lib.ref_max_threads.argtypes = []
     _lib = lib
     return lib
 
@@ -349,6 +353,15 @@ def temp_update(atm: Atm, st: State, Fup: np.ndarray, Fdn: np.ndarray, p: RefPar
                                  st.T.ctypes.data, st.mult.ctypes.data, st.hist.ctypes.data,
                                  st.nhist.ctypes.data, ctypes.byref(metric), dT.ctypes.data)
     return rc, metric.value, dT
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's OpenMP loops over bins (timing on 1 core and on all)."""
+    _load().ref_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().ref_max_threads())
 
 
 def solve_re(atm: Atm, st: State, p: RefParams = None):

@@ -21,6 +21,10 @@
  */
 #include "helios_ref.h"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -422,6 +426,24 @@ void ref_layer_exact(double F1up, double F2dn, double B1, double B2, double dtau
 /* Number of flux passes per temperature step (Sect. 2.2.3): one plus the
  * additional scattering passes when any bin scatters; one otherwise (with
  * omega0 = 0 the up and down streams decouple and one pass is exact). */
+void ref_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int ref_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 int ref_passes(const ref_atm* a, const ref_params* p)
 {
     if (a->rayleigh) return 1 + p->n_scat;

@@ -117,6 +117,9 @@ int    ref_temp_update(const ref_atm* a, const ref_params* p, const double* Fup_
 int    ref_solve_re(const ref_atm* a, const ref_params* p, double* T, double* mult, int* hist, int* nhist,
                     double* warm, int* iters, double* metric);
 int    ref_passes(const ref_atm* a, const ref_params* p);
+/* host threads of the OpenMP loops over bins (for timing the oracle on 1 core and on all) */
+void   ref_set_threads(int n);
+int    ref_max_threads(void);
 
 #ifdef __cplusplus
 }
