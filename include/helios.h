@@ -320,7 +320,8 @@ int helios_solve_re(helios_plan* plan, double* T_layer, int32_t* iters, int32_t*
  * n_in -> hidden_layers x n_hidden (SiLU) -> n_out (linear), FP32 master
  * parameters; every matrix product rounds both operands to BF16 and accumulates
  * in FP32 on the 5th-generation tensor cores (tcgen05 MMAs with the accumulator
- * in tensor memory, 128 x 128 tiles).  Parameter layout (device, float): for each layer
+ * in tensor memory, 128 x 64 output tiles; the weight operand reaches shared memory as
+ * pre-tiled BF16 by bulk asynchronous copies).  Parameter layout (device, float): for each layer
  * l, W_l [in][out] row-major then b_l [out].  Initial weights are uniform in
  * +-1/sqrt(fan_in) from `seed`.  Batches hold up to max_batch rows.
  *   helios_mlp_forward: y[B][n_out] = net(x[B][n_in]) (device arrays)
@@ -335,6 +336,12 @@ int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers
                       unsigned long long seed, int max_batch, helios_mlp** mlp);
 int helios_mlp_destroy(helios_mlp* mlp);
 int helios_mlp_params(helios_mlp* mlp, float** params, float** grads, long long* count);
+/* The matrix products read the weights from a BF16 copy laid out in the tensor cores' shared-memory
+ * tile order (both orientations, built from the FP32 parameters before the first product and kept
+ * current by every helios_mlp_adam).  A caller that writes the parameters through the pointer of
+ * helios_mlp_params declares it here, so that the copy is rebuilt before the next product (on the
+ * stream of that product).  No counterpart in the paper. */
+int helios_mlp_params_changed(helios_mlp* mlp);
 /* Synchronous: *flag = 1 if a matrix product of this network gave up waiting for its tensor-core
  * operations (a bounded wait that expired; its results are then invalid), else 0. */
 int helios_mlp_error(helios_mlp* mlp, int* flag);

@@ -409,8 +409,14 @@ class MLP:
         except Exception:
             pass
 
+    def params_changed(self):
+        """Declare that the parameters were written through `params` (helios_mlp_params_changed):
+        the BF16 weight tiles of the matrix products are rebuilt before the next product."""
+        check(self.lib.helios_mlp_params_changed(self.h))
+
     def layer_views(self):
-        """[(W_l [in, out], b_l [out])] views into the parameter buffer."""
+        """[(W_l [in, out], b_l [out])] views into the parameter buffer (after writing through them,
+        call params_changed)."""
         out, o = [], 0
         for a, b in zip(self.dims[:-1], self.dims[1:]):
             W = self.params[o:o + a * b].view(a, b); o += a * b

@@ -47,7 +47,7 @@ EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "heli
            "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
            "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_re_step_host", "helios_solve_re", "helios_measure_peaks", "helios_device_recip", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
-           "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_forward",
+           "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_params_changed", "helios_mlp_forward",
            "helios_mlp_grad", "helios_mlp_adam", "helios_mlp_train_step", "helios_mlp_initial_profiles", "helios_mlp_error",
            "helios_column_stats", "helios_standardize"]
 
@@ -88,6 +88,7 @@ def load(path: str = SO_PATH):
     lib.helios_mlp_create.argtypes = [vp, c_int, c_int, c_int, c_int, ctypes.c_ulonglong, c_int, P(vp)]
     lib.helios_mlp_destroy.argtypes = [vp]
     lib.helios_mlp_params.argtypes = [vp, P(vp), P(vp), P(ctypes.c_longlong)]
+    lib.helios_mlp_params_changed.argtypes = [vp]
     lib.helios_mlp_forward.argtypes = [vp, vp, vp, c_int, vp]
     lib.helios_mlp_grad.argtypes = [vp, vp, vp, c_int, vp, vp]
     lib.helios_mlp_adam.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, vp]

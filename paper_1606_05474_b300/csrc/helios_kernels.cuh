@@ -727,11 +727,17 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
             } else if (pt && emits) {
                 B = planck_ff(bc, P.invT[q], x);
                 if (warm_valid) {
-                    // B_old - B_new = B_new (e^y - 1) / (1 - e^{-x_old}), y = x_new - x_old
+                    // B_old - B_new = B_new (e^y - 1) / (1 - e^{-x_old}), y = x_new - x_old (x_old: the
+                    // high part of the old exponent, as planck_ff forms it); the old Planck value
+                    // itself only for a large change (rare once the iteration settles: a branch)
                     const float y = bc.xs * P.dinv_step[q];
-                    float xo;
-                    const float Bo = planck_ff(bc, P.invT_old[q], xo);
-                    sh = fabsf(y) < 1.0f ? B * __fdividef(em1(y), -em1(-xo)) : Bo - B;
+                    if (fabsf(y) < 1.0f) {
+                        const float xo = bc.xs * P.invT_old[q].x;
+                        sh = B * __fdividef(em1(y), -em1(-xo));
+                    } else {
+                        float xo;
+                        sh = planck_ff(bc, P.invT_old[q], xo) - B;
+                    }
                 }
             }
             const float Bb = __shfl_down_sync(FULL, B, 1);          // B of point p + 1

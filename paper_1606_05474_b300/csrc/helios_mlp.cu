@@ -4,8 +4,13 @@
 //
 // Layers: n_in -> hidden x n_hidden_layers (SiLU) -> n_out (linear).  Parameters are
 // FP32 master copies; every matrix product rounds both operands to BF16 and accumulates in
-// FP32 on the tensor cores (warp-level mma.sync m16n8k16).  Training minimises the mean
-// squared error with Adam.  All reductions have a fixed order (deterministic).
+// FP32 on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor memory).  The
+// weights are also kept as BF16, laid out tile by tile as the tensor cores read them from shared
+// memory, in both orientations (forward and backward products); those copies are made once from
+// the parameters, updated in place by every Adam step, and reach shared memory by one bulk
+// asynchronous copy per tile.
+// Training minimises the mean squared error with Adam.  All reductions have a fixed order
+// (deterministic).
 #include "helios.h"
 
 #include <cuda_bf16.h>
@@ -60,7 +65,11 @@ __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf
 // double-buffered: the next K step is staged while the MMAs of this one run, and a buffer is
 // overwritten only after the MMAs that read it have completed.  Staging issues all of a thread's
 // global loads (float4 along the contiguous dimension where the rows are 16-byte aligned) before
-// converting and storing any, so their latencies overlap.  The epilogue reads the accumulator back
+// converting and storing any, so their latencies overlap.  With BT the B operand is a weight
+// matrix already held as BF16 tiles in that layout (64 x 64, 8 KB each, [n tile][K step]): one
+// thread copies a K step's tile with one bulk asynchronous copy (cp.async.bulk, completion
+// counted in bytes on a per-buffer mbarrier) and waits for it before issuing the MMAs that read it.
+// The epilogue reads the accumulator back
 // with tcgen05.ld (warp w holds rows 32w .. 32w+31, a thread one row) and applies the bias / SiLU /
 // SiLU-derivative.  Every wait on the mbarrier is bounded: on expiry the kernel records an error
 // in *err, stops issuing, waits (bounded again) for what it issued, releases its tensor memory and
@@ -68,7 +77,8 @@ __device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + expf
 constexpr int UM_BM = 128, UM_BN = 64, UM_BK = 64;
 constexpr uint32_t UM_ABYTES = UM_BM * UM_BK * 2, UM_BBYTES = UM_BN * UM_BK * 2;
 constexpr uint32_t UM_STAGE = UM_ABYTES + UM_BBYTES;                 // one buffer: A then B
-constexpr uint32_t UM_BAR = 2 * UM_STAGE, UM_SLOT = UM_BAR + 8;
+constexpr uint32_t UM_BAR = 2 * UM_STAGE, UM_SLOT = UM_BAR + 8;   // MMA-commit mbarrier, TMEM address
+constexpr uint32_t UM_LDBAR = UM_BAR + 16;                          // two bulk-copy mbarriers (BT)
 constexpr size_t UM_SMEM = 72 * 1024;        // 48 KB of tiles, padded so that at most 3 CTAs share an SM
 constexpr uint32_t UM_COLS = 64;             // FP32 accumulator columns (a power of two >= 32)
 constexpr long UM_WAIT_LIMIT = 1L << 22;     // mbarrier polls before the kernel gives up
@@ -150,9 +160,22 @@ __device__ __forceinline__ void um_stage(unsigned char* dst, const float* __rest
     }
 }
 
-template <bool TA, bool TB, int EPI>
+// thread 0: the BF16 tile of K step st of the pre-tiled B operand into the B half of buffer `buf`
+__device__ __forceinline__ void um_bulk_b(uint32_t s0, uint32_t buf, const __nv_bfloat16* Bt, int steps, int st)
+{
+    const uint32_t ldbar = s0 + UM_LDBAR + 8u * (uint32_t)(st & 1);
+    const __nv_bfloat16* src = Bt + ((size_t)blockIdx.x * steps + st) * (UM_BN * UM_BK);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ldbar), "r"(UM_BBYTES) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s0 + buf + UM_ABYTES),
+                 "l"(src), "r"(UM_BBYTES), "r"(ldbar)
+                 : "memory");
+}
+
+template <bool TA, bool TB, int EPI, bool BT>
 __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const float* __restrict__ A, int lda,
-                                                   const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+                                                   const float* __restrict__ B, int ldb,
+                                                   const __nv_bfloat16* __restrict__ Bt, float* __restrict__ C, int ldc,
                                                    const float* __restrict__ bias, float* __restrict__ Zout,
                                                    const float* __restrict__ Zin, int ldz, float scale, int* __restrict__ err)
 {
@@ -169,24 +192,41 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    const int steps = (K + UM_BK - 1) / UM_BK;
+    int ld_issued = 0, ld_done = 0;          // thread 0: bulk copies issued / waited for (in order)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+        if (BT) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s0 + UM_LDBAR), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s0 + UM_LDBAR + 8), "r"(1) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (BT) {
+            um_bulk_b(s0, 0, Bt, steps, 0);
+            ld_issued = 1;
+        }
     }
     // the first K step's tiles into buffer 0
     um_stage<UM_BM, !TA>(sm, A, lda, m0, M, 0, K, tid, va);
-    um_stage<UM_BN, TB>(sm + UM_ABYTES, B, ldb, n0, N, 0, K, tid, vb);
+    if (!BT) um_stage<UM_BN, TB>(sm + UM_ABYTES, B, ldb, n0, N, 0, K, tid, vb);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");      // visible to the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + UM_SLOT);
-    const int steps = (K + UM_BK - 1) / UM_BK;
     bool ok = true;
     uint32_t gave_up = 0;                    // the parity of the commit a failed wait gave up on
     for (int st = 0; st < steps && ok; ++st) {
         const uint32_t buf = (uint32_t)(st & 1) * UM_STAGE;
-        if (tid == 0) {
+        bool lok = true;                     // thread 0: this step's B tile has arrived
+        if (tid == 0 && BT) {
+            lok = um_wait(s0 + UM_LDBAR + 8u * (uint32_t)(st & 1), (uint32_t)((st >> 1) & 1));
+            if (lok) ld_done = st + 1;
+        }
+        if (tid == 0 && !lok) {
+            // no MMAs: complete the commit barrier's phase by hand so that no thread waits for it
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+        } else if (tid == 0) {
 #pragma unroll
             for (int kk = 0; kk < UM_BK / 16; ++kk) {
                 const uint64_t da = um_desc(s0 + buf + kk * 2 * (16 * UM_BM), 16 * UM_BM, 128);
@@ -204,11 +244,15 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
         // the next K step into the other buffer while these MMAs run (its MMAs completed last step)
         if (st + 1 < steps) {
             const uint32_t nb = (uint32_t)((st + 1) & 1) * UM_STAGE;
+            if (BT && tid == 0 && lok) {
+                um_bulk_b(s0, nb, Bt, steps, st + 1);
+                ld_issued = st + 2;
+            }
             um_stage<UM_BM, !TA>(sm + nb, A, lda, m0, M, (st + 1) * UM_BK, K, tid, va);
-            um_stage<UM_BN, TB>(sm + nb + UM_ABYTES, B, ldb, n0, N, (st + 1) * UM_BK, K, tid, vb);
+            if (!BT) um_stage<UM_BN, TB>(sm + nb + UM_ABYTES, B, ldb, n0, N, (st + 1) * UM_BK, K, tid, vb);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
-        ok = __syncthreads_and(um_wait(bar, (uint32_t)(st & 1)) ? 1 : 0) != 0;     // one decision for the CTA
+        ok = __syncthreads_and((um_wait(bar, (uint32_t)(st & 1)) && lok) ? 1 : 0) != 0;   // one decision for the CTA
         if (!ok) gave_up = (uint32_t)(st & 1);
         if (!ok && tid == 0) atomicExch(err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -248,11 +292,31 @@ __global__ void __launch_bounds__(128, 1) mlp_umma(int M, int N, int K, const fl
     } else {
         // the commit the wait gave up on (bounded again): its MMAs may still read the tiles
         um_wait(bar, gave_up);
+        // and the bulk copies still in flight into the tiles (bounded again)
+        if (BT && tid == 0)
+            for (int j = ld_done; j < ld_issued; ++j) um_wait(s0 + UM_LDBAR + 8u * (uint32_t)(j & 1), (uint32_t)((j >> 1) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UM_COLS) : "memory");
+}
+
+// BF16 tiles of a weight matrix as the B operand op(B)[k][n] = trans ? W[n ld + k] : W[k ld + n]
+// (K x N): tile (n tile t, K step j) at dst + (t ks + j) 4096, element (r, c) of a tile at the
+// K-major core offset of (r, c); zero outside K x N.  One thread per tile element.
+__global__ void retile_kernel(const float* __restrict__ W, int ld, int K, int N, int trans, int ks,
+                              __nv_bfloat16* __restrict__ dst, long long total)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const long long tile = e / (UM_BN * UM_BK);
+    const int w = (int)(e - tile * (UM_BN * UM_BK));
+    const int r = w / UM_BK, c = w % UM_BK;                      // row (n) and column (k) in the tile
+    const int n = (int)(tile / ks) * UM_BN + r, k = (int)(tile % ks) * UM_BK + c;
+    const float v = (n < N && k < K) ? W[trans ? (size_t)n * ld + k : (size_t)k * ld + n] : 0.0f;
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(dst + tile * (UM_BN * UM_BK)) +
+                                      um_core_off<UM_BN>(r, c)) = __float2bfloat16_rn(v);
 }
 
 // dOut = 2 (Y - T) / (B * N); per-block partial sums of the squared error (fixed order)
@@ -294,9 +358,19 @@ __global__ void colsum_kernel(const float* __restrict__ dZ, int M, int N, float*
     db[n] = s;
 }
 
+// where the weights of each layer sit in the parameters and in the BF16 tiles
+struct TileMap {
+    int nl;
+    int in[kMaxLayers], out[kMaxLayers];
+    long long woff[kMaxLayers], wtf[kMaxLayers], wtb[kMaxLayers];
+};
+
+// one Adam step; a weight's new value also goes, as BF16, into its places in the forward tiles
+// (row n, column k of op(B) = W) and, beyond the first layer, the backward tiles (row k, column n
+// of op(B) = W^T), so the tiles stay current without a separate pass
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
-                            float c2)
+                            float c2, TileMap tm, __nv_bfloat16* __restrict__ wt)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -304,7 +378,23 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
         const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        const float pn = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pn;
+        int l = tm.nl - 1;
+        while (l > 0 && i < tm.woff[l]) --l;
+        const long long e = i - tm.woff[l];
+        const int in = tm.in[l], out = tm.out[l];
+        if (e >= (long long)in * out) continue;                  // a bias
+        const int k = (int)(e / out), c = (int)(e - (long long)k * out);
+        const __nv_bfloat16 h = __float2bfloat16_rn(pn);
+        const int ksf = (in + UM_BK - 1) / UM_BK;
+        unsigned char* f = reinterpret_cast<unsigned char*>(wt + tm.wtf[l] + ((long long)(c / UM_BN) * ksf + k / UM_BK) * (UM_BN * UM_BK));
+        *reinterpret_cast<__nv_bfloat16*>(f + um_core_off<UM_BN>(c % UM_BN, k % UM_BK)) = h;
+        if (l > 0) {
+            const int ksb = (out + UM_BK - 1) / UM_BK;
+            unsigned char* b = reinterpret_cast<unsigned char*>(wt + tm.wtb[l] + ((long long)(k / UM_BN) * ksb + c / UM_BK) * (UM_BN * UM_BK));
+            *reinterpret_cast<__nv_bfloat16*>(b + um_core_off<UM_BN>(k % UM_BN, c % UM_BK)) = h;
+        }
     }
 }
 
@@ -403,6 +493,9 @@ struct helios_mlp {
     int64_t woff[kMaxLayers], boff[kMaxLayers], n_params;
     int max_B;
     float *p, *g, *m, *v;
+    __nv_bfloat16* wt;       // BF16 weight tiles: forward orientation, then backward (layers >= 1)
+    int64_t wtf[kMaxLayers], wtb[kMaxLayers];   // element offsets of each layer's tiles
+    bool wt_stale;           // the FP32 parameters changed since the tiles were made
     float* act;              // per layer: Z (hidden layers) and Y, max_B rows
     float *dA, *dB;          // backprop ping-pong buffers
     float* dout;
@@ -450,6 +543,18 @@ int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers
             h[i] = (float)((2.0 * u - 1.0) * bound);
         }
     }
+    // BF16 weight tiles: forward (op(B) = W_l, K = in, N = out) and, for layers >= 1, backward
+    // (op(B) = W_l^T, K = out, N = in)
+    int64_t wt_elems = 0;
+    auto ntiles = [](int K, int N) { return (int64_t)((N + UM_BN - 1) / UM_BN) * ((K + UM_BK - 1) / UM_BK); };
+    for (int l = 0; l < m->nl; ++l) {
+        m->wtf[l] = wt_elems;
+        wt_elems += ntiles(m->dims[l], m->dims[l + 1]) * UM_BN * UM_BK;
+    }
+    for (int l = 0; l < m->nl; ++l) {
+        m->wtb[l] = wt_elems;
+        if (l > 0) wt_elems += ntiles(m->dims[l + 1], m->dims[l]) * UM_BN * UM_BK;
+    }
     size_t act_floats = 0;
     for (int l = 0; l < m->nl; ++l) act_floats += (size_t)2 * max_batch * m->dims[l + 1];
     int widest = 0;
@@ -459,6 +564,9 @@ int helios_mlp_create(helios_ctx* ctx, int n_in, int n_hidden, int hidden_layers
         if (cudaMalloc((void**)b, sizeof(float) * off) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp params"); }
         m->allocs.push_back(*b);
     }
+    if (cudaMalloc((void**)&m->wt, sizeof(__nv_bfloat16) * wt_elems) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp weight tiles"); }
+    m->allocs.push_back(m->wt);
+    m->wt_stale = true;
     if (cudaMalloc((void**)&m->act, sizeof(float) * act_floats) != cudaSuccess) { helios_mlp_destroy(m); return mfail(HELIOS_ENOMEM, "mlp activations"); }
     m->allocs.push_back(m->act);
     const size_t wide = (size_t)max_batch * widest;
@@ -513,6 +621,13 @@ int helios_mlp_params(helios_mlp* m, float** params, float** grads, long long* c
     return HELIOS_OK;
 }
 
+int helios_mlp_params_changed(helios_mlp* m)
+{
+    if (!m) return mfail(HELIOS_EINVAL, "helios_mlp_params_changed: null argument");
+    m->wt_stale = true;
+    return HELIOS_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -520,36 +635,62 @@ namespace {
 float* Zbuf(helios_mlp* m, int l) { size_t o = 0; for (int k = 0; k < l; ++k) o += (size_t)2 * m->max_B * m->dims[k + 1]; return m->act + o; }
 float* Ybuf(helios_mlp* m, int l) { return Zbuf(m, l) + (size_t)m->max_B * m->dims[l + 1]; }
 
-template <bool TA, bool TB, int EPI>
+// Bt: the B operand as BF16 tiles (B then unused); null: B staged from FP32
+template <bool TA, bool TB, int EPI, bool BT = false>
 int gemm(helios_mlp* m, int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-         const float* bias, float* Zout, const float* Zin, int ldz, float scale, cudaStream_t s)
+         const float* bias, float* Zout, const float* Zin, int ldz, float scale, cudaStream_t s,
+         const __nv_bfloat16* Bt = nullptr)
 {
     static thread_local int configured[64] = {};          // per device: the dynamic shared-memory limit set
     if (m->device < 0 || m->device >= 64) return mfail(HELIOS_EINVAL, "device %d", m->device);
     if (!configured[m->device]) {
-        MLP_CUDA(cudaFuncSetAttribute(mlp_umma<TA, TB, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UM_SMEM));
+        MLP_CUDA(cudaFuncSetAttribute(mlp_umma<TA, TB, EPI, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)UM_SMEM));
         configured[m->device] = 1;
     }
     dim3 grid((N + UM_BN - 1) / UM_BN, (M + UM_BM - 1) / UM_BM);
-    mlp_umma<TA, TB, EPI><<<grid, 128, UM_SMEM, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, Zout, Zin, ldz, scale,
-                                                      m->err);
+    mlp_umma<TA, TB, EPI, BT><<<grid, 128, UM_SMEM, s>>>(M, N, K, A, lda, B, ldb, Bt, C, ldc, bias, Zout, Zin, ldz,
+                                                          scale, m->err);
     MLP_CUDA(cudaGetLastError());
+    return HELIOS_OK;
+}
+
+// the BF16 weight tiles of every layer from the FP32 parameters, once after they changed
+int refresh_tiles(helios_mlp* m, cudaStream_t s)
+{
+    if (!m->wt_stale) return HELIOS_OK;
+    for (int l = 0; l < m->nl; ++l) {
+        const int in = m->dims[l], out = m->dims[l + 1];
+        for (int dir = 0; dir < 2; ++dir) {
+            if (dir == 1 && l == 0) continue;                  // no input gradient of the first layer
+            const int K = dir ? out : in, N = dir ? in : out;
+            const int ks = (K + UM_BK - 1) / UM_BK;
+            const long long total = (long long)((N + UM_BN - 1) / UM_BN) * ks * UM_BN * UM_BK;
+            retile_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(m->p + m->woff[l], out, K, N, dir, ks,
+                                                                         m->wt + (dir ? m->wtb[l] : m->wtf[l]), total);
+            MLP_CUDA(cudaGetLastError());
+        }
+    }
+    m->wt_stale = false;
     return HELIOS_OK;
 }
 
 // forward pass; hidden activations kept for the backward pass; output to `y`
 int forward(helios_mlp* m, const float* x, float* y, int B, cudaStream_t s)
 {
+    int rc = refresh_tiles(m, s);
+    if (rc) return rc;
     const float* in = x;
     for (int l = 0; l < m->nl; ++l) {
         const int K = m->dims[l], N = m->dims[l + 1];
-        const float* W = m->p + m->woff[l];
         const float* b = m->p + m->boff[l];
-        int rc;
+        const __nv_bfloat16* Wt = m->wt + m->wtf[l];
         if (l + 1 < m->nl)
-            rc = gemm<false, false, EPI_BIAS_SILU>(m, B, N, K, in, K, W, N, Ybuf(m, l), N, b, Zbuf(m, l), nullptr, N, 1.0f, s);
+            rc = gemm<false, false, EPI_BIAS_SILU, true>(m, B, N, K, in, K, nullptr, N, Ybuf(m, l), N, b, Zbuf(m, l),
+                                                         nullptr, N, 1.0f, s, Wt);
         else
-            rc = gemm<false, false, EPI_BIAS>(m, B, N, K, in, K, W, N, y, N, b, nullptr, nullptr, N, 1.0f, s);
+            rc = gemm<false, false, EPI_BIAS, true>(m, B, N, K, in, K, nullptr, N, y, N, b, nullptr, nullptr, N, 1.0f,
+                                                    s, Wt);
         if (rc) return rc;
         in = Ybuf(m, l);
     }
@@ -583,8 +724,8 @@ int backward(helios_mlp* m, const float* x, const float* target, int B, float* l
         MLP_CUDA(cudaGetLastError());
         if (l > 0) {
             // dZ_{l-1} = (dZ_l W_l^T) * SiLU'(Z_{l-1})
-            rc = gemm<false, true, EPI_DSILU>(m, B, K, N, dcur, N, m->p + m->woff[l], N, dnext, K, nullptr, nullptr,
-                                              Zbuf(m, l - 1), K, 1.0f, s);
+            rc = gemm<false, true, EPI_DSILU, true>(m, B, K, N, dcur, N, nullptr, N, dnext, K, nullptr, nullptr,
+                                                    Zbuf(m, l - 1), K, 1.0f, s, m->wt + m->wtb[l]);
             if (rc) return rc;
             std::swap(dcur, dnext);
         }
@@ -619,7 +760,20 @@ int helios_mlp_adam(helios_mlp* m, float lr, float beta1, float beta2, float eps
     m->t += 1;
     const float c1 = (float)(1.0 - std::pow((double)beta1, (double)m->t));
     const float c2 = (float)(1.0 - std::pow((double)beta2, (double)m->t));
-    adam_kernel<<<256, 256, 0, s>>>(m->p, m->g, m->m, m->v, m->n_params, lr, beta1, beta2, eps, c1, c2);
+    // tiles made first if the parameters changed since (their zero padding is written only there)
+    int rc = refresh_tiles(m, s);
+    if (rc) return rc;
+    TileMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    tm.nl = m->nl;
+    for (int l = 0; l < m->nl; ++l) {
+        tm.in[l] = m->dims[l];
+        tm.out[l] = m->dims[l + 1];
+        tm.woff[l] = m->woff[l];
+        tm.wtf[l] = m->wtf[l];
+        tm.wtb[l] = m->wtb[l];
+    }
+    adam_kernel<<<256, 256, 0, s>>>(m->p, m->g, m->m, m->v, m->n_params, lr, beta1, beta2, eps, c1, c2, tm, m->wt);
     MLP_CUDA(cudaGetLastError());
     return HELIOS_OK;
 }

@@ -90,6 +90,32 @@ def test_adam_step_matches_oracle():
     assert np.max(np.abs(p1 - po)) < 1e-6
 
 
+def test_new_parameters_reach_the_products():
+    # the products read a BF16 tiled copy of the weights: after an Adam step, and after the caller
+    # writes the parameters and declares it (params_changed), the forward pass uses the new values
+    import torch
+    B = 150
+    net = _net(B, seed=11)
+    x, t = _data(B, 4)
+    xf = x.astype(np.float32)
+    xg = torch.from_numpy(xf).cuda()
+    net.forward(xg)                                    # tiles made from the initial parameters
+    net.grad(xg, torch.from_numpy(t.astype(np.float32)).cuda())
+    net.adam(lr=1e-2)
+    for step in ("adam", "written"):
+        if step == "written":
+            rng = np.random.default_rng(12)
+            new = (rng.uniform(-1, 1, size=net.params.numel()) * 0.06).astype(np.float32)
+            net.params.copy_(torch.from_numpy(new).cuda())
+            net.params_changed()
+        y = net.forward(xg).double().cpu().numpy()
+        p = net.params.double().cpu().numpy()
+        yo, _, _ = omlp.forward(p, DIMS, xf.astype(np.float64), bf16_ops=True)
+        sy, _ = omlp.magnitude_sums(p, DIMS, xf.astype(np.float64), np.zeros((B, DIMS[-1])))
+        _check_scaled(y, yo, sy, f"forward after {step}")
+    assert net.error() == 0
+
+
 def test_learned_initializer_saves_iterations_and_reaches_the_same_equilibrium():
     import synth
     from helpers import ctx, make_plan, pack
