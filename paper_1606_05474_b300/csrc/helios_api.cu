@@ -775,6 +775,12 @@ int launch_sweep_MB(helios_plan* p, const MGroup& gr, const int* status, int n_p
     if (conf != p->ctx->device + 1) {
         CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB, DIRECT, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       200 * 1024));
+        // shared memory for the MINB blocks the registers allow (at G = 20), the rest of the SM's
+        // 256 KB stays L1 for the table gathers (batched workload +1%)
+        const size_t need = (size_t)MINB * (sweep_smem_bytes(M, 20, CL) + 1024);
+        const int pct = (int)std::min<size_t>(100, (100 * need + 228 * 1024 - 1) / (228 * 1024));
+        CUDA_TRY(cudaFuncSetAttribute(sweep_kernel<M, MINB, DIRECT, CL>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      pct));
         conf = p->ctx->device + 1;
     }
     const bool pdl = use_pdl(p, s);
