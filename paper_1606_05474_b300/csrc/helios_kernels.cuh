@@ -679,10 +679,12 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         // warm start, its columns' upward deviations (one contiguous block of G W floats)
         if (l + 1 < l_end) {
             if (tid == 0) prefetch_l2(P.bins + ad.bin_off + l + 1);
-            if (ad.n_spec <= 1) {
+            // (every species table of a mixed opacity, eq. 34)
+            for (int sp = 0; sp < max(1, ad.n_spec); ++sp) {
+                const float* ts = ad.n_spec > 1 ? P.tabs[P.spec_tab[ad.spec_off + sp]].kappa : tab;
                 const int lg1 = (l + 1) * G;
                 for (int p = tid; p < NP; p += nthreads) {
-                    const float* r = tab + P.row[ad.pt_off + p] + lg1;
+                    const float* r = ts + P.row[ad.pt_off + p] + lg1;
                     const float* c[4] = {r, r + td.offP, r + td.offT, r + td.offP + td.offT};
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -760,16 +762,40 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         // ... and the opacity gather, consecutive threads on consecutive g
         if (ad.n_spec > 1) {
             // eq. (34): kappa = sum_j X_j kappa_j over species tables sharing the (T, P) grid, so
-            // the corner offsets and weights of a point serve every species
-            const int lg = l * G + g_of;
-            for (int p = p_first; p < NP; p += p_stride) {
-                const int q = ad.pt_off + p;
-                const int row = P.row[q];
-                const float4 w = P.wq[q];
-                float k = 0.0f;
-                for (int j = 0; j < ad.n_spec; ++j)
-                    k = fmaf(P.spec_w[ad.spec_off + j], kappa_at(P.tabs[P.spec_tab[ad.spec_off + j]].kappa, td, row, w, lg), k);
-                kap[g_of * KST + p] = k;
+            // the corner offsets and weights of a point serve every species.  The species in turn
+            // (table and weight read once per bin), each thread adding species j to its own
+            // entries, in the order j = 0, 1, ... (kappa = fma(X_j, kappa_j, kappa) from 0)
+            for (int j = 0; j < ad.n_spec; ++j) {
+                const float* tj = P.tabs[P.spec_tab[ad.spec_off + j]].kappa;
+                const float xj = P.spec_w[ad.spec_off + j];
+                if (vec4) {
+                    const int lg = l * G + 4 * g4_of;
+                    for (int p = p4_first; p < NP; p += p4_stride) {
+                        const int q = ad.pt_off + p;
+                        const float4 w = P.wq[q];
+                        const float* r = tj + P.row[q] + lg;
+                        const float4 k00 = __ldg(reinterpret_cast<const float4*>(r));
+                        const float4 k10 = __ldg(reinterpret_cast<const float4*>(r + td.offP));
+                        const float4 k01 = __ldg(reinterpret_cast<const float4*>(r + td.offT));
+                        const float4 k11 = __ldg(reinterpret_cast<const float4*>(r + td.offP + td.offT));
+                        float* dst = kap + (4 * g4_of) * KST + p;
+                        const float b0 = fmaf(w.w, k11.x, fmaf(w.z, k01.x, fmaf(w.y, k10.x, w.x * k00.x)));
+                        const float b1 = fmaf(w.w, k11.y, fmaf(w.z, k01.y, fmaf(w.y, k10.y, w.x * k00.y)));
+                        const float b2 = fmaf(w.w, k11.z, fmaf(w.z, k01.z, fmaf(w.y, k10.z, w.x * k00.z)));
+                        const float b3 = fmaf(w.w, k11.w, fmaf(w.z, k01.w, fmaf(w.y, k10.w, w.x * k00.w)));
+                        dst[0] = fmaf(xj, b0, j ? dst[0] : 0.0f);
+                        dst[KST] = fmaf(xj, b1, j ? dst[KST] : 0.0f);
+                        dst[2 * KST] = fmaf(xj, b2, j ? dst[2 * KST] : 0.0f);
+                        dst[3 * KST] = fmaf(xj, b3, j ? dst[3 * KST] : 0.0f);
+                    }
+                } else {
+                    const int lg = l * G + g_of;
+                    for (int p = p_first; p < NP; p += p_stride) {
+                        const int q = ad.pt_off + p;
+                        float* dst = kap + g_of * KST + p;
+                        *dst = fmaf(xj, kappa_at(tj, td, P.row[q], P.wq[q], lg), j ? *dst : 0.0f);
+                    }
+                }
             }
         } else if (vec4) {
             const int lg = l * G + 4 * g4_of;
