@@ -432,7 +432,13 @@ int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_kt
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
         const int cm = ad[amax].cl, mm = ad[amax].M;
         const int per_sm = std::max(1, sweep_occupancy(mm, threads, sweep_smem(mm, G, cm), false, cm));
-        TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + (int64_t)nsm * per_sm - 1) / ((int64_t)nsm * per_sm)));
+        const int64_t slots = (int64_t)nsm * per_sm;
+        TB = (int)std::max<int64_t>(1, std::min<int64_t>(32, (bins + slots - 1) / slots));
+        // a batch of at least four waves of 8-bin items takes items of 8 bins: once most
+        // atmospheres of a radiative-equilibrium solve have converged, an iteration of the rest
+        // lasts as long as one item's bins one after the other (measured on 512 atmospheres of 300
+        // bins: 20% less solve time than 32-bin items, 2% more time per step with all active)
+        if (bins >= 4 * slots * 8) TB = std::min(TB, 8);
     }
     P->TB = TB;
     std::vector<int2> items;
