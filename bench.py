@@ -660,7 +660,7 @@ def cpu_baseline(wl, a=0, seconds=12.0):
         if time.time() - t0 > seconds:
             break
     dt = time.time() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.max_threads()                    # the OpenMP threads the oracle's loops used
     return {"value": round(cells * steps / dt / 1e9, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{steps} full RE steps of atmosphere {a} of the workload ({atm.n} layers x {atm.L} bins x "
                       f"{atm.G} g = {cells} cells each), {dt:.1f} s"}
@@ -885,7 +885,7 @@ def run_reference(args):
         cells += one(args.warmup + i)
     dt = time.time() - t0
     v = cells / dt / 1e9
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.max_threads()                    # the OpenMP threads the oracle's loops used
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -163,6 +163,24 @@ def test_species_mixing_matches_mixed_table():
         assert rel_err(Fus[i], r["Fup"]) < FLUX_TOL and rel_err(Fds[i], r["Fdn"]) < FLUX_TOL
 
 
+@pytest.mark.parametrize("G", [6, 20])
+def test_species_mixing_three_tables(G):
+    # eq. (34) with three species on the per-thread gather (G not a multiple of 4) and on the
+    # four-Gauss-point one, several lane tiles and a ragged tail; the emergent spectrum too
+    import dataclasses
+    L, n = 11, 45
+    tabs = [synth.make_ktable(synth.SEED_BASE + 31, j, L, G, -6.0, 3.0) for j in range(3)]
+    a0 = synth.small_scattering(L=L, n=n, G=G).atms[0]
+    wl = synth.Workload(name=f"mix3-{G}", atms=[dataclasses.replace(a0, species=[(0, 0.5), (1, 0.3), (2, 0.2)])],
+                        tables=tabs, n_scat=4)
+    T = synth.perturbed_profile(wl.atms[0], 41)
+    plan = make_plan(wl)
+    Fu, Fd, toa = plan.flux_sweep(pack([T]), n_passes=5)
+    r = _oracle_sweep(wl, 0, T, n_passes=5)
+    _check_fluxes(Fu, Fd, r)
+    _check_toa(toa, r, oracle.Atm.from_workload(wl, 0))
+
+
 @pytest.mark.parametrize("n,L,passes", [(40, 12, 1), (40, 12, 81), (101, 9, 81), (239, 3, 5)])
 def test_isothermal_layer_grid_emission_spectrum(n, L, passes):
     # the grid of the post-processing spectra (isothermal layers, Sect. 2.2.1 and Sect. 3),
