@@ -281,6 +281,29 @@ def test_rayleigh_scattering_only_conserves_net_flux():
     assert np.max(np.abs(net - net[0])) < 1e-5 * np.max(r["Fup"])
 
 
+@pytest.mark.parametrize("n,L,G", [(40, 12, 7), (150, 5, 3), (200, 3, 9)])
+def test_thirty_two_lane_columns_odd_gauss_points(n, L, G):
+    # a warp per Gauss point taking the points in two rounds: an odd G leaves the last warp idle
+    # in the second round; cold then warm-started passes, and the exact column solve
+    wl = synth.small_scattering(L=L, n=n, G=G)
+    atm = oracle.Atm.from_workload(wl)
+    T1 = synth.perturbed_profile(wl.atms[0], 14)
+    T2 = T1 + 4.0 * np.sin(np.arange(n))
+    plan = make_plan(wl, col_lanes=32)
+    Fu, Fd, toa = plan.flux_sweep(pack([T1]), n_passes=5)
+    warm = np.zeros(atm.L * atm.G * (2 * n + 1))
+    r1 = oracle.flux_sweep(atm, T1, n_passes=5, warm=warm, warm_valid=False)
+    _check_fluxes(Fu, Fd, r1)
+    _check_toa(toa, r1, atm)
+    Fu2, Fd2, toa2 = plan.flux_sweep(pack([T2]), n_passes=5, warm=True)
+    r2 = oracle.flux_sweep(atm, T2, n_passes=5, warm=warm, warm_valid=True)
+    _check_fluxes(Fu2, Fd2, r2)
+    _check_toa(toa2, r2, atm)
+    Fu3, Fd3, toa3 = plan.flux_sweep(pack([T1]), n_passes=hp.DIRECT)
+    r3 = oracle.flux_direct(atm, T1)
+    _check_fluxes(Fu3, Fd3, r3)
+
+
 @pytest.mark.parametrize("n,L,G", [(36, 9, 20), (40, 12, 7), (111, 7, 20), (119, 4, 3)])
 def test_sixteen_lane_columns_match_oracle(n, L, G):
     # two Gauss points per warp (16 lanes per column; odd G leaves half a warp idle), cold
