@@ -704,7 +704,9 @@ __device__ __forceinline__ void sweep_item(const PlanDev& P, int item, const int
         // takes 31 consecutive points plus, in lane 31, the first point of the next group, so a
         // lane reads the Planck value of the point above from its neighbour (no barrier and no
         // second evaluation; lane 31's value serves only that read) ...
-        for (int p0 = (tid >> 5) * 31; p0 < W; p0 += (nthreads >> 5) * 31) {
+        // (the last warps take them: the block's first threads hold one opacity-gather task more)
+        const int pw_need = (W + 30) / 31, pw_off = max(0, (nthreads >> 5) - pw_need);
+        for (int p0 = ((tid >> 5) - pw_off) * 31; (tid >> 5) >= pw_off && p0 < W; p0 += ((nthreads >> 5) - pw_off) * 31) {
             const int p = p0 + lane;
             const bool pt = p < NP;
             const int q = ad.pt_off + p;
