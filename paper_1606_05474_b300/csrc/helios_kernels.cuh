@@ -613,12 +613,13 @@ __host__ __device__ constexpr int sweep_block_threads(int G, bool direct)
 }
 
 // resident blocks per SM that a sweep kernel is compiled for (its register budget): 32-lane
-// columns, iterated passes -- three 320-thread blocks (64 registers) up to lane chunk 7, two (96)
-// beyond; the exact solve -- two 640-thread blocks (48 registers) up to chunk 7, one beyond
+// columns, iterated passes -- three 320-thread blocks (64 registers) up to lane chunk 9 (chunk 9
+// spills some registers and still runs faster than two blocks at 96), two (96) beyond; the exact
+// solve -- two 640-thread blocks (48 registers) up to chunk 7, one beyond
 template <int M, bool DIRECT>
 constexpr int sweep_minb()
 {
-    return DIRECT ? (M <= 7 ? 2 : 1) : (M <= 7 ? 3 : 2);
+    return DIRECT ? (M <= 7 ? 2 : 1) : (M <= 9 ? 3 : 2);
 }
 
 // ---------------------------------------------------------------------------
