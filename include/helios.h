@@ -204,6 +204,23 @@ typedef struct {
 } helios_plan_info_t;
 int helios_plan_info(const helios_plan* plan, helios_plan_info_t* info);
 
+/* Checkpoint and resume of an iteration (no counterpart in the paper).  Between steps a plan
+ * keeps two things of its own: the upward fluxes of its last evaluation (the next warm start)
+ * and that evaluation's point temperatures (from which the warm start is shifted to the new
+ * temperatures).  With the caller's arrays (T_layer, mult, hist, nhist, status, iters) they are
+ * the whole state of a radiative-equilibrium iteration: imported into this plan or into another
+ * plan made from the same batch, tables and parameters, later steps continue the iteration bit
+ * for bit.
+ *   helios_plan_state_bytes: the size of a checkpoint
+ *   helios_plan_state_export: copies this plan's state into buf (host or device memory,
+ *     state_bytes long), queued on `stream`; EINVAL before the plan's first evaluation
+ *   helios_plan_state_import: waits for `stream`, checks that buf holds a checkpoint of a plan
+ *     of this shape (EINVAL otherwise), and queues the copies into the plan on `stream`; the next
+ *     step with warm = 1 starts from it */
+int helios_plan_state_bytes(const helios_plan* plan, int64_t* bytes);
+int helios_plan_state_export(helios_plan* plan, void* buf, cudaStream_t stream);
+int helios_plan_state_import(helios_plan* plan, const void* buf, cudaStream_t stream);
+
 /* Measurement support (no counterpart in the paper).  helios_plan_set_timing
  * keeps a ring of `slots` CUDA event pairs (0 turns timing off; at most
  * 65536); while on, every helios_flux_sweep records a pair around its sweep

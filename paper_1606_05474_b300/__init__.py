@@ -363,6 +363,26 @@ class Plan:
         return v.value
 
     # ---- packing helpers
+    def export_state(self, out=None, stream=None):
+        """Checkpoint of the plan's own iteration state (helios_plan_state_export): a uint8 tensor
+        (device by default, or `out`, host or device) that import_state restores."""
+        torch = _torch()
+        n = ctypes.c_int64()
+        check(self.lib.helios_plan_state_bytes(self.h, ctypes.byref(n)))
+        buf = out if out is not None else torch.empty(n.value, dtype=torch.uint8, device=self.dev)
+        if buf.dtype != torch.uint8 or buf.numel() != n.value or not buf.is_contiguous():
+            raise ValueError(f"the checkpoint buffer must be a contiguous uint8 tensor of {n.value} bytes")
+        check(self.lib.helios_plan_state_export(self.h, buf.data_ptr(), _stream_ptr(stream)))
+        return buf
+
+    def import_state(self, buf, stream=None):
+        """Restore a checkpoint made by export_state of a plan of the same shape
+        (helios_plan_state_import); the next re_step with warm=True continues from it."""
+        torch = _torch()
+        if buf.dtype != torch.uint8 or not buf.is_contiguous():
+            raise ValueError("the checkpoint must be a contiguous uint8 tensor")
+        check(self.lib.helios_plan_state_import(self.h, buf.data_ptr(), _stream_ptr(stream)))
+
     def split_layers(self, x):
         return [x[self.lay_off[a]:self.lay_off[a + 1]] for a in range(self.A)]
 

@@ -44,7 +44,8 @@ class PlanInfo(ctypes.Structure):
 
 
 EXPORTS = ["helios_default_params", "helios_version", "helios_last_error", "helios_create", "helios_destroy",
-           "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_interp_opacity",
+           "helios_plan_create", "helios_plan_destroy", "helios_plan_info", "helios_plan_state_bytes",
+           "helios_plan_state_export", "helios_plan_state_import", "helios_interp_opacity",
            "helios_flux_sweep", "helios_temp_update", "helios_re_step", "helios_re_step_host", "helios_solve_re", "helios_measure_peaks", "helios_device_recip", "helios_plan_set_timing",
            "helios_plan_last_sweep_ms", "helios_plan_sweep_times", "helios_flux_sweep_noalloc",
            "helios_autotune", "helios_mlp_create", "helios_mlp_destroy", "helios_mlp_params", "helios_mlp_params_changed", "helios_mlp_forward",
@@ -73,6 +74,9 @@ def load(path: str = SO_PATH):
     lib.helios_plan_create.argtypes = [vp, P(Batch), P(KTable), c_int, P(Params), P(vp)]
     lib.helios_plan_destroy.argtypes = [vp]
     lib.helios_plan_info.argtypes = [vp, P(PlanInfo)]
+    lib.helios_plan_state_bytes.argtypes = [vp, P(c_int64)]
+    lib.helios_plan_state_export.argtypes = [vp, vp, vp]
+    lib.helios_plan_state_import.argtypes = [vp, vp, vp]
     lib.helios_interp_opacity.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.helios_flux_sweep.argtypes = [vp, vp, c_int, c_int, vp, vp, vp, vp, vp, vp]
     lib.helios_temp_update.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]

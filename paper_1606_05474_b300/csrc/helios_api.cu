@@ -193,6 +193,7 @@ struct helios_plan {
     uint8_t *hist, *nhist;
     int* n_active;
     bool warm_ready;
+    int64_t state_hdr[4];   // header of an exported checkpoint (host memory of a pending copy)
     cudaGraphExec_t graph;
     const void* graph_key[3];
     int graph_chunk;
@@ -698,6 +699,59 @@ int helios_plan_last_sweep_ms(helios_plan* p, float* ms)
     int rc = helios_plan_sweep_times(p, ms, 1, &n);
     if (rc) return rc;
     if (n == 0) return fail(HELIOS_EINVAL, "no timed evaluation yet");
+    return HELIOS_OK;
+}
+
+// ---- checkpoint of the iteration state a plan keeps between steps: a header (magic, points,
+// warm-start floats, layers), the point temperatures of the last evaluation (the old
+// temperatures of the next warm-start shift) and the warm-start upward fluxes
+constexpr int64_t kStateMagic = 0x4b43534f494c4548LL;     // "HELIOSCK"
+
+static int64_t state_bytes(const helios_plan* p)
+{
+    return (int64_t)sizeof(p->state_hdr) + (int64_t)sizeof(double) * p->points +
+           (int64_t)sizeof(float) * p->warm_floats;
+}
+
+int helios_plan_state_bytes(const helios_plan* p, int64_t* bytes)
+{
+    if (!p || !bytes) return fail(HELIOS_EINVAL, "helios_plan_state_bytes: null argument");
+    *bytes = state_bytes(p);
+    return HELIOS_OK;
+}
+
+int helios_plan_state_export(helios_plan* p, void* buf, cudaStream_t s)
+{
+    if (!p || !buf) return fail(HELIOS_EINVAL, "helios_plan_state_export: null argument");
+    if (!p->warm_ready) return fail(HELIOS_EINVAL, "helios_plan_state_export: no evaluation has been made yet");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    p->state_hdr[0] = kStateMagic;
+    p->state_hdr[1] = p->points;
+    p->state_hdr[2] = p->warm_floats;
+    p->state_hdr[3] = p->layers;
+    unsigned char* b = static_cast<unsigned char*>(buf);
+    CUDA_TRY(cudaMemcpyAsync(b, p->state_hdr, sizeof(p->state_hdr), cudaMemcpyDefault, s));
+    b += sizeof(p->state_hdr);
+    CUDA_TRY(cudaMemcpyAsync(b, p->dev.Tpt, sizeof(double) * p->points, cudaMemcpyDefault, s));
+    b += sizeof(double) * p->points;
+    CUDA_TRY(cudaMemcpyAsync(b, p->dev.warm, sizeof(float) * p->warm_floats, cudaMemcpyDefault, s));
+    return HELIOS_OK;
+}
+
+int helios_plan_state_import(helios_plan* p, const void* buf, cudaStream_t s)
+{
+    if (!p || !buf) return fail(HELIOS_EINVAL, "helios_plan_state_import: null argument");
+    CUDA_TRY(cudaSetDevice(p->ctx->device));
+    CUDA_TRY(cudaStreamSynchronize(s));                  // the checkpoint may still be being written
+    int64_t hdr[4];
+    CUDA_TRY(cudaMemcpy(hdr, buf, sizeof hdr, cudaMemcpyDefault));
+    if (hdr[0] != kStateMagic || hdr[1] != p->points || hdr[2] != p->warm_floats || hdr[3] != p->layers)
+        return fail(HELIOS_EINVAL, "helios_plan_state_import: the checkpoint was not made by a plan of this shape");
+    const unsigned char* b = static_cast<const unsigned char*>(buf) + sizeof hdr;
+    CUDA_TRY(cudaMemcpyAsync(p->dev.Tpt, b, sizeof(double) * p->points, cudaMemcpyDefault, s));
+    b += sizeof(double) * p->points;
+    CUDA_TRY(cudaMemcpyAsync(p->dev.warm, b, sizeof(float) * p->warm_floats, cudaMemcpyDefault, s));
+    p->warm_ready = true;
     return HELIOS_OK;
 }
 

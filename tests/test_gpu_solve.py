@@ -298,3 +298,46 @@ def test_dependent_launches_give_the_same_step_bitwise():
         res.append([x.cpu().numpy().copy() for x in (T, Fu, Fd, Fs, Gs, toa, st["mult"], st["metric"])])
     for a, b in zip(*res):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_checkpoint_resume_continues_bit_for_bit(where):
+    # an iteration checkpointed after 7 steps (the caller's arrays plus the plan's exported
+    # state) and resumed in a fresh plan of the same inputs continues exactly as the uninterrupted
+    # iteration: temperatures, multipliers, sign histories, statuses and step counts bit for bit
+    import torch
+    import paper_1606_05474_b300 as hp
+    wls = [synth.small_scattering(L=9, n=40), synth.small_scattering(L=7, n=130, seed_offset=8)]
+    wl = synth.Workload(name="ragged", atms=[w.atms[0] for w in wls], tables=[wls[0].tables[0], wls[1].tables[0]],
+                        n_scat=4)
+    wl.atms[1].table_id = 1
+    T0 = [synth.perturbed_profile(a, 17 + i) for i, a in enumerate(wl.atms)]
+    plan = make_plan(wl)
+    T = pack(T0)
+    st = plan.new_state()
+    for k in range(7):
+        plan.re_step(T, st, warm=k > 0)
+    out = None if where == "device" else torch.empty(0)
+    if out is not None:
+        n = plan.export_state().numel()
+        out = torch.empty(n, dtype=torch.uint8).pin_memory()
+    ck = plan.export_state(out=out)
+    torch.cuda.synchronize()
+    ck_T, ck_st = T.clone(), {k: v.clone() for k, v in st.items()}
+    for _ in range(5):
+        plan.re_step(T, st, warm=True)
+    torch.cuda.synchronize()
+    plan2 = make_plan(wl)
+    with pytest.raises(hp.HeliosError):
+        plan2.export_state()                    # nothing to checkpoint before a first evaluation
+    plan2.import_state(ck)
+    for _ in range(5):
+        plan2.re_step(ck_T, ck_st, warm=True)
+    torch.cuda.synchronize()
+    assert torch.equal(ck_T, T)
+    for k in ("mult", "hist", "nhist", "status", "iters", "metric"):
+        assert torch.equal(ck_st[k], st[k]), k
+    # a checkpoint of a plan of another shape is refused
+    other = make_plan(synth.small_scattering(L=9, n=41))
+    with pytest.raises(hp.HeliosError):
+        other.import_state(ck)
