@@ -151,7 +151,7 @@ class ClockSampler:
 # DRAM traffic (read + write) per cell of the sweep kernel, from ncu captures of the same command
 # on smaller cases (the summaries under profiles/ give each command), valid only for the kernel
 # source they were taken on (sha256 prefix of the kernels and the launch code); null otherwise.
-SWEEP_TRAFFIC = {"kernels_sha256": "5578858e67ef3072", "bytes_per_cell": {"single": 10.14, "batched": 17.40}}
+SWEEP_TRAFFIC = {"kernels_sha256": "86227aafd4f8eac1", "bytes_per_cell": {"single": 10.14, "batched": 17.40}}
 
 
 def kernel_source_hash():

@@ -16,6 +16,17 @@
 
 #include "helios_setup.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// a named range on a profiler's timeline around each call of the boundary (nothing is recorded
+// when no tool is attached)
+namespace {
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 using namespace helios_dev;
 using namespace helios_setup;
 
@@ -303,6 +314,7 @@ int helios_plan_destroy(helios_plan* p)
 int helios_plan_create(helios_ctx* ctx, const helios_batch_t* b, const helios_ktable_t* tabs, int ntab,
                        const helios_params_t* prm, helios_plan** out)
 {
+    CallRange range_("helios_plan_create");
     if (!out) return fail(HELIOS_EINVAL, "helios_plan_create: null output pointer");
     *out = nullptr;
     if (!ctx || !b || !tabs || !prm) return fail(HELIOS_EINVAL, "helios_plan_create: null argument");
@@ -722,6 +734,7 @@ int helios_plan_state_bytes(const helios_plan* p, int64_t* bytes)
 
 int helios_plan_state_export(helios_plan* p, void* buf, cudaStream_t s)
 {
+    CallRange range_("helios_plan_state_export");
     if (!p || !buf) return fail(HELIOS_EINVAL, "helios_plan_state_export: null argument");
     if (!p->warm_ready) return fail(HELIOS_EINVAL, "helios_plan_state_export: no evaluation has been made yet");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
@@ -740,6 +753,7 @@ int helios_plan_state_export(helios_plan* p, void* buf, cudaStream_t s)
 
 int helios_plan_state_import(helios_plan* p, const void* buf, cudaStream_t s)
 {
+    CallRange range_("helios_plan_state_import");
     if (!p || !buf) return fail(HELIOS_EINVAL, "helios_plan_state_import: null argument");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
     CUDA_TRY(cudaStreamSynchronize(s));                  // the checkpoint may still be being written
@@ -971,6 +985,7 @@ extern "C" {
 int helios_interp_opacity(helios_plan* p, const double* T_layer, float* kappa_pts, int32_t* idx_pts, double* w_pts,
                           cudaStream_t s)
 {
+    CallRange range_("helios_interp_opacity");
     if (!p || !T_layer) return fail(HELIOS_EINVAL, "helios_interp_opacity: null argument");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
     long long off = 0;
@@ -988,6 +1003,7 @@ int helios_interp_opacity(helios_plan* p, const double* T_layer, float* kappa_pt
 int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int warm, float* Fup_warm,
                       double* Fup_bol, double* Fdn_bol, float* Fup_toa, float* F_spec, cudaStream_t s)
 {
+    CallRange range_("helios_flux_sweep");
     if (!p || !T_layer || !Fup_bol || !Fdn_bol) return fail(HELIOS_EINVAL, "helios_flux_sweep: null argument");
     if (Fup_warm && (reinterpret_cast<uintptr_t>(Fup_warm) & 15))
         return fail(HELIOS_EINVAL, "helios_flux_sweep: Fup_warm is not 16-byte aligned");
@@ -1013,6 +1029,7 @@ int helios_flux_sweep(helios_plan* p, const double* T_layer, int n_passes, int w
 int helios_temp_update(helios_plan* p, const double* Fup_bol, const double* Fdn_bol, double* T_layer, double* mult,
                        uint8_t* hist, uint8_t* nhist, int32_t* status, int32_t* iters, double* metric, cudaStream_t s)
 {
+    CallRange range_("helios_temp_update");
     if (!p || !Fup_bol || !Fdn_bol || !T_layer || !mult || !hist || !nhist || !status)
         return fail(HELIOS_EINVAL, "helios_temp_update: null argument");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
@@ -1022,6 +1039,7 @@ int helios_temp_update(helios_plan* p, const double* Fup_bol, const double* Fdn_
 int helios_re_step(helios_plan* p, double* T_layer, int warm, double* mult, uint8_t* hist, uint8_t* nhist,
                    int32_t* status, int32_t* iters, double* metric, double* Fup_bol, double* Fdn_bol, cudaStream_t s)
 {
+    CallRange range_("helios_re_step");
     if (!p || !T_layer || !mult || !hist || !nhist || !status)
         return fail(HELIOS_EINVAL, "helios_re_step: null argument");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
@@ -1040,6 +1058,7 @@ int helios_re_step_host(helios_plan* p, double* T_host, double* T_dev, int warm,
                         uint8_t* nhist, int32_t* status, int32_t* iters, double* metric, int32_t* status_host,
                         cudaStream_t s)
 {
+    CallRange range_("helios_re_step_host");
     if (!p || !T_host || !T_dev || !status_host) return fail(HELIOS_EINVAL, "helios_re_step_host: null argument");
     CUDA_TRY(cudaSetDevice(p->ctx->device));
     const size_t tb = sizeof(double) * (size_t)p->layers;
@@ -1053,6 +1072,7 @@ int helios_re_step_host(helios_plan* p, double* T_host, double* T_dev, int warm,
 
 int helios_solve_re(helios_plan* p, double* T_layer, int32_t* iters, int32_t* status, cudaStream_t s)
 {
+    CallRange range_("helios_solve_re");
     if (!p || !T_layer || !iters || !status) return fail(HELIOS_EINVAL, "helios_solve_re: null argument");
     helios_ctx* c = p->ctx;
     CUDA_TRY(cudaSetDevice(c->device));
@@ -1235,6 +1255,7 @@ void cache_store(const char* path, const std::string& key, int tb, int pers, dou
 extern "C" int helios_autotune(helios_ctx* ctx, const helios_batch_t* b, const helios_ktable_t* tabs, int ntab,
                                const helios_params_t* base, const char* cache_path, helios_params_t* tuned)
 {
+    CallRange range_("helios_autotune");
     if (!ctx || !b || !tabs || !base || !tuned || b->A < 1 || ntab < 1)
         return fail(HELIOS_EINVAL, "helios_autotune: bad argument");
     CUDA_TRY(cudaSetDevice(ctx->device));

@@ -24,6 +24,17 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+// a named range on a profiler's timeline around each call of the boundary (nothing is recorded
+// when no tool is attached)
+namespace {
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+};
+}  // namespace
+
 __attribute__((visibility("hidden"))) void helios_set_error_text(const char* msg);
 __attribute__((visibility("hidden"))) int helios_ctx_device(const helios_ctx* ctx);
 __attribute__((visibility("hidden"))) const int2* helios_plan_layers_dev(const helios_plan* p, int* A);
@@ -745,6 +756,7 @@ extern "C" {
 
 int helios_mlp_forward(helios_mlp* m, const float* x, float* y, int B, cudaStream_t s)
 {
+    CallRange range_("helios_mlp_forward");
     if (!m || !x || !y) return mfail(HELIOS_EINVAL, "helios_mlp_forward: null argument");
     if (B < 1 || B > m->max_B) return mfail(HELIOS_EINVAL, "helios_mlp_forward: batch %d outside [1, %d]", B, m->max_B);
     MLP_CUDA(cudaSetDevice(m->device));
@@ -753,6 +765,7 @@ int helios_mlp_forward(helios_mlp* m, const float* x, float* y, int B, cudaStrea
 
 int helios_mlp_grad(helios_mlp* m, const float* x, const float* target, int B, float* loss, cudaStream_t s)
 {
+    CallRange range_("helios_mlp_grad");
     if (!m || !x || !target) return mfail(HELIOS_EINVAL, "helios_mlp_grad: null argument");
     if (B < 1 || B > m->max_B) return mfail(HELIOS_EINVAL, "helios_mlp_grad: batch %d outside [1, %d]", B, m->max_B);
     MLP_CUDA(cudaSetDevice(m->device));
@@ -761,6 +774,7 @@ int helios_mlp_grad(helios_mlp* m, const float* x, const float* target, int B, f
 
 int helios_mlp_adam(helios_mlp* m, float lr, float beta1, float beta2, float eps, cudaStream_t s)
 {
+    CallRange range_("helios_mlp_adam");
     if (!m) return mfail(HELIOS_EINVAL, "helios_mlp_adam: null argument");
     MLP_CUDA(cudaSetDevice(m->device));
     m->t += 1;
@@ -809,6 +823,7 @@ int helios_mlp_initial_profiles(helios_mlp* m, const helios_plan* plan, const fl
                                 const float* x_sd, const float* y_mu, const float* y_sd, const double* T_fallback,
                                 double T_min, double T_max, double* T_layer, int32_t* used, cudaStream_t s)
 {
+    CallRange range_("helios_mlp_initial_profiles");
     if (!m || !plan || !feats || !x_mu || !x_sd || !y_mu || !y_sd || !T_fallback || !T_layer)
         return mfail(HELIOS_EINVAL, "helios_mlp_initial_profiles: null argument");
     if (m->dims[m->nl] < 2) return mfail(HELIOS_EINVAL, "helios_mlp_initial_profiles: the network has fewer than 2 outputs");
@@ -831,6 +846,7 @@ int helios_mlp_initial_profiles(helios_mlp* m, const helios_plan* plan, const fl
 int helios_mlp_train_step(helios_mlp* m, const float* x, const float* target, int B, float lr, float* loss,
                           cudaStream_t s)
 {
+    CallRange range_("helios_mlp_train_step");
     int rc = helios_mlp_grad(m, x, target, B, loss, s);
     if (rc) return rc;
     return helios_mlp_adam(m, lr, 0.9f, 0.999f, 1e-8f, s);
