@@ -659,7 +659,7 @@ int gemm(helios_mlp* m, int M, int N, int K, const float* A, int lda, const floa
                                       (int)UM_SMEM));
         // shared memory for one CTA per SM, the rest of the SM's 256 KB stays L1: the grids here are
         // a few to a hundred CTAs, and the epilogue's row-wise stores merge in L1 (with the largest
-        // carve-out, which the driver picks when three CTAs could share an SM, the forward products
+        // carve-out, which the CUDA driver picks when three CTAs could share an SM, the forward products
         // ran 17% slower)
         MLP_CUDA(cudaFuncSetAttribute(mlp_umma<TA, TB, EPI, BT>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)((100 * (UM_SMEM + 1024) + 228 * 1024 - 1) / (228 * 1024))));
